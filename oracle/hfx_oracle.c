@@ -1,0 +1,643 @@
+/*
+ * hfx_oracle.c -- plain, slow, FP64 CPU oracle for the nonlocal
+ * Hartree-Fock exchange matrix of Betzinger, Friedrich and Bluegel,
+ * "Hybrid functionals within the all-electron FLAPW method" (Sec. III).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only tests/, the smoke check and the CPU-baseline leg of
+ * bench.py do.  It shares no code, header, table or constant with the CUDA
+ * library: every formula below is written out from the paper's definitions.
+ *
+ * Every function states the passage it follows.  Loops are direct sums over
+ * the indices of the definition; OpenMP only distributes independent (k,q)
+ * pairs of the Brillouin-zone sum over host threads.
+ *
+ * Parity pins (tests/test_oracle_*.py) tie each function to something other
+ * than itself: 3-j closed forms and numerical quadrature of spherical
+ * harmonics (Gaunt), radial quadrature of the sphere Fourier transform and a
+ * real-space brute force of the interstitial integral (step function and
+ * Z^IPW), a 3-D quadrature of the muffin-tin triple product (Z^MT),
+ * orthogonality and invariance (multipole transform), Hermiticity,
+ * negative semi-definiteness and a literal four-index sum (V^x), the
+ * analytic integral behind Eq. (div final), and the exchange-energy identity.
+ *
+ * Conventions: complex numbers are interleaved double pairs; see the python
+ * binding oracle/oracle.py for array shapes.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct { double re, im; } cplx;
+
+static inline cplx cmul(cplx a, cplx b) { cplx r = {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; return r; }
+static inline cplx cconjmul(cplx a, cplx b) { /* conj(a) * b */ cplx r = {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re}; return r; }
+static inline cplx cadd(cplx a, cplx b) { cplx r = {a.re + b.re, a.im + b.im}; return r; }
+static inline cplx cscale(cplx a, double s) { cplx r = {a.re * s, a.im * s}; return r; }
+
+/* All inputs of one build.  Pointers are borrowed (owned by the caller). */
+typedef struct {
+    double lattice[9];          /* rows a_i, bohr */
+    int n_atoms;
+    const double *pos_frac;     /* [n_atoms][3] */
+    const double *rmt;          /* [n_atoms] */
+    int lmax, Lmax, P;
+    int mesh[3];
+    const int *n_bands;         /* [N_k] */
+    const int *n_occ;           /* [N_k] */
+    const int *npw;             /* [N_k] */
+    const long long *pw_off;    /* [N_k] row offset into Gk */
+    const int *Gk;              /* [sum npw][3] */
+    const long long *c_off;     /* [N_k] complex offset into c */
+    const double *c;            /* per k: [n_bands][npw] complex */
+    const long long *A_off;     /* [N_k] complex offset into A */
+    const double *A;            /* per k: [n_bands][n_atoms][N_lmp] complex */
+    const double *R;            /* [n_atoms][(Lmax+1)P][2(lmax+1)][2(lmax+1)] */
+    const double *mu;           /* [n_atoms][(Lmax+1)P] */
+    const int *n_ipw;           /* [N_k] per q */
+    const long long *gaux_off;  /* [N_k] row offset into Gaux */
+    const int *Gaux;            /* [sum n_ipw][3] */
+    const long long *v_off;     /* [N_k] complex offset into v */
+    const double *v;            /* per q: [N_aux][N_aux] complex, row-major */
+    double beta;
+} OraSys;
+
+/* ---------------------------------------------------------------- geometry */
+
+static double det3(const double *m) {
+    return m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+           m[2] * (m[3] * m[7] - m[4] * m[6]);
+}
+
+/* Unit-cell volume Omega (Eq. FLAPW-basis normalisation). */
+double ora_omega(const OraSys *s) { return fabs(det3(s->lattice)); }
+
+/* Reciprocal rows b_i with a_i . b_j = 2 pi delta_ij. */
+static void recip(const OraSys *s, double *B) {
+    const double *a = s->lattice;
+    double det = det3(a);
+    /* B = 2 pi (A^{-1})^T ; (A^{-1})^T = cofactor(A) / det */
+    double cof[9];
+    cof[0] = a[4] * a[8] - a[5] * a[7];
+    cof[1] = -(a[3] * a[8] - a[5] * a[6]);
+    cof[2] = a[3] * a[7] - a[4] * a[6];
+    cof[3] = -(a[1] * a[8] - a[2] * a[7]);
+    cof[4] = a[0] * a[8] - a[2] * a[6];
+    cof[5] = -(a[0] * a[7] - a[1] * a[6]);
+    cof[6] = a[1] * a[5] - a[2] * a[4];
+    cof[7] = -(a[0] * a[5] - a[2] * a[3]);
+    cof[8] = a[0] * a[4] - a[1] * a[3];
+    for (int i = 0; i < 9; ++i) B[i] = 2.0 * M_PI * cof[i] / det;
+}
+
+static int n_k(const OraSys *s) { return s->mesh[0] * s->mesh[1] * s->mesh[2]; }
+
+static void mesh_j(const OraSys *s, int ik, int *j) {
+    j[2] = ik % s->mesh[2];
+    j[1] = (ik / s->mesh[2]) % s->mesh[1];
+    j[0] = ik / (s->mesh[1] * s->mesh[2]);
+}
+
+/* Sec. III.C: the mesh contains k - q.  For a pair (k, q) return k' = k - q
+ * folded into the mesh and the reciprocal vector G0 = k - q - k' (integer
+ * coordinates in units of b_i). */
+void ora_fold(const OraSys *s, int ik, int iq, int *ikp, int *G0) {
+    int jk[3], jq[3], jp[3];
+    mesh_j(s, ik, jk);
+    mesh_j(s, iq, jq);
+    for (int i = 0; i < 3; ++i) {
+        int d = jk[i] - jq[i];
+        int f = ((d % s->mesh[i]) + s->mesh[i]) % s->mesh[i];
+        jp[i] = f;
+        G0[i] = (d - f) / s->mesh[i];
+    }
+    *ikp = (jp[0] * s->mesh[1] + jp[1]) * s->mesh[2] + jp[2];
+}
+
+static void cart_of(const double *B, const double *frac, double *out) {
+    for (int x = 0; x < 3; ++x) out[x] = frac[0] * B[0 * 3 + x] + frac[1] * B[1 * 3 + x] + frac[2] * B[2 * 3 + x];
+}
+
+/* ---------------------------------------------------------------- Gaunt */
+
+static double fact(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= (double)i;
+    return f;
+}
+
+/* Wigner 3-j symbol from Racah's closed formula. */
+double ora_threej(int j1, int j2, int j3, int m1, int m2, int m3) {
+    if (m1 + m2 + m3 != 0) return 0.0;
+    if (j3 < abs(j1 - j2) || j3 > j1 + j2) return 0.0;
+    if (abs(m1) > j1 || abs(m2) > j2 || abs(m3) > j3) return 0.0;
+    /* (j1 j2 j3; 0 0 0) vanishes for odd j1 + j2 + j3 (reflection symmetry) */
+    if (m1 == 0 && m2 == 0 && ((j1 + j2 + j3) & 1)) return 0.0;
+    double tri = fact(j1 + j2 - j3) * fact(j1 - j2 + j3) * fact(-j1 + j2 + j3) / fact(j1 + j2 + j3 + 1);
+    double pre = sqrt(tri * fact(j1 + m1) * fact(j1 - m1) * fact(j2 + m2) * fact(j2 - m2) *
+                      fact(j3 + m3) * fact(j3 - m3));
+    double sum = 0.0;
+    for (int t = 0; t <= j1 + j2 + j3; ++t) {
+        int a1 = j3 - j2 + t + m1, a2 = j3 - j1 + t - m2, a3 = j1 + j2 - j3 - t;
+        int a4 = j1 - t - m1, a5 = j2 - t + m2;
+        if (a1 < 0 || a2 < 0 || a3 < 0 || a4 < 0 || a5 < 0) continue;
+        double den = fact(t) * fact(a1) * fact(a2) * fact(a3) * fact(a4) * fact(a5);
+        sum += ((t & 1) ? -1.0 : 1.0) / den;
+    }
+    int ph = j1 - j2 - m3;
+    double sign = ((ph % 2) + 2) % 2 ? -1.0 : 1.0;
+    return sign * pre * sum;
+}
+
+/* Integral of Y_{l1 m1} Y_{l2 m2} Y_{l3 m3} over the unit sphere (complex
+ * Condon-Shortley harmonics; textbook 3-j form). */
+static double int_yyy(int l1, int m1, int l2, int m2, int l3, int m3) {
+    double w = ora_threej(l1, l2, l3, 0, 0, 0);
+    if (w == 0.0) return 0.0;
+    return sqrt((2.0 * l1 + 1.0) * (2.0 * l2 + 1.0) * (2.0 * l3 + 1.0) / (4.0 * M_PI)) * w *
+           ora_threej(l1, l2, l3, m1, m2, m3);
+}
+
+/* G(LM; l m; l' m') = int Y*_LM Y*_lm Y_l'm' dOmega: the angular factor of
+ * the MT product functions u_lp u_l'p' Y_LM (Sec. III.B).  Uses
+ * Y*_lm = (-1)^m Y_{l,-m}. */
+double ora_gaunt(int L, int M, int l1, int m1, int l2, int m2) {
+    if (abs(M) > L || abs(m1) > l1 || abs(m2) > l2) return 0.0;
+    double s = ((M + m1) & 1) ? -1.0 : 1.0;
+    return s * int_yyy(L, -M, l1, -m1, l2, m2);
+}
+
+/* ---------------------------------------------------------- step function */
+
+/* Theta_K = (1/Omega) int_cell Theta(r) e^{-i K.r} d^3r for the step function
+ * of Eq. (step function): 1 in the interstitial, 0 inside every MT sphere.
+ * The Fourier transform of a sphere of radius S at R_a is
+ * e^{-i K.R_a} 4 pi S^3 j1(|K| S) / (|K| S). */
+void ora_theta(const OraSys *s, int n, const int *K, double *out) {
+    double B[9];
+    recip(s, B);
+    double om = ora_omega(s);
+    for (int i = 0; i < n; ++i) {
+        double kf[3] = {(double)K[3 * i], (double)K[3 * i + 1], (double)K[3 * i + 2]};
+        double kc[3];
+        cart_of(B, kf, kc);
+        double kn = sqrt(kc[0] * kc[0] + kc[1] * kc[1] + kc[2] * kc[2]);
+        int zero = (K[3 * i] == 0 && K[3 * i + 1] == 0 && K[3 * i + 2] == 0);
+        cplx t = {zero ? 1.0 : 0.0, 0.0};
+        for (int a = 0; a < s->n_atoms; ++a) {
+            double S = s->rmt[a];
+            double f;
+            double x = kn * S;
+            if (zero) {
+                f = 4.0 * M_PI * S * S * S / 3.0;
+            } else if (x < 1e-3) {
+                /* j1(x)/x = 1/3 - x^2/30 + O(x^4) */
+                f = 4.0 * M_PI * S * S * S * (1.0 / 3.0 - x * x / 30.0);
+            } else {
+                double j1 = sin(x) / (x * x) - cos(x) / x;
+                f = 4.0 * M_PI * S * S * S * j1 / x;
+            }
+            /* phase e^{-i K.R_a}, K.R_a = 2 pi sum_i K_i f_i */
+            double ph = 2.0 * M_PI * (K[3 * i] * s->pos_frac[3 * a] + K[3 * i + 1] * s->pos_frac[3 * a + 1] +
+                                      K[3 * i + 2] * s->pos_frac[3 * a + 2]);
+            t.re -= f * cos(ph) / om;
+            t.im -= -f * sin(ph) / om;
+        }
+        out[2 * i] = t.re;
+        out[2 * i + 1] = t.im;
+    }
+}
+
+/* ------------------------------------------------------- index helpers */
+
+static int n_lmp(const OraSys *s) { return 2 * (s->lmax + 1) * (s->lmax + 1); }
+static int n_lp(const OraSys *s) { return 2 * (s->lmax + 1); }
+static int n_mt(const OraSys *s) { return s->n_atoms * (s->Lmax + 1) * (s->Lmax + 1) * s->P; }
+static int lm_idx(int l, int m) { return l * l + l + m; }
+
+static const cplx *cptr(const double *base, long long off) { return (const cplx *)(base + 2 * off); }
+
+/* ------------------------------------------------------------ Z^MT */
+
+/* Muffin-tin part of the projection vectors (Sec. III.B and Eq. vec-mat-vec):
+ *   Z[(a,L,M,P), m, n] = < M^q_{aLMP} phi_{m,k-q} | phi_{n,k} >
+ *     = e^{-i q.R_a} sum_{l m1 p l' p'} G(LM; l m1; l', m1+M)
+ *         R^a_{LP; lp; l'p'} conj(A^a_{l m1 p}(m, k')) A^a_{l', m1+M, p'}(n, k).
+ * The phase comes from the Bloch sum Eq. (MT functions) evaluated in the home
+ * cell; the MT coefficients of phi_{m,k-q} are those of phi_{m,k'}.
+ * Output Z[I][m][n], I over the MT product basis, m < n_occ(k'), n < n_bands(k). */
+int ora_zmt(const OraSys *s, int ik, int iq, double *Zout) {
+    int ikp, G0[3];
+    ora_fold(s, ik, iq, &ikp, G0);
+    int nb = s->n_bands[ik], no = s->n_occ[ikp];
+    int nlmp = n_lmp(s), nlp = n_lp(s), P = s->P;
+    int nLP = (s->Lmax + 1) * P;
+    int nlm = (s->lmax + 1) * (s->lmax + 1), nLM = (s->Lmax + 1) * (s->Lmax + 1);
+    /* Gaunt values G(LM; l m1; l2, m1+M), tabulated once per call */
+    double *gt = (double *)malloc(sizeof(double) * nLM * nlm * (s->lmax + 1));
+    for (int L = 0; L <= s->Lmax; ++L)
+        for (int M = -L; M <= L; ++M)
+            for (int l = 0; l <= s->lmax; ++l)
+                for (int m1 = -l; m1 <= l; ++m1)
+                    for (int l2 = 0; l2 <= s->lmax; ++l2)
+                        gt[((size_t)lm_idx(L, M) * nlm + lm_idx(l, m1)) * (s->lmax + 1) + l2] =
+                            ora_gaunt(L, M, l, m1, l2, m1 + M);
+    int jq[3];
+    mesh_j(s, iq, jq);
+    double qf[3] = {(double)jq[0] / s->mesh[0], (double)jq[1] / s->mesh[1], (double)jq[2] / s->mesh[2]};
+    const cplx *Ak = cptr(s->A, s->A_off[ik]);
+    const cplx *Akp = cptr(s->A, s->A_off[ikp]);
+    cplx *Z = (cplx *)Zout;
+    for (int a = 0; a < s->n_atoms; ++a) {
+        /* e^{-i q.R_a}, q.R_a = 2 pi sum_i qf_i f_i */
+        double ph = 2.0 * M_PI * (qf[0] * s->pos_frac[3 * a] + qf[1] * s->pos_frac[3 * a + 1] + qf[2] * s->pos_frac[3 * a + 2]);
+        cplx phase = {cos(ph), -sin(ph)};
+        for (int L = 0; L <= s->Lmax; ++L)
+            for (int M = -L; M <= L; ++M)
+                for (int Pi = 0; Pi < P; ++Pi) {
+                    int I = (a * nLM + lm_idx(L, M)) * P + Pi;
+                    const double *Rap = s->R + ((size_t)a * nLP + (size_t)L * P + Pi) * nlp * nlp;
+                    for (int m = 0; m < no; ++m)
+                        for (int n = 0; n < nb; ++n) {
+                            cplx acc = {0.0, 0.0};
+                            for (int l = 0; l <= s->lmax; ++l)
+                                for (int m1 = -l; m1 <= l; ++m1)
+                                    for (int p = 0; p < 2; ++p)
+                                        for (int l2 = 0; l2 <= s->lmax; ++l2) {
+                                            int m2 = m1 + M;
+                                            if (m2 < -l2 || m2 > l2) continue;
+                                            double g = gt[((size_t)lm_idx(L, M) * nlm + lm_idx(l, m1)) * (s->lmax + 1) + l2];
+                                            if (g == 0.0) continue;
+                                            for (int p2 = 0; p2 < 2; ++p2) {
+                                                double r = Rap[(2 * l + p) * nlp + 2 * l2 + p2];
+                                                cplx am = Akp[((size_t)m * s->n_atoms + a) * nlmp + 2 * lm_idx(l, m1) + p];
+                                                cplx an = Ak[((size_t)n * s->n_atoms + a) * nlmp + 2 * lm_idx(l2, m2) + p2];
+                                                acc = cadd(acc, cscale(cconjmul(am, an), g * r));
+                                            }
+                                        }
+                            Z[((size_t)I * no + m) * nb + n] = cmul(phase, acc);
+                        }
+                }
+    }
+    free(gt);
+    return 0;
+}
+
+/* ------------------------------------------------------------ Z^IPW */
+
+/* Interstitial part, definition (Sec. III.B, IPW functions and Eq. step
+ * function, with the wave functions of Eq. FLAPW-basis):
+ *   Z[G, m, n] = < M^q_G phi_{m,k-q} | phi_{n,k} >
+ *     = Omega^{-1/2} sum_{G1 in k'} sum_{G2 in k} conj(c_{G1}(m,k')) c_{G2}(n,k)
+ *         Theta_{G + G1 - G2 - G0},   G0 = k - q - k'.
+ * Direct triple sum; used on small inputs. */
+int ora_zipw_direct(const OraSys *s, int ik, int iq, double *Zout) {
+    int ikp, G0[3];
+    ora_fold(s, ik, iq, &ikp, G0);
+    int nb = s->n_bands[ik], no = s->n_occ[ikp];
+    int npk = s->npw[ik], npp = s->npw[ikp], ng = s->n_ipw[iq];
+    const int *Gk = s->Gk + 3 * s->pw_off[ik];
+    const int *Gp = s->Gk + 3 * s->pw_off[ikp];
+    const int *Ga = s->Gaux + 3 * s->gaux_off[iq];
+    const cplx *ck = cptr(s->c, s->c_off[ik]);
+    const cplx *cp = cptr(s->c, s->c_off[ikp]);
+    double rs = 1.0 / sqrt(ora_omega(s));
+    cplx *Z = (cplx *)Zout;
+    for (int g = 0; g < ng; ++g) {
+        for (int m = 0; m < no; ++m)
+            for (int n = 0; n < nb; ++n) {
+                cplx acc = {0.0, 0.0};
+                for (int i1 = 0; i1 < npp; ++i1)
+                    for (int i2 = 0; i2 < npk; ++i2) {
+                        int K[3];
+                        for (int x = 0; x < 3; ++x) K[x] = Ga[3 * g + x] + Gp[3 * i1 + x] - Gk[3 * i2 + x] - G0[x];
+                        double th[2];
+                        ora_theta(s, 1, K, th);
+                        cplx t = {th[0], th[1]};
+                        cplx prod = cconjmul(cp[(size_t)m * npp + i1], ck[(size_t)n * npk + i2]);
+                        acc = cadd(acc, cmul(prod, t));
+                    }
+                Z[((size_t)g * no + m) * nb + n] = cscale(acc, rs);
+            }
+    }
+    return 0;
+}
+
+/* The same quantity organised in the two steps of the survey's hot path:
+ * first the step-function-weighted wave function in reciprocal space,
+ *   T_n(K) = sum_{G2 in k} Theta_{K - G2} c_{G2}(n,k),
+ * then Z[G, m, n] = Omega^{-1/2} sum_{G1 in k'} conj(c_{G1}(m,k')) T_n(G + G1 - G0).
+ * T_n is evaluated on demand for each needed K (no tables), so this function
+ * differs from the direct sum only in the order of the two finite sums. */
+typedef struct { int lo[3], dim[3]; cplx *T; } ThetaPsi;
+
+static void thetapsi_build(const OraSys *s, int ik, const int *lo, const int *hi, ThetaPsi *tp) {
+    int nb = s->n_bands[ik], npk = s->npw[ik];
+    const int *Gk = s->Gk + 3 * s->pw_off[ik];
+    const cplx *ck = cptr(s->c, s->c_off[ik]);
+    for (int x = 0; x < 3; ++x) { tp->lo[x] = lo[x]; tp->dim[x] = hi[x] - lo[x] + 1; }
+    size_t nbox = (size_t)tp->dim[0] * tp->dim[1] * tp->dim[2];
+    tp->T = (cplx *)calloc(nbox * nb, sizeof(cplx));
+    /* step function on the difference box K - G2 */
+    int dlo[3], dhi[3];
+    for (int x = 0; x < 3; ++x) {
+        int gmin = 1 << 30, gmax = -(1 << 30);
+        for (int i = 0; i < npk; ++i) { if (Gk[3 * i + x] < gmin) gmin = Gk[3 * i + x]; if (Gk[3 * i + x] > gmax) gmax = Gk[3 * i + x]; }
+        dlo[x] = lo[x] - gmax;
+        dhi[x] = hi[x] - gmin;
+    }
+    int dd[3] = {dhi[0] - dlo[0] + 1, dhi[1] - dlo[1] + 1, dhi[2] - dlo[2] + 1};
+    size_t nd = (size_t)dd[0] * dd[1] * dd[2];
+    int *Kd = (int *)malloc(nd * 3 * sizeof(int));
+    double *th = (double *)malloc(nd * 2 * sizeof(double));
+    for (size_t i = 0; i < nd; ++i) {
+        int z = (int)(i % dd[2]), y = (int)((i / dd[2]) % dd[1]), xx = (int)(i / ((size_t)dd[1] * dd[2]));
+        Kd[3 * i] = dlo[0] + xx; Kd[3 * i + 1] = dlo[1] + y; Kd[3 * i + 2] = dlo[2] + z;
+    }
+    ora_theta(s, (int)nd, Kd, th);
+#pragma omp parallel for schedule(dynamic)
+    for (long long ib = 0; ib < (long long)nbox; ++ib) {
+        int z = (int)(ib % tp->dim[2]), y = (int)((ib / tp->dim[2]) % tp->dim[1]), xx = (int)(ib / ((size_t)tp->dim[1] * tp->dim[2]));
+        int K[3] = {lo[0] + xx, lo[1] + y, lo[2] + z};
+        for (int n = 0; n < nb; ++n) {
+            cplx acc = {0.0, 0.0};
+            for (int i2 = 0; i2 < npk; ++i2) {
+                int d0 = K[0] - Gk[3 * i2] - dlo[0], d1 = K[1] - Gk[3 * i2 + 1] - dlo[1], d2 = K[2] - Gk[3 * i2 + 2] - dlo[2];
+                size_t di = ((size_t)d0 * dd[1] + d1) * dd[2] + d2;
+                cplx t = {th[2 * di], th[2 * di + 1]};
+                acc = cadd(acc, cmul(t, ck[(size_t)n * npk + i2]));
+            }
+            tp->T[(size_t)n * nbox + ib] = acc;
+        }
+    }
+    free(Kd);
+    free(th);
+}
+
+/* Bounds of every K = G + G1 - G0 needed by the pairs of k. */
+static void thetapsi_bounds(const OraSys *s, int ik, int *lo, int *hi) {
+    for (int x = 0; x < 3; ++x) { lo[x] = 1 << 30; hi[x] = -(1 << 30); }
+    for (int iq = 0; iq < n_k(s); ++iq) {
+        int ikp, G0[3];
+        ora_fold(s, ik, iq, &ikp, G0);
+        const int *Gp = s->Gk + 3 * s->pw_off[ikp];
+        const int *Ga = s->Gaux + 3 * s->gaux_off[iq];
+        for (int x = 0; x < 3; ++x) {
+            int amin = 1 << 30, amax = -(1 << 30), pmin = 1 << 30, pmax = -(1 << 30);
+            for (int g = 0; g < s->n_ipw[iq]; ++g) { int v = Ga[3 * g + x]; if (v < amin) amin = v; if (v > amax) amax = v; }
+            for (int g = 0; g < s->npw[ikp]; ++g) { int v = Gp[3 * g + x]; if (v < pmin) pmin = v; if (v > pmax) pmax = v; }
+            if (s->n_ipw[iq] == 0 || s->npw[ikp] == 0) continue;
+            if (amin + pmin - G0[x] < lo[x]) lo[x] = amin + pmin - G0[x];
+            if (amax + pmax - G0[x] > hi[x]) hi[x] = amax + pmax - G0[x];
+        }
+    }
+    for (int x = 0; x < 3; ++x) if (lo[x] > hi[x]) { lo[x] = 0; hi[x] = 0; }
+}
+
+static void zipw_from_thetapsi(const OraSys *s, int ik, int iq, const ThetaPsi *tp, cplx *Z) {
+    int ikp, G0[3];
+    ora_fold(s, ik, iq, &ikp, G0);
+    int nb = s->n_bands[ik], no = s->n_occ[ikp];
+    int npp = s->npw[ikp], ng = s->n_ipw[iq];
+    const int *Gp = s->Gk + 3 * s->pw_off[ikp];
+    const int *Ga = s->Gaux + 3 * s->gaux_off[iq];
+    const cplx *cp = cptr(s->c, s->c_off[ikp]);
+    size_t nbox = (size_t)tp->dim[0] * tp->dim[1] * tp->dim[2];
+    double rs = 1.0 / sqrt(ora_omega(s));
+    for (int g = 0; g < ng; ++g)
+        for (int m = 0; m < no; ++m)
+            for (int n = 0; n < nb; ++n) {
+                cplx acc = {0.0, 0.0};
+                for (int i1 = 0; i1 < npp; ++i1) {
+                    int K0 = Ga[3 * g] + Gp[3 * i1] - G0[0] - tp->lo[0];
+                    int K1 = Ga[3 * g + 1] + Gp[3 * i1 + 1] - G0[1] - tp->lo[1];
+                    int K2 = Ga[3 * g + 2] + Gp[3 * i1 + 2] - G0[2] - tp->lo[2];
+                    size_t bi = ((size_t)K0 * tp->dim[1] + K1) * tp->dim[2] + K2;
+                    acc = cadd(acc, cconjmul(cp[(size_t)m * npp + i1], tp->T[(size_t)n * nbox + bi]));
+                }
+                Z[((size_t)g * no + m) * nb + n] = cscale(acc, rs);
+            }
+}
+
+int ora_zipw(const OraSys *s, int ik, int iq, double *Zout) {
+    int lo[3], hi[3];
+    thetapsi_bounds(s, ik, lo, hi);
+    ThetaPsi tp;
+    thetapsi_build(s, ik, lo, hi, &tp);
+    zipw_from_thetapsi(s, ik, iq, &tp, (cplx *)Zout);
+    free(tp.T);
+    return 0;
+}
+
+/* ------------------------------------------------- multipole transform */
+
+/* Sec. III.C, unitary transformation of the MT functions of one (a, L):
+ * an orthogonal P x P matrix T whose first row is mu/|mu| (the function that
+ * keeps the multipole moment) and whose remaining rows span the multipole-free
+ * complement.  For P = 2 this is exactly the paper's two-function formula
+ * (second row (mu2, -mu1)/|mu|); for P > 2 ("generally") the complement is the
+ * Householder reflection that maps mu/|mu| to e_1.  Row-major output. */
+void ora_transform_T(int P, const double *mu, double *T) {
+    double nrm = 0.0;
+    for (int i = 0; i < P; ++i) nrm += mu[i] * mu[i];
+    nrm = sqrt(nrm);
+    memset(T, 0, sizeof(double) * P * P);
+    if (nrm == 0.0) {
+        for (int i = 0; i < P; ++i) T[i * P + i] = 1.0;
+        return;
+    }
+    if (P == 1) { T[0] = mu[0] / nrm; return; }
+    if (P == 2) {
+        T[0] = mu[0] / nrm; T[1] = mu[1] / nrm;
+        T[2] = mu[1] / nrm; T[3] = -mu[0] / nrm;
+        return;
+    }
+    /* w = u + s e_1 with u = mu/|mu|, s = sign(u_1); H = I - 2 w w^T / w^T w
+     * maps u to -s e_1, so T = -s H has first row u and is orthogonal. */
+    double u0 = mu[0] / nrm, sg = (u0 >= 0.0) ? 1.0 : -1.0;
+    double *w = (double *)malloc(sizeof(double) * P);
+    double ww = 0.0;
+    for (int i = 0; i < P; ++i) { w[i] = mu[i] / nrm; }
+    w[0] += sg;
+    for (int i = 0; i < P; ++i) ww += w[i] * w[i];
+    for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j)
+            T[i * P + j] = -sg * ((i == j ? 1.0 : 0.0) - 2.0 * w[i] * w[j] / ww);
+    free(w);
+}
+
+/* ------------------------------------------------------------ V^x */
+
+/* Full projection vector of a pair, Z[I][m][n] over the whole MPB (MT part
+ * first, then the interstitial plane waves in list order). */
+static void z_pair(const OraSys *s, int ik, int iq, const ThetaPsi *tp, cplx *Z) {
+    int ikp, G0[3];
+    ora_fold(s, ik, iq, &ikp, G0);
+    int nb = s->n_bands[ik], no = s->n_occ[ikp];
+    size_t mt = (size_t)n_mt(s) * no * nb;
+    ora_zmt(s, ik, iq, (double *)Z);
+    zipw_from_thetapsi(s, ik, iq, tp, Z + mt);
+}
+
+/* Apply the multipole transform of every (a, L, M) to the MT rows of Z
+ * (Z_t = T Z) and to v (v_t = T v T^T); the interstitial rows are unchanged. */
+static void transform_pair(const OraSys *s, int n_aux, int ncol, cplx *Z, cplx *v) {
+    int P = s->P, nlm = (s->Lmax + 1) * (s->Lmax + 1);
+    double *T = (double *)malloc(sizeof(double) * P * P);
+    cplx *tmp = (cplx *)malloc(sizeof(cplx) * P * (size_t)(ncol > n_aux ? ncol : n_aux));
+    for (int a = 0; a < s->n_atoms; ++a)
+        for (int L = 0; L <= s->Lmax; ++L) {
+            ora_transform_T(P, s->mu + (size_t)a * (s->Lmax + 1) * P + (size_t)L * P, T);
+            for (int M = -L; M <= L; ++M) {
+                int base = (a * nlm + lm_idx(L, M)) * P;
+                /* rows of Z */
+                for (int i = 0; i < P; ++i)
+                    for (int cc = 0; cc < ncol; ++cc) {
+                        cplx acc = {0, 0};
+                        for (int j = 0; j < P; ++j) acc = cadd(acc, cscale(Z[(size_t)(base + j) * ncol + cc], T[i * P + j]));
+                        tmp[(size_t)i * ncol + cc] = acc;
+                    }
+                for (int i = 0; i < P; ++i) memcpy(Z + (size_t)(base + i) * ncol, tmp + (size_t)i * ncol, sizeof(cplx) * ncol);
+                /* rows of v */
+                for (int i = 0; i < P; ++i)
+                    for (int cc = 0; cc < n_aux; ++cc) {
+                        cplx acc = {0, 0};
+                        for (int j = 0; j < P; ++j) acc = cadd(acc, cscale(v[(size_t)(base + j) * n_aux + cc], T[i * P + j]));
+                        tmp[(size_t)i * n_aux + cc] = acc;
+                    }
+                for (int i = 0; i < P; ++i) memcpy(v + (size_t)(base + i) * n_aux, tmp + (size_t)i * n_aux, sizeof(cplx) * n_aux);
+                /* columns of v */
+                for (int r = 0; r < n_aux; ++r) {
+                    cplx row[64];
+                    for (int i = 0; i < P; ++i) {
+                        cplx acc = {0, 0};
+                        for (int j = 0; j < P; ++j) acc = cadd(acc, cscale(v[(size_t)r * n_aux + base + j], T[i * P + j]));
+                        row[i] = acc;
+                    }
+                    for (int i = 0; i < P; ++i) v[(size_t)r * n_aux + base + i] = row[i];
+                }
+            }
+        }
+    free(T);
+    free(tmp);
+}
+
+/* Eq. (div final) with e^{-beta q0^2} = beta, returned as the positive
+ * bracket b such that the diagonal correction is -f_nk b:
+ *   b = (pi beta)^{-1/2} erf(sqrt(beta) q0)
+ *       - (4 pi / (N_k Omega)) sum_{q in mesh, G: 0 < |q+G| <= q0} e^{-beta|q+G|^2}/|q+G|^2.
+ * The 4 pi turns the discrete sum into (1/2pi^2) times the BZ integral of the
+ * same integrand (the paper's printed prefactor lacks it). */
+double ora_vdiv(const OraSys *s) {
+    double beta = s->beta;
+    double q0 = sqrt(-log(beta) / beta);
+    double B[9];
+    recip(s, B);
+    double om = ora_omega(s);
+    int nk = n_k(s);
+    double sum = 0.0;
+    int bound[3];
+    for (int i = 0; i < 3; ++i) {
+        double an = sqrt(s->lattice[3 * i] * s->lattice[3 * i] + s->lattice[3 * i + 1] * s->lattice[3 * i + 1] +
+                         s->lattice[3 * i + 2] * s->lattice[3 * i + 2]);
+        bound[i] = (int)ceil(q0 * an / (2.0 * M_PI)) + 2;
+    }
+    for (int iq = 0; iq < nk; ++iq) {
+        int j[3];
+        mesh_j(s, iq, j);
+        double qf[3] = {(double)j[0] / s->mesh[0], (double)j[1] / s->mesh[1], (double)j[2] / s->mesh[2]};
+        for (int g0 = -bound[0]; g0 <= bound[0]; ++g0)
+            for (int g1 = -bound[1]; g1 <= bound[1]; ++g1)
+                for (int g2 = -bound[2]; g2 <= bound[2]; ++g2) {
+                    double f[3] = {qf[0] + g0, qf[1] + g1, qf[2] + g2};
+                    double c[3];
+                    cart_of(B, f, c);
+                    double q2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+                    if (q2 == 0.0 || q2 > q0 * q0) continue;
+                    sum += exp(-beta * q2) / q2;
+                }
+    }
+    return erf(sqrt(beta) * q0) / sqrt(M_PI * beta) - 4.0 * M_PI / (nk * om) * sum;
+}
+
+/* V^x_{nn'}(k) of Eq. (vec-mat-vec), with the Brillouin-zone sum read as
+ * (1/N_k) sum_q:
+ *   V[n][n'] = -(1/N_k) sum_q sum_{m < n_occ(k-q)} sum_{I,J}
+ *                 conj(Z[I,m,n]) v_IJ(q) Z[J,m,n']
+ * plus, if q0term, -delta_nn' f_nk b (Eq. div final; f_nk = 1 for
+ * n < n_occ(k)).  transformed = 1 evaluates the same sum in the multipole-
+ * transformed basis (Z_t = T Z, v_t = T v T^T, Sec. III.C) with dense loops.
+ * Output V[n][n'] complex, n_bands(k)^2.  OpenMP distributes the q sum; the
+ * per-q results are added in q order. */
+int ora_vx(const OraSys *s, int ik, int transformed, int q0term, double *Vout) {
+    int nk = n_k(s), nb = s->n_bands[ik];
+    int lo[3], hi[3];
+    thetapsi_bounds(s, ik, lo, hi);
+    ThetaPsi tp;
+    thetapsi_build(s, ik, lo, hi, &tp);
+    cplx *part = (cplx *)calloc((size_t)nk * nb * nb, sizeof(cplx));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int iq = 0; iq < nk; ++iq) {
+        int ikp, G0[3];
+        ora_fold(s, ik, iq, &ikp, G0);
+        int no = s->n_occ[ikp];
+        int n_aux = n_mt(s) + s->n_ipw[iq];
+        int ncol = no * nb;
+        cplx *Z = (cplx *)malloc(sizeof(cplx) * (size_t)n_aux * ncol);
+        z_pair(s, ik, iq, &tp, Z);
+        const cplx *vq = cptr(s->v, s->v_off[iq]);
+        cplx *vw = (cplx *)vq;
+        cplx *vcopy = NULL;
+        if (transformed) {
+            vcopy = (cplx *)malloc(sizeof(cplx) * (size_t)n_aux * n_aux);
+            memcpy(vcopy, vq, sizeof(cplx) * (size_t)n_aux * n_aux);
+            transform_pair(s, n_aux, ncol, Z, vcopy);
+            vw = vcopy;
+        }
+        /* Y = v Z (each Y[I][c] summed over J in ascending order) */
+        cplx *Y = (cplx *)calloc((size_t)n_aux * ncol, sizeof(cplx));
+        for (int I = 0; I < n_aux; ++I)
+            for (int J = 0; J < n_aux; ++J) {
+                cplx vij = vw[(size_t)I * n_aux + J];
+                const cplx *zr = Z + (size_t)J * ncol;
+                cplx *yr = Y + (size_t)I * ncol;
+                for (int cc = 0; cc < ncol; ++cc) yr[cc] = cadd(yr[cc], cmul(vij, zr[cc]));
+            }
+        /* P[n][n'] = sum_m sum_I conj(Z[I,m,n]) Y[I,m,n'] (m outer, I inner) */
+        cplx *Pq = part + (size_t)iq * nb * nb;
+        for (int m = 0; m < no; ++m)
+            for (int I = 0; I < n_aux; ++I) {
+                const cplx *zr = Z + (size_t)I * ncol + (size_t)m * nb;
+                const cplx *yr = Y + (size_t)I * ncol + (size_t)m * nb;
+                for (int n = 0; n < nb; ++n)
+                    for (int n2 = 0; n2 < nb; ++n2)
+                        Pq[(size_t)n * nb + n2] = cadd(Pq[(size_t)n * nb + n2], cconjmul(zr[n], yr[n2]));
+            }
+        free(Y);
+        free(Z);
+        free(vcopy);
+    }
+    cplx *V = (cplx *)Vout;
+    for (int i = 0; i < nb * nb; ++i) { V[i].re = 0.0; V[i].im = 0.0; }
+    for (int iq = 0; iq < nk; ++iq)
+        for (int i = 0; i < nb * nb; ++i) V[i] = cadd(V[i], part[(size_t)iq * nb * nb + i]);
+    for (int i = 0; i < nb * nb; ++i) V[i] = cscale(V[i], -1.0 / nk);
+    if (q0term) {
+        double b = ora_vdiv(s);
+        for (int n = 0; n < s->n_occ[ik] && n < nb; ++n) V[(size_t)n * nb + n].re -= b;
+    }
+    free(part);
+    free(tp.T);
+    return 0;
+}
+
+int ora_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
