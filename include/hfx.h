@@ -1,0 +1,217 @@
+/*
+ * hfx.h -- C ABI of the GB300 (sm_103a) library that builds the nonlocal
+ * Hartree-Fock exchange matrix of the PBE0-in-FLAPW method (Betzinger,
+ * Friedrich, Bluegel; Sec. III):
+ *
+ *   V^x_{nn'}(k) = -(1/N_k) sum_q sum_{m<n_occ(k-q)} sum_{IJ}
+ *                   conj(Z_q[I,m,n]) v_IJ(q) Z_q[J,m,n']           Eq. (vec-mat-vec)
+ *                 - delta_nn' f_nk b                               Eq. (div final)
+ *
+ * with the mixed-product-basis projections Z_q[I,m,n] = < M_I^q phi_{m,k-q} | phi_{n,k} >
+ * (Sec. III.B) and the Coulomb matrix v(q) of Eq. (coulomb matrix), which the
+ * library makes block-sparse with the multipole transformation of Sec. III.C.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Status: every function returns HFX_OK (0) or a negative HFX_E* code; no
+ *   exception, abort or exit crosses the ABI.  hfx_strerror() names a code and
+ *   hfx_last_error() returns the context's last message (valid until the next
+ *   call on that context).
+ * - Ownership: inputs are deep-copied (to the device) before the call
+ *   returns; the caller keeps and may free its buffers.  Outputs go into
+ *   caller-allocated buffers of the documented size.
+ * - Complex numbers are interleaved double pairs (C99 double _Complex layout).
+ *   Matrices are row-major, dense, 0-based.
+ * - Index conventions (Eq. FLAPW-basis and Sec. III.B):
+ *     LAPW MT index  lmp = 2*(l*l + l + m) + p,  p in {0,1},  N_lmp = 2(lmax+1)^2
+ *     radial index   lp  = 2*l + p
+ *     MPB MT index   I   = (a*(Lmax+1)^2 + L*L + L + M)*P + Pidx   (atom outermost)
+ *     MPB IPW index  I   = N_MT + g, g over the per-q plane-wave list,
+ *                    N_MT = n_atoms (Lmax+1)^2 P,  N_aux(q) = N_MT + n_ipw(q)
+ *     k mesh         k = sum_i (j_i/N_i) b_i,  ik = (j0*N1 + j1)*N2 + j2 (Gamma-centred);
+ *                    the q mesh is the same set and k - q is folded back into it.
+ * - One context is not thread-safe.  All device work runs on the stream given
+ *   in hfx_options (NULL = the legacy default stream) on the device given there.
+ * - A context keeps every input resident in device memory; building V^x leaves
+ *   the result on the device until hfx_get_exchange copies it out.
+ */
+#ifndef HFX_H
+#define HFX_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define HFX_API __attribute__((visibility("default")))
+#else
+#define HFX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status */
+#define HFX_OK 0
+#define HFX_EINVAL (-1)        /* bad size, index, pointer or option */
+#define HFX_ENOTHERM (-2)      /* v(q) not Hermitian within tolerance */
+#define HFX_ENONFINITE (-3)    /* NaN or Inf in an input */
+#define HFX_EMISSING (-4)      /* build requested before every required set_* call */
+#define HFX_EDEVICE (-5)       /* CUDA error (message in hfx_last_error) */
+#define HFX_ETIMEOUT (-6)      /* a bounded device wait expired */
+#define HFX_ENOMEM (-7)        /* host or device allocation failed */
+#define HFX_ENOTSPARSE (-8)    /* sparse mode forced but v(q) is not block-sparse */
+#define HFX_EUNSUPPORTED (-9)  /* size or option outside what this build supports */
+
+/* -------------------------------------------------------------- types */
+typedef struct hfx_ctx hfx_ctx;
+
+/* Crystal and basis description (Eq. FLAPW-basis, Sec. III.B). */
+typedef struct {
+    double lattice[9];        /* rows a_1, a_2, a_3 in bohr */
+    int n_atoms;              /* atoms (MT spheres) per cell, >= 1 */
+    const double *pos_frac;   /* [n_atoms][3] fractional positions */
+    const double *rmt;        /* [n_atoms] MT radii S_a (bohr), >= 0, non-overlapping */
+    int lmax;                 /* LAPW angular cutoff (0..8) */
+    int Lmax;                 /* MPB angular cutoff (0..8), Sec. III.B */
+    int n_rad;                /* P: MT product functions per (atom, L) after the
+                                 linear-dependence removal (1..16) */
+    int mesh[3];              /* k mesh N_1 x N_2 x N_3, each >= 1 */
+} hfx_system;
+
+enum {
+    HFX_PREC_FP64 = 0,        /* every step in FP64 on the CUDA cores (the plain FP64 GPU build) */
+    HFX_PREC_SLICED = 1       /* contractions on the tensor cores in exact fixed-point
+                                 BF16 slice arithmetic (four 8-bit slices per operand
+                                 line, exact class sums, compensated combination);
+                                 projections, transform, q->0 term and q sum in FP64 */
+};
+enum {
+    HFX_SPARSE_AUTO = 0,      /* use the block-sparse form if every v(q) has it */
+    HFX_SPARSE_ON = 1,        /* require it (HFX_ENOTSPARSE otherwise) */
+    HFX_SPARSE_OFF = 2        /* dense vector-matrix-vector products */
+};
+
+typedef struct {
+    int precision;            /* HFX_PREC_* */
+    int sparse;               /* HFX_SPARSE_* */
+    int q0_term;              /* nonzero: add Eq. (div final) to the occupied diagonal */
+    double beta;              /* Eq. (F(q)) parameter, > 0; q0 from e^{-beta q0^2} = beta */
+    double herm_tol;          /* relative Hermiticity tolerance for v(q) */
+    double sparse_tol;        /* relative size of elements treated as zero in the
+                                 transformed v(q) */
+    void *stream;             /* cudaStream_t (NULL: legacy default stream) */
+    int device;               /* CUDA device ordinal */
+    size_t work_bytes;        /* device budget for per-q working buffers (0: auto) */
+} hfx_options;
+
+/* Per-build statistics (filled if the pointer is non-NULL). */
+typedef struct {
+    double ms_total;          /* device time of the build (CUDA events) */
+    double ms_stage1;         /* projections Z (MT + interstitial) */
+    double ms_contract;       /* Coulomb apply and Z^H (vZ) */
+    double ms_finish;         /* q sum, q->0 term, E_x */
+    double useful_flops;      /* the method's flop count (Sec. III.C sparse form) */
+    int n_pairs;              /* (k, q) pairs processed */
+    int n_batches;            /* q batches */
+    int sparse_used;          /* 1 if the block-sparse form was used */
+    int n_launches;           /* kernels launched by this build */
+    double ms_zipw;           /* interstitial projection kernel (all launches) */
+    double ms_apply;          /* Coulomb apply Y = v_t Z (dense block, all launches) */
+    double ms_zhy;            /* Z^H Y contraction (all launches) */
+    double flops_apply;       /* useful flops of the dense-block apply: 8 D^2 per column */
+    double flops_zhy;         /* useful flops of Z^H Y: 8 N_aux n per column */
+    double flops_zipw;        /* useful flops of the interstitial projection */
+} hfx_stats;
+
+/* ------------------------------------------------------------ entry points */
+
+/* Fill *opt with defaults: SLICED, sparse AUTO, q0 term on, beta = 0.005
+ * (Sec. III.E), herm_tol 1e-10, sparse_tol 1e-12, NULL stream, device 0. */
+HFX_API void hfx_default_options(hfx_options *opt);
+
+/* Create a context for one spin channel.  Validates the system (sizes,
+ * finite values, non-overlapping spheres), selects the device, and builds the
+ * Gaunt table G(LM; lm; l'm') = int Y*_LM Y*_lm Y_l'm' (MT product functions,
+ * Sec. III.B) on the device.  *out receives the context (NULL on failure). */
+HFX_API int hfx_create(const hfx_system *sys, const hfx_options *opt, hfx_ctx **out);
+
+/* Radial data of one atom (Sec. III.B-C).
+ *   R  [(Lmax+1)*P][2(lmax+1)][2(lmax+1)] real: radial product integrals
+ *      int_0^S M_{aLP}(r) u_{lp}(r) u_{l'p'}(r) r^2 dr, symmetric in lp <-> l'p'
+ *      (checked, HFX_EINVAL).
+ *   mu [(Lmax+1)*P] real: multipole moments mu_{aLP} = int_0^S M_{aLP} r^{L+2} dr,
+ *      which define the unitary transform of Sec. III.C. */
+HFX_API int hfx_set_radial(hfx_ctx *ctx, int atom, const double *R, const double *mu);
+
+/* Wave functions of one k point (Eq. FLAPW-basis), uploaded to the device.
+ *   n_bands   band window n_max of Sec. III (V^x is n_bands x n_bands), >= 1
+ *   n_occ     occupied bands (f_nk = 1 for n < n_occ), 0..n_bands
+ *   npw, G    [npw][3] integer reciprocal vectors of the plane waves |k+G| <= Gmax
+ *   c         [n_bands][npw] complex: interstitial coefficients, phi = Omega^{-1/2} sum c e^{i(k+G)r}
+ *   A         [n_bands][n_atoms][N_lmp] complex: MT coefficients of phi in the home cell */
+HFX_API int hfx_set_kpoint(hfx_ctx *ctx, int ik, int n_bands, int n_occ, int npw, const int *G,
+                   const double *c, const double *A);
+
+/* Coulomb matrix of one q point (Eq. coulomb matrix), built once per SCF cycle.
+ *   n_ipw, G_aux  [n_ipw][3] integer G of the interstitial plane waves M^q_G
+ *   v             [N_aux][N_aux] complex, Hermitian (HFX_ENOTHERM beyond herm_tol),
+ *                 in the MPB order above; v(q=0) is the finite part v'(0) of
+ *                 Eq. (div + nondiv part).
+ * The library applies the multipole transform v_t = T v T^T in FP64 on the
+ * device at the next build (after every hfx_set_radial). */
+HFX_API int hfx_set_coulomb(hfx_ctx *ctx, int iq, int n_ipw, const int *G_aux, const double *v);
+
+/* Supply the projection vectors of one (k, q) pair directly instead of
+ * computing them from the wave functions (Eq. vec-mat-vec):
+ *   Z  [N_aux(q)][n_occ(k-q)][n_bands(k)] complex, MPB order above.
+ * Z == NULL removes an earlier override.  The override persists across builds. */
+HFX_API int hfx_set_products(hfx_ctx *ctx, int ik, int iq, const double *Z);
+
+/* Copy the projection vectors of one pair, as computed by the last build,
+ * into Z (layout of hfx_set_products; untransformed MPB order).  Requires a
+ * preceding build with keep_products = 1 (see hfx_build_all). */
+HFX_API int hfx_get_products(hfx_ctx *ctx, int ik, int iq, double *Z);
+
+/* Build V^x(k) for every k of the mesh and E_x, leaving them on the device.
+ * keep_products != 0 also keeps every pair's Z for hfx_get_products (memory
+ * permitting, else HFX_ENOMEM).  Requires hfx_set_radial for every atom,
+ * hfx_set_kpoint for every k and hfx_set_coulomb for every q (HFX_EMISSING). */
+HFX_API int hfx_build_all(hfx_ctx *ctx, int keep_products, hfx_stats *st);
+
+/* Build V^x for one k only (its N_k pairs) and copy it to Vx
+ * [n_bands][n_bands] complex. */
+HFX_API int hfx_build_exchange(hfx_ctx *ctx, int ik, double *Vx, hfx_stats *st);
+
+/* Copy V^x(k) of the last hfx_build_all into Vx [n_bands][n_bands] complex. */
+HFX_API int hfx_get_exchange(hfx_ctx *ctx, int ik, double *Vx);
+
+/* Device pointer of V^x(k) of the last build ([n_bands][n_bands] complex
+ * double, valid until the next build or hfx_destroy). */
+HFX_API int hfx_exchange_device_ptr(hfx_ctx *ctx, int ik, const double **Vx_dev);
+
+/* Exchange energy of one spin channel of the last build (Eq. HF exchange
+ * energy): E_x = (1/2)(1/N_k) sum_k sum_{n<n_occ(k)} Re V^x_nn(k). */
+HFX_API int hfx_get_energy(hfx_ctx *ctx, double *Ex);
+
+/* The q->0 bracket b of Eq. (div final) (FP64, computed on the device):
+ * b = (pi beta)^{-1/2} erf(sqrt(beta) q0)
+ *     - (4 pi / (N_k Omega)) sum_{q, G: 0<|q+G|<=q0} e^{-beta|q+G|^2}/|q+G|^2. */
+HFX_API int hfx_get_q0_bracket(hfx_ctx *ctx, double *b);
+
+/* Release every host and device resource of the context (NULL is a no-op). */
+HFX_API void hfx_destroy(hfx_ctx *ctx);
+
+/* Static description of a status code. */
+HFX_API const char *hfx_strerror(int code);
+
+/* Last error message of the context ("" if none). */
+HFX_API const char *hfx_last_error(const hfx_ctx *ctx);
+
+/* Library version string. */
+HFX_API const char *hfx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFX_H */

@@ -1,0 +1,846 @@
+// k_contract_tc.cu -- the contraction on the 5th-generation tensor cores
+// (tcgen05.mma kind::f16 with BF16 operands, FP32 accumulators in TMEM,
+// operands staged by TMA into 128-byte-swizzled shared memory), in
+// fixed-point slice arithmetic that makes every tensor-core sum exact.
+//
+// Slices.  Every operand line (a row of A, a column of B) shares one power of
+// two 2^e with e chosen so that the line's largest magnitude is below 2^e.  An
+// element x is cut into four 8-bit integer slices,
+//   x = 2^e (s0 2^-8 + s1 2^-16 + s2 2^-24 + s3 2^-32) + r,  |s0| <= 256, |s1..3| <= 128,
+// each stored exactly as a BF16 number.  A product of two lines is the sum of
+// the ten slice products s_i t_j with i + j <= 3, grouped by weight class
+// w = i + j (weight 2^-8(w+2)).  Every class is accumulated in its own TMEM
+// accumulator; since all summands are integers and a class sum over at most
+// 256 K elements stays below 2^24, the FP32 accumulation is exact whatever
+// the rounding mode of the tensor-core adder.  After each K group of <= 256
+// the four class sums are combined, scaled by 2^(e_A + e_B) and added into
+// compensated FP32 (hi, lo) pairs on the CUDA cores.  The result carries about
+// 2^-33 relative error per element line, far below what the exchange matrix
+// needs, with no systematic bias.
+//
+// Complex arithmetic uses the real embedding [[Re, -Im], [Im, Re]].
+//   GEMM1 (per q, all k of the batch):  Y_D = v_t[D, all] Z          (Fig. 1 dense block)
+//   GEMM2 (per pair (k,q)):             P = sum_m Z_m^H Y_m          (Eq. vec-mat-vec)
+// The q sum is then done in FP64 (k_finish.cu).
+//
+// Every wait is bounded (about two seconds); on expiry the kernel records an
+// error code, stops issuing work, lets its in-flight copies and MMAs drain
+// (again bounded), frees its TMEM and returns.
+#include <algorithm>
+#include <string>
+
+#include "hfx_internal.cuh"
+
+namespace hfx {
+
+namespace {
+
+constexpr unsigned long long kWaitNs = 2000000000ULL;  // 2 s
+
+// ------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\tselp.b32 %0, 1, 0, P1;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok;
+}
+// Bounded wait.  Returns false (and raises the CTA abort flag and the global
+// error word) if the phase did not complete in time or the CTA is aborting.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err,
+                                          int code) {
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            unsigned long long now = gtimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitNs) {
+                *abort_flag = 1;
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+// Best-effort bounded wait used only while draining after an abort.
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
+    unsigned long long t0 = gtimer();
+    while (!mbar_try(bar, parity)) {
+        if (gtimer() - t0 > kWaitNs) return;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(dst),
+        "l"((uint64_t)map), "r"(saddr(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand, 128-byte swizzle:
+// 8-row atoms of 1024 bytes (stride-byte-offset), leading offset unused.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ------------------------------------------------------------- slices
+constexpr int NPL = 4;      // slices per operand
+constexpr int NTERM = 10;   // slice products s_i t_j with i + j <= 3
+__device__ __constant__ int kSA[NTERM] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+__device__ __constant__ int kSB[NTERM] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+__device__ __constant__ int kSW[NTERM] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
+
+// exponent e with max < 2^e (0 for an all-zero line)
+__device__ __forceinline__ int line_exp(double mx) {
+    if (!(mx > 0.0)) return 0;
+    int e;
+    frexp(mx, &e);
+    return e;
+}
+
+__device__ __forceinline__ void slice4(double x, int e, __nv_bfloat16 *o /* 4 */) {
+    double u = ldexp(x, -e);
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        u *= 256.0;
+        double s = rint(u);
+        u -= s;
+        o[i] = __double2bfloat16(s);   // |s| <= 256: exact in BF16
+    }
+}
+
+// Combine the four exact class sums of one K group (units 2^(eA+eB-16)) and
+// add them, scaled by sc, into the compensated pair (hi, lo).
+__device__ __forceinline__ void class_accumulate(float a0, float a1, float a2, float a3, float sc, float &hi,
+                                                 float &lo) {
+    float c = fmaf(a3, 0x1p-8f, a2);
+    c = fmaf(c, 0x1p-8f, a1);
+    float x = a0 * sc;
+    float s = hi + x;
+    float bb = s - hi;
+    float er = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += er + c * (0x1p-8f * sc);
+}
+
+// ------------------------------------------------------------- column slicing
+// For every column of the batch: exponent over its rows (real and imaginary
+// parts of rows [0, N0) and [N0, N0 + D_q) of Zc), then slices into
+// XS[p][col][u]: u in [0, HS) real parts, [HS, 2 HS) imaginary parts (mu=0
+// rows padded to N0pad, dense rows padded to Dpad).  One warp per column.
+template <typename V>
+__global__ void slice_cols_kernel(const V *__restrict__ Z, long long RSc, const QDesc *__restrict__ qd, int N0,
+                                  int N0pad, int Dpad, int RS, long long NC, __nv_bfloat16 *__restrict__ XS,
+                                  int *__restrict__ xexp) {
+    const QDesc q = qd[blockIdx.y];
+    int HS = N0pad + Dpad;
+    int wpb = blockDim.x / 32, lane = threadIdx.x % 32;
+    long long plane = NC * RS;
+    for (long long c = (long long)blockIdx.x * wpb + threadIdx.x / 32; c < q.ncols; c += (long long)gridDim.x * wpb) {
+        long long col = q.colbase + c;
+        const V *z = Z + col * RSc;
+        int nrow = N0 + q.D;
+        double mx = 0.0;
+        for (int r = lane; r < nrow; r += 32) {
+            V v = z[r];
+            mx = fmax(mx, fmax(fabs((double)v.x), fabs((double)v.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int e = line_exp(mx);
+        if (lane == 0) xexp[col] = e;
+        size_t base = (size_t)col * RS;
+        for (int u = lane; u < HS; u += 32) {
+            int row = -1;
+            if (u < N0pad) row = (u < N0) ? u : -1;
+            else if (u - N0pad < q.D) row = N0 + (u - N0pad);
+            double xr = 0.0, xi = 0.0;
+            if (row >= 0) {
+                V v = z[row];
+                xr = (double)v.x;
+                xi = (double)v.y;
+            }
+            __nv_bfloat16 sr[NPL], si[NPL];
+            slice4(xr, e, sr);
+            slice4(xi, e, si);
+#pragma unroll
+            for (int p = 0; p < NPL; ++p) {
+                XS[p * plane + base + u] = sr[p];
+                XS[p * plane + base + HS + u] = si[p];
+            }
+        }
+    }
+}
+
+// Y rows of the mu=0 functions (on-site blocks of Fig. 1), FP64.
+template <typename V>
+__global__ void block_y_kernel(const QDesc *__restrict__ qd, const double2 *const *__restrict__ VB,
+                               const V *__restrict__ Z, double2 *__restrict__ Y, long long RSc, int P, int N0) {
+    const QDesc q = qd[blockIdx.y];
+    const double2 *vb = VB[blockIdx.y];
+    long long total = q.ncols * N0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int u = (int)(e % N0);
+        long long col = q.colbase + e / N0;
+        int ch = u / (P - 1), i = u % (P - 1);
+        const V *z = Z + col * RSc;
+        const double2 *row = vb + ((size_t)ch * (P - 1) + i) * P;
+        V z0 = z[N0 + ch];
+        double2 acc = cmul(row[0], make_double2((double)z0.x, (double)z0.y));
+        for (int s = 1; s < P; ++s) {
+            V zs = z[ch * (P - 1) + s - 1];
+            acc = cfma(row[s], make_double2((double)zs.x, (double)zs.y), acc);
+        }
+        Y[col * RSc + u] = acc;
+    }
+}
+
+// ------------------------------------------------------------- GEMM1
+// Tile: 128 rows of A' (one q) x 64 columns of Z; K chunks of 64 (one
+// 128-byte swizzled row per operand row), the four slices of both operands
+// per stage; four class accumulators, double-buffered in TMEM.
+struct G1Tile { int qslot, mrow, ncol0, klen; };
+
+struct G1Params {
+    const G1Tile *tiles;
+    int ntiles;
+    const QDesc *qd;
+    const int *aexp;       // per A' row: [nk][MP]
+    const int *zexp;       // per column of the batch
+    double2 *Y;            // [col][RSc] (rows N0 + r)
+    long long RSc;
+    long long NC;          // columns of the batch (plane stride in rows of ZS)
+    int RS, HS, MP, N0pad, Dpad, N0;
+    int *err;
+};
+
+constexpr int G1_BM = 128, G1_BN = 64, G1_KC = 64;
+constexpr int G1_A_PLANE = G1_BM * G1_KC * 2;              // 16 KB
+constexpr int G1_B_PLANE = G1_BN * G1_KC * 2;              // 8 KB
+constexpr int G1_STAGE = NPL * (G1_A_PLANE + G1_B_PLANE);   // 96 KB
+constexpr int G1_STAGES = 2;
+constexpr int G1_GROUP = 4;                                // chunks per exact K group (256)
+constexpr int G1_TMEM = 512;                               // 2 buffers x 4 classes x 64 columns
+constexpr int G1_EPI = 8;                                  // epilogue warps
+
+// warp 0: TMA producer; warp 1: MMA issuer; warps 2..9: epilogue
+// (lane quarter = w % 4, column half = (w - 2) / 4)
+__global__ void __launch_bounds__(64 + 32 * G1_EPI, 1) gemm1_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                    const __grid_constant__ CUtensorMap tmB,
+                                                                    G1Params p) {
+    extern __shared__ __align__(1024) unsigned char g1_smem[];
+    uintptr_t base = (reinterpret_cast<uintptr_t>(g1_smem) + 1023) & ~(uintptr_t)1023;
+    unsigned char *stages = reinterpret_cast<unsigned char *>(base);
+    __shared__ uint64_t full_bar[G1_STAGES], empty_bar[G1_STAGES], tfull_bar[2], tempty_bar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G1_STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull_bar[b], 1);
+            mbar_init(&tempty_bar[b], G1_EPI);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&tmem_slot, G1_TMEM);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;
+            for (int t = blockIdx.x; t < p.ntiles && !abort_flag; t += gridDim.x) {
+                G1Tile tl = p.tiles[t];
+                int qi = p.qd[tl.qslot].iq;
+                int nk = tl.klen / G1_KC;
+                bool stop = false;
+                for (int kc = 0; kc < 2 * nk; ++kc) {
+                    if (!mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma)) { stop = true; break; }
+                    int x = (kc < nk) ? kc * G1_KC : p.HS + (kc - nk) * G1_KC;
+                    unsigned char *st = stages + (size_t)s * G1_STAGE;
+                    mbar_expect_tx(&full_bar[s], G1_STAGE);
+                    for (int pl = 0; pl < NPL; ++pl) {
+                        tma_load_2d(saddr(st + pl * G1_A_PLANE), &tmA, &full_bar[s], x, (qi * NPL + pl) * p.MP + tl.mrow);
+                        tma_load_2d(saddr(st + NPL * G1_A_PLANE + pl * G1_B_PLANE), &tmB, &full_bar[s], x,
+                                    (int)(pl * p.NC + tl.ncol0));
+                    }
+                    ++issued;
+                    if (++s == G1_STAGES) { s = 0; ph ^= 1; }
+                }
+                if (stop) break;
+            }
+            if (abort_flag) {
+                for (int i = 0; i < G1_STAGES && i < issued; ++i) mbar_drain(&full_bar[i], 0), mbar_drain(&full_bar[i], 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int buf = 0;
+            uint32_t buf_ph[2] = {0, 0};
+            constexpr uint32_t idesc = idesc_bf16(G1_BM, G1_BN);
+            bool ok = true;
+            for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+                G1Tile tl = p.tiles[t];
+                int nchunk = 2 * (tl.klen / G1_KC);
+                for (int g0 = 0; g0 < nchunk && ok; g0 += G1_GROUP) {
+                    if (!mbar_wait(&tempty_bar[buf], buf_ph[buf] ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
+                    tc_fence_after();
+                    uint32_t dt = tmem + buf * (NPL * G1_BN);
+                    int started = 0;   // bit w: class w written in this group
+                    for (int kc = g0; kc < min(nchunk, g0 + G1_GROUP); ++kc) {
+                        if (!mbar_wait(&full_bar[s], ph, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
+                        tc_fence_after();
+                        unsigned char *st = stages + (size_t)s * G1_STAGE;
+                        uint32_t a0 = saddr(st), b0 = saddr(st + NPL * G1_A_PLANE);
+                        for (int tm = 0; tm < NTERM; ++tm) {
+                            int w = kSW[tm];
+                            uint64_t da = desc_sw128(a0 + kSA[tm] * G1_A_PLANE);
+                            uint64_t db = desc_sw128(b0 + kSB[tm] * G1_B_PLANE);
+#pragma unroll
+                            for (int ks = 0; ks < G1_KC / 16; ++ks) {
+                                umma_bf16(dt + w * G1_BN, da + 2 * ks, db + 2 * ks, idesc, ((started >> w) & 1) ? 1u : 0u);
+                                started |= 1 << w;
+                            }
+                        }
+                        umma_commit(&empty_bar[s]);
+                        if (++s == G1_STAGES) { s = 0; ph ^= 1; }
+                    }
+                    if (!ok) break;
+                    umma_commit(&tfull_bar[buf]);
+                    buf_ph[buf] ^= 1;
+                    buf ^= 1;
+                }
+            }
+        }
+    } else {
+        int e = warp - 2;
+        int quarter = warp % 4, half = e / 4;
+        int buf = 0;
+        uint32_t buf_ph[2] = {0, 0};
+        bool ok = true;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+            G1Tile tl = p.tiles[t];
+            const QDesc q = p.qd[tl.qslot];
+            int nchunk = 2 * (tl.klen / G1_KC);
+            int ngroups = (nchunk + G1_GROUP - 1) / G1_GROUP;
+            float hi[32], lo[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int g = 0; g < ngroups; ++g) {
+                if (!mbar_wait(&tfull_bar[buf], buf_ph[buf], &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
+                tc_fence_after();
+                uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (NPL * G1_BN) + half * 32;
+#pragma unroll
+                for (int c0 = 0; c0 < 32; c0 += 16) {
+                    uint32_t a0[16], a1[16], a2[16], a3[16];
+                    tmem_ld16(tb + 0 * G1_BN + c0, a0);
+                    tmem_ld16(tb + 1 * G1_BN + c0, a1);
+                    tmem_ld16(tb + 2 * G1_BN + c0, a2);
+                    tmem_ld16(tb + 3 * G1_BN + c0, a3);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        class_accumulate(__uint_as_float(a0[j]), __uint_as_float(a1[j]), __uint_as_float(a2[j]),
+                                         __uint_as_float(a3[j]), 1.0f, hi[c0 + j], lo[c0 + j]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty_bar[buf]);
+                buf_ph[buf] ^= 1;
+                buf ^= 1;
+            }
+            if (!ok) break;
+            int r = tl.mrow + quarter * 32 + lane;           // row of A' in this q
+            bool im = r >= p.Dpad;
+            int rr = im ? r - p.Dpad : r;
+            if (rr < q.D) {
+                int ea = p.aexp[(size_t)q.iq * p.MP + r];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    long long col = tl.ncol0 + half * 32 + j;
+                    if (col < q.colbase + q.ncols) {
+                        double v = ldexp((double)hi[j] + (double)lo[j], ea + p.zexp[col] - 16);
+                        double *dst = reinterpret_cast<double *>(p.Y + col * p.RSc + p.N0 + rr);
+                        dst[im ? 1 : 0] = v;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, G1_TMEM);
+    }
+}
+
+// ------------------------------------------------------------- GEMM2
+struct G2Tile { int pair, bi, bj, pad; };
+
+struct G2Params {
+    const G2Tile *tiles;
+    int ntiles;
+    const PairDesc *pairs;
+    const QDesc *qd;
+    const long long *praw_off;   // per pair, in doubles
+    double *praw;
+    const int *zexp, *yexp;      // per column of the batch
+    long long NC;
+    int HS, N0pad, nstages, stage_bytes;
+    int *err;
+};
+
+constexpr int G2_A_PLANE = 128 * 64 * 2;    // 16 KB: rows [0,NB) Re, [NB,2NB) Im, rest zero
+constexpr int G2_GROUP = 4;                 // chunks per exact K group (256)
+constexpr int G2_EPI_WARPS = 8;
+constexpr int G2_MAX_STAGES = 4;
+
+// number of 64-row K chunks of a pair: mu=0 rows plus the dense rows of its q
+__device__ __forceinline__ int g2_chunks(const QDesc &q, int N0pad) { return (N0pad + q.D + 63) / 64; }
+
+// warp 0: TMA; warp 1: MMA; warps 2..9: epilogue (lane quarter = w%4,
+// column half = (w-2)/4 of the 2NB accumulator columns).  Four class
+// accumulators of 2NB columns each, single-buffered.
+template <int NB>
+__global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const __grid_constant__ CUtensorMap tmZ,
+                                                                          const __grid_constant__ CUtensorMap tmY,
+                                                                          G2Params p) {
+    constexpr int W = 2 * NB, CW = W / 2;   // accumulator columns; per thread
+    constexpr int B_PLANE = W * 128;
+    extern __shared__ __align__(1024) unsigned char g2_smem[];
+    uintptr_t base = (reinterpret_cast<uintptr_t>(g2_smem) + 1023) & ~(uintptr_t)1023;
+    unsigned char *stages = reinterpret_cast<unsigned char *>(base);
+    __shared__ uint64_t full_bar[G2_MAX_STAGES], empty_bar[G2_MAX_STAGES], tfull_bar, tempty_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int NS = p.nstages, SB = p.stage_bytes;
+    for (int s = 0; s < NS; ++s)
+        for (int pl = 0; pl < NPL; ++pl) {
+            uint4 *a = reinterpret_cast<uint4 *>(stages + (size_t)s * SB + pl * G2_A_PLANE);
+            for (int i = threadIdx.x; i < G2_A_PLANE / 16; i += blockDim.x) a[i] = make_uint4(0, 0, 0, 0);
+        }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&tfull_bar, 1);
+        mbar_init(&tempty_bar, G2_EPI_WARPS);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 1) tmem_alloc(&tmem_slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    uint32_t tmem = tmem_slot;
+    constexpr uint32_t box_bytes = 64u * NB * 2u;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;
+            for (int t = blockIdx.x; t < p.ntiles && !abort_flag; t += gridDim.x) {
+                G2Tile tl = p.tiles[t];
+                const PairDesc pr = p.pairs[tl.pair];
+                const QDesc q = p.qd[pr.qslot];
+                int nc = g2_chunks(q, p.N0pad);
+                bool stop = false;
+                for (int m = 0; m < pr.no && !stop; ++m) {
+                    long long ya = pr.col0 + (long long)m * pr.nb + tl.bi * NB;
+                    long long yb = pr.col0 + (long long)m * pr.nb + tl.bj * NB;
+                    for (int c = 0; c < nc; ++c) {
+                        if (!mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma)) { stop = true; break; }
+                        unsigned char *st = stages + (size_t)s * SB;
+                        mbar_expect_tx(&full_bar[s], 4u * NPL * box_bytes);
+                        for (int pl = 0; pl < NPL; ++pl) {
+                            unsigned char *a = st + pl * G2_A_PLANE;
+                            unsigned char *b = st + NPL * G2_A_PLANE + pl * B_PLANE;
+                            int ra = (int)(pl * p.NC + ya), rb = (int)(pl * p.NC + yb);
+                            tma_load_2d(saddr(a), &tmZ, &full_bar[s], c * 64, ra);
+                            tma_load_2d(saddr(a + NB * 128), &tmZ, &full_bar[s], p.HS + c * 64, ra);
+                            tma_load_2d(saddr(b), &tmY, &full_bar[s], c * 64, rb);
+                            tma_load_2d(saddr(b + NB * 128), &tmY, &full_bar[s], p.HS + c * 64, rb);
+                        }
+                        ++issued;
+                        if (++s == NS) { s = 0; ph ^= 1; }
+                    }
+                }
+                if (stop) break;
+            }
+            if (abort_flag) {
+                for (int i = 0; i < NS && i < issued; ++i) mbar_drain(&full_bar[i], 0), mbar_drain(&full_bar[i], 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t tph = 0;
+            constexpr uint32_t idesc = idesc_bf16(128, W);
+            bool ok = true;
+            for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+                G2Tile tl = p.tiles[t];
+                const PairDesc pr = p.pairs[tl.pair];
+                const QDesc q = p.qd[pr.qslot];
+                int nc = g2_chunks(q, p.N0pad);
+                for (int m = 0; m < pr.no && ok; ++m) {
+                    for (int g0 = 0; g0 < nc && ok; g0 += G2_GROUP) {
+                        if (!mbar_wait(&tempty_bar, tph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
+                        tc_fence_after();
+                        int started = 0;
+                        for (int c = g0; c < min(nc, g0 + G2_GROUP); ++c) {
+                            if (!mbar_wait(&full_bar[s], ph, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
+                            tc_fence_after();
+                            unsigned char *st = stages + (size_t)s * SB;
+                            uint32_t a0 = saddr(st), b0 = saddr(st + NPL * G2_A_PLANE);
+                            for (int tm = 0; tm < NTERM; ++tm) {
+                                int w = kSW[tm];
+                                uint64_t da = desc_sw128(a0 + kSA[tm] * G2_A_PLANE);
+                                uint64_t db = desc_sw128(b0 + kSB[tm] * B_PLANE);
+#pragma unroll
+                                for (int ks = 0; ks < 4; ++ks) {
+                                    umma_bf16(tmem + w * W, da + 2 * ks, db + 2 * ks, idesc, ((started >> w) & 1) ? 1u : 0u);
+                                    started |= 1 << w;
+                                }
+                            }
+                            umma_commit(&empty_bar[s]);
+                            if (++s == NS) { s = 0; ph ^= 1; }
+                        }
+                        if (!ok) break;
+                        umma_commit(&tfull_bar);
+                        tph ^= 1;
+                    }
+                }
+            }
+        }
+    } else {
+        int e = warp - 2;
+        int quarter = warp % 4, cg = e / 4;
+        uint32_t tph = 0;
+        bool ok = true;
+        int row = quarter * 32 + lane;            // accumulator row: Re (< NB) or Im part of band bi*NB + row % NB
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+            G2Tile tl = p.tiles[t];
+            const PairDesc pr = p.pairs[tl.pair];
+            const QDesc q = p.qd[pr.qslot];
+            int nc = g2_chunks(q, p.N0pad);
+            float hi[CW], lo[CW];
+#pragma unroll
+            for (int j = 0; j < CW; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int m = 0; m < pr.no && ok; ++m) {
+                long long cola = pr.col0 + (long long)m * pr.nb + tl.bi * NB + (row % NB);
+                long long colb0 = pr.col0 + (long long)m * pr.nb + tl.bj * NB;
+                int ea = p.zexp[min(cola, p.NC - 1)] - 16;
+                for (int g0 = 0; g0 < nc; g0 += G2_GROUP) {
+                    if (!mbar_wait(&tfull_bar, tph, &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
+                    tc_fence_after();
+                    uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + cg * CW;
+#pragma unroll
+                    for (int c0 = 0; c0 < CW; c0 += 8) {
+                        uint32_t x[8], y[8];
+                        float c[8];
+                        // classes 3 and 2, then 1, then the exact class 0
+                        tmem_ld8(tb + 3 * W + c0, x);
+                        tmem_ld8(tb + 2 * W + c0, y);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) c[j] = fmaf(__uint_as_float(x[j]), 0x1p-8f, __uint_as_float(y[j]));
+                        tmem_ld8(tb + 1 * W + c0, x);
+                        tmem_ld8(tb + 0 * W + c0, y);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            int b = cg * CW + c0 + j;
+                            float sc = ldexpf(1.0f, ea + p.yexp[min(colb0 + (b % NB), p.NC - 1)]);
+                            float cc = fmaf(c[j], 0x1p-8f, __uint_as_float(x[j]));
+                            float xv = __uint_as_float(y[j]) * sc;
+                            float s2 = hi[c0 + j] + xv;
+                            float bb = s2 - hi[c0 + j];
+                            float er = (hi[c0 + j] - (s2 - bb)) + (xv - bb);
+                            hi[c0 + j] = s2;
+                            lo[c0 + j] += er + cc * (0x1p-8f * sc);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty_bar);
+                    tph ^= 1;
+                }
+            }
+            if (!ok) break;
+            if (row < W) {
+                int nblk = (pr.nb + NB - 1) / NB;
+                double *out = p.praw + p.praw_off[tl.pair] + ((size_t)tl.bi * nblk + tl.bj) * W * W + (size_t)row * W +
+                              cg * CW;
+#pragma unroll
+                for (int j = 0; j < CW; ++j) out[j] = (double)hi[j] + (double)lo[j];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult qr;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor [rows][cols] (cols contiguous), box {64, box_rows}, 128-byte swizzle
+int make_map(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_err(ctx, HFX_EDEVICE, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_err(ctx, HFX_EDEVICE, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return HFX_OK;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace
+
+template <typename V>
+void launch_slice_cols(const V *d_Z, long long RSc, const QDesc *d_q, int nq, long long NC, long long maxcols, int N0,
+                       int N0pad, int Dpad, int RS, __nv_bfloat16 *d_XS, int *d_exp, cudaStream_t st) {
+    long long g = (maxcols + 7) / 8;
+    if (g > 8192) g = 8192;
+    if (g < 1) g = 1;
+    dim3 grid((unsigned)g, (unsigned)nq);
+    slice_cols_kernel<V><<<grid, 256, 0, st>>>(d_Z, RSc, d_q, N0, N0pad, Dpad, RS, NC, d_XS, d_exp);
+}
+template void launch_slice_cols<float2>(const float2 *, long long, const QDesc *, int, long long, long long, int, int,
+                                        int, int, __nv_bfloat16 *, int *, cudaStream_t);
+template void launch_slice_cols<double2>(const double2 *, long long, const QDesc *, int, long long, long long, int, int,
+                                         int, int, __nv_bfloat16 *, int *, cudaStream_t);
+
+template <typename V>
+void launch_block_y(const QDesc *d_q, int nq, const double2 *const *d_VB, const V *d_Z, double2 *d_Y, long long RSc,
+                    int P, int N0, long long maxcols, cudaStream_t st) {
+    if (N0 == 0 || nq == 0) return;
+    long long per = maxcols * N0;
+    long long g = (per + 255) / 256;
+    if (g > 8192) g = 8192;
+    dim3 grid((unsigned)g, (unsigned)nq);
+    block_y_kernel<V><<<grid, 256, 0, st>>>(d_q, d_VB, d_Z, d_Y, RSc, P, N0);
+}
+template void launch_block_y<float2>(const QDesc *, int, const double2 *const *, const float2 *, double2 *, long long,
+                                     int, int, long long, cudaStream_t);
+template void launch_block_y<double2>(const QDesc *, int, const double2 *const *, const double2 *, double2 *, long long,
+                                      int, int, long long, cudaStream_t);
+
+int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *h_q,
+                    const QDesc *d_q, int nq, const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc,
+                    long long NC, int N0, int N0pad, int Dpad, int RS, void *d_tiles_buf, size_t tiles_cap) {
+    int HS = N0pad + Dpad, MP = 2 * Dpad;
+    std::vector<G1Tile> tiles;
+    for (int s = 0; s < nq; ++s) {
+        const QDesc &q = h_q[s];
+        int klen = ((N0pad + q.D + G1_KC - 1) / G1_KC) * G1_KC;
+        int mt = (q.D + G1_BM - 1) / G1_BM;   // tiles per half that touch real rows
+        for (long long n0 = 0; n0 < q.ncols; n0 += G1_BN)
+            for (int half = 0; half < 2; ++half)
+                for (int i = 0; i < mt; ++i) tiles.push_back(G1Tile{s, half * Dpad + i * G1_BM, (int)(q.colbase + n0), klen});
+    }
+    if (tiles.empty()) return HFX_OK;
+    if (tiles.size() * sizeof(G1Tile) > tiles_cap) return set_err(ctx, HFX_ENOMEM, "gemm1 tile table too large");
+    if (NC > 0x7fffffffLL / 4) return set_err(ctx, HFX_EUNSUPPORTED, "batch has too many columns for 32-bit TMA coordinates");
+    int rc = cuda_check(ctx, cudaMemcpyAsync(d_tiles_buf, tiles.data(), tiles.size() * sizeof(G1Tile),
+                                             cudaMemcpyHostToDevice, ctx->stream), "gemm1 tiles");
+    if (rc) return rc;
+    CUtensorMap mA, mB;
+    if ((rc = make_map(ctx, &mA, d_Ap_all, ap_rows, RS, G1_BM))) return rc;
+    if ((rc = make_map(ctx, &mB, d_ZS, (long long)NPL * NC, RS, G1_BN))) return rc;
+    G1Params p;
+    p.tiles = reinterpret_cast<const G1Tile *>(d_tiles_buf);
+    p.ntiles = (int)tiles.size();
+    p.qd = d_q;
+    p.aexp = d_aexp;
+    p.zexp = d_zexp;
+    p.Y = d_Y;
+    p.RSc = RSc;
+    p.N0 = N0;
+    p.NC = NC;
+    p.RS = RS;
+    p.HS = HS;
+    p.MP = MP;
+    p.N0pad = N0pad;
+    p.Dpad = Dpad;
+    p.err = ctx->d_err;
+    size_t smem = (size_t)G1_STAGES * G1_STAGE + 1024;
+    cudaFuncSetAttribute(gemm1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = std::min<int>(num_sms(), p.ntiles);
+    gemm1_kernel<<<grid, 64 + 32 * G1_EPI, smem, ctx->stream>>>(mA, mB, p);
+    return cuda_check(ctx, cudaGetLastError(), "gemm1 launch");
+}
+
+int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16 *d_YS, const int *d_zexp,
+                    const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *h_pairs,
+                    const PairDesc *d_pairs, int npairs, const QDesc *d_q, int NB, const long long *d_praw_off,
+                    double *d_praw, void *d_tiles_buf, size_t tiles_cap) {
+    if (NB % 16 != 0 || NB < 16 || NB > 64) return set_err(ctx, HFX_EINVAL, "gemm2: band tile must be 16, 32, 48 or 64");
+    std::vector<G2Tile> tiles;
+    for (int i = 0; i < npairs; ++i) {
+        int nblk = (h_pairs[i].nb + NB - 1) / NB;
+        if (h_pairs[i].no == 0) continue;
+        for (int bi = 0; bi < nblk; ++bi)
+            for (int bj = 0; bj < nblk; ++bj) tiles.push_back(G2Tile{i, bi, bj, 0});
+    }
+    if (tiles.empty()) return HFX_OK;
+    if (tiles.size() * sizeof(G2Tile) > tiles_cap) return set_err(ctx, HFX_ENOMEM, "gemm2 tile table too large");
+    if (NC > 0x7fffffffLL / 4) return set_err(ctx, HFX_EUNSUPPORTED, "batch has too many columns for 32-bit TMA coordinates");
+    int rc = cuda_check(ctx, cudaMemcpyAsync(d_tiles_buf, tiles.data(), tiles.size() * sizeof(G2Tile),
+                                             cudaMemcpyHostToDevice, ctx->stream), "gemm2 tiles");
+    if (rc) return rc;
+    CUtensorMap mZ, mY;
+    if ((rc = make_map(ctx, &mZ, d_ZS, (long long)NPL * NC, RS, NB))) return rc;
+    if ((rc = make_map(ctx, &mY, d_YS, (long long)NPL * NC, RS, NB))) return rc;
+    G2Params p;
+    p.tiles = reinterpret_cast<const G2Tile *>(d_tiles_buf);
+    p.ntiles = (int)tiles.size();
+    p.pairs = d_pairs;
+    p.qd = d_q;
+    p.praw_off = d_praw_off;
+    p.praw = d_praw;
+    p.zexp = d_zexp;
+    p.yexp = d_yexp;
+    p.NC = NC;
+    p.HS = HS;
+    p.N0pad = N0pad;
+    p.err = ctx->d_err;
+    p.stage_bytes = NPL * (G2_A_PLANE + 2 * NB * 128);
+    p.nstages = std::min(G2_MAX_STAGES, (int)((226 * 1024) / p.stage_bytes));
+    if (p.nstages < 1) return set_err(ctx, HFX_EUNSUPPORTED, "gemm2 stage does not fit in shared memory");
+    size_t smem = (size_t)p.nstages * p.stage_bytes + 1024;
+    int grid = std::min<int>(num_sms(), p.ntiles);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, 64 + 32 * G2_EPI_WARPS, smem, ctx->stream>>>(mZ, mY, p);
+    };
+    switch (NB) {
+    case 16: go(gemm2_kernel<16>); break;
+    case 32: go(gemm2_kernel<32>); break;
+    case 48: go(gemm2_kernel<48>); break;
+    default: go(gemm2_kernel<64>); break;
+    }
+    return cuda_check(ctx, cudaGetLastError(), "gemm2 launch");
+}
+
+}  // namespace hfx

@@ -1,0 +1,343 @@
+"""Thin ctypes binding of libhfx.so (include/hfx.h), same entry-point names.
+
+Argument marshalling only: every step of the exchange-matrix build runs in the
+CUDA library.  There is no CPU fallback: if the library is missing or cannot
+be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+HFX_OK = 0
+HFX_EINVAL = -1
+HFX_ENOTHERM = -2
+HFX_ENONFINITE = -3
+HFX_EMISSING = -4
+HFX_EDEVICE = -5
+HFX_ETIMEOUT = -6
+HFX_ENOMEM = -7
+HFX_ENOTSPARSE = -8
+HFX_EUNSUPPORTED = -9
+
+HFX_PREC_FP64 = 0
+HFX_PREC_SLICED = 1
+HFX_SPARSE_AUTO, HFX_SPARSE_ON, HFX_SPARSE_OFF = 0, 1, 2
+
+EXPORTS = (
+    "hfx_default_options", "hfx_create", "hfx_set_radial", "hfx_set_kpoint", "hfx_set_coulomb",
+    "hfx_set_products", "hfx_get_products", "hfx_build_all", "hfx_build_exchange", "hfx_get_exchange",
+    "hfx_exchange_device_ptr", "hfx_get_energy", "hfx_get_q0_bracket", "hfx_destroy", "hfx_strerror",
+    "hfx_last_error", "hfx_version",
+)
+
+
+class HfxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class hfx_system(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_double * 9),
+        ("n_atoms", ctypes.c_int),
+        ("pos_frac", ctypes.c_void_p),
+        ("rmt", ctypes.c_void_p),
+        ("lmax", ctypes.c_int),
+        ("Lmax", ctypes.c_int),
+        ("n_rad", ctypes.c_int),
+        ("mesh", ctypes.c_int * 3),
+    ]
+
+
+class hfx_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("sparse", ctypes.c_int),
+        ("q0_term", ctypes.c_int),
+        ("beta", ctypes.c_double),
+        ("herm_tol", ctypes.c_double),
+        ("sparse_tol", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("device", ctypes.c_int),
+        ("work_bytes", ctypes.c_size_t),
+    ]
+
+
+class hfx_stats(ctypes.Structure):
+    _fields_ = [
+        ("ms_total", ctypes.c_double),
+        ("ms_stage1", ctypes.c_double),
+        ("ms_contract", ctypes.c_double),
+        ("ms_finish", ctypes.c_double),
+        ("useful_flops", ctypes.c_double),
+        ("n_pairs", ctypes.c_int),
+        ("n_batches", ctypes.c_int),
+        ("sparse_used", ctypes.c_int),
+        ("n_launches", ctypes.c_int),
+        ("ms_zipw", ctypes.c_double),
+        ("ms_apply", ctypes.c_double),
+        ("ms_zhy", ctypes.c_double),
+        ("flops_apply", ctypes.c_double),
+        ("flops_zhy", ctypes.c_double),
+        ("flops_zipw", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libhfx.so; raise if it is absent (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    L.hfx_default_options.restype = None
+    L.hfx_default_options.argtypes = [P(hfx_options)]
+    L.hfx_create.restype = ip
+    L.hfx_create.argtypes = [P(hfx_system), P(hfx_options), P(vp)]
+    L.hfx_set_radial.restype = ip
+    L.hfx_set_radial.argtypes = [vp, ip, vp, vp]
+    L.hfx_set_kpoint.restype = ip
+    L.hfx_set_kpoint.argtypes = [vp, ip, ip, ip, ip, vp, vp, vp]
+    L.hfx_set_coulomb.restype = ip
+    L.hfx_set_coulomb.argtypes = [vp, ip, ip, vp, vp]
+    L.hfx_set_products.restype = ip
+    L.hfx_set_products.argtypes = [vp, ip, ip, vp]
+    L.hfx_get_products.restype = ip
+    L.hfx_get_products.argtypes = [vp, ip, ip, vp]
+    L.hfx_build_all.restype = ip
+    L.hfx_build_all.argtypes = [vp, ip, P(hfx_stats)]
+    L.hfx_build_exchange.restype = ip
+    L.hfx_build_exchange.argtypes = [vp, ip, vp, P(hfx_stats)]
+    L.hfx_get_exchange.restype = ip
+    L.hfx_get_exchange.argtypes = [vp, ip, vp]
+    L.hfx_exchange_device_ptr.restype = ip
+    L.hfx_exchange_device_ptr.argtypes = [vp, ip, P(vp)]
+    L.hfx_get_energy.restype = ip
+    L.hfx_get_energy.argtypes = [vp, P(dp)]
+    L.hfx_get_q0_bracket.restype = ip
+    L.hfx_get_q0_bracket.argtypes = [vp, P(dp)]
+    L.hfx_destroy.restype = None
+    L.hfx_destroy.argtypes = [vp]
+    L.hfx_strerror.restype = ctypes.c_char_p
+    L.hfx_strerror.argtypes = [ip]
+    L.hfx_last_error.restype = ctypes.c_char_p
+    L.hfx_last_error.argtypes = [vp]
+    L.hfx_version.restype = ctypes.c_char_p
+    L.hfx_version.argtypes = []
+    _lib = L
+    return L
+
+
+def _c(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _check(ctx, code: int):
+    if code != HFX_OK:
+        L = load()
+        msg = L.hfx_last_error(ctx).decode() if ctx else ""
+        raise HfxError(code, f"{L.hfx_strerror(code).decode()}: {msg}")
+
+
+# ----------------------------------------------------------- same-name wrappers
+
+def hfx_default_options() -> hfx_options:
+    o = hfx_options()
+    load().hfx_default_options(ctypes.byref(o))
+    return o
+
+
+def hfx_create(lattice, pos_frac, rmt, lmax, Lmax, n_rad, mesh, opt: Optional[hfx_options] = None):
+    L = load()
+    pos = _c(pos_frac, np.float64)
+    rm = _c(rmt, np.float64)
+    s = hfx_system()
+    s.lattice[:] = [float(x) for x in np.asarray(lattice, dtype=np.float64).ravel()]
+    s.n_atoms = int(pos.shape[0])
+    s.pos_frac = pos.ctypes.data
+    s.rmt = rm.ctypes.data
+    s.lmax, s.Lmax, s.n_rad = int(lmax), int(Lmax), int(n_rad)
+    s.mesh[:] = [int(x) for x in mesh]
+    if opt is None:
+        opt = hfx_default_options()
+    h = ctypes.c_void_p()
+    code = L.hfx_create(ctypes.byref(s), ctypes.byref(opt), ctypes.byref(h))
+    if code != HFX_OK:
+        raise HfxError(code, L.hfx_strerror(code).decode())
+    return h
+
+
+def hfx_set_radial(ctx, atom: int, R, mu):
+    R = _c(R, np.float64)
+    mu = _c(mu, np.float64)
+    _check(ctx, load().hfx_set_radial(ctx, int(atom), R.ctypes.data, mu.ctypes.data))
+
+
+def hfx_set_kpoint(ctx, ik: int, n_bands: int, n_occ: int, G, c, A):
+    G = _c(G, np.int32)
+    c = _c(c, np.complex128)
+    A = _c(A, np.complex128)
+    _check(ctx, load().hfx_set_kpoint(ctx, int(ik), int(n_bands), int(n_occ), int(G.shape[0]), G.ctypes.data,
+                                      c.ctypes.data, A.ctypes.data))
+
+
+def hfx_set_coulomb(ctx, iq: int, G_aux, v):
+    G = _c(G_aux, np.int32).reshape(-1, 3)
+    v = _c(v, np.complex128)
+    _check(ctx, load().hfx_set_coulomb(ctx, int(iq), int(G.shape[0]), G.ctypes.data if G.size else None,
+                                       v.ctypes.data))
+
+
+def hfx_set_products(ctx, ik: int, iq: int, Z):
+    if Z is None:
+        _check(ctx, load().hfx_set_products(ctx, int(ik), int(iq), None))
+        return
+    Z = _c(Z, np.complex128)
+    _check(ctx, load().hfx_set_products(ctx, int(ik), int(iq), Z.ctypes.data))
+
+
+def hfx_get_products(ctx, ik: int, iq: int, shape) -> np.ndarray:
+    out = np.zeros(shape, np.complex128)
+    _check(ctx, load().hfx_get_products(ctx, int(ik), int(iq), out.ctypes.data))
+    return out
+
+
+def hfx_build_all(ctx, keep_products: bool = False) -> dict:
+    st = hfx_stats()
+    _check(ctx, load().hfx_build_all(ctx, int(bool(keep_products)), ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in hfx_stats._fields_}
+
+
+def hfx_build_exchange(ctx, ik: int, n_bands: int) -> np.ndarray:
+    out = np.zeros((n_bands, n_bands), np.complex128)
+    st = hfx_stats()
+    _check(ctx, load().hfx_build_exchange(ctx, int(ik), out.ctypes.data, ctypes.byref(st)))
+    return out
+
+
+def hfx_get_exchange(ctx, ik: int, n_bands: int) -> np.ndarray:
+    out = np.zeros((n_bands, n_bands), np.complex128)
+    _check(ctx, load().hfx_get_exchange(ctx, int(ik), out.ctypes.data))
+    return out
+
+
+def hfx_exchange_device_ptr(ctx, ik: int) -> int:
+    p = ctypes.c_void_p()
+    _check(ctx, load().hfx_exchange_device_ptr(ctx, int(ik), ctypes.byref(p)))
+    return int(p.value)
+
+
+def hfx_get_energy(ctx) -> float:
+    e = ctypes.c_double()
+    _check(ctx, load().hfx_get_energy(ctx, ctypes.byref(e)))
+    return float(e.value)
+
+
+def hfx_get_q0_bracket(ctx) -> float:
+    b = ctypes.c_double()
+    _check(ctx, load().hfx_get_q0_bracket(ctx, ctypes.byref(b)))
+    return float(b.value)
+
+
+def hfx_destroy(ctx):
+    if ctx:
+        load().hfx_destroy(ctx)
+
+
+def hfx_version() -> str:
+    return load().hfx_version().decode()
+
+
+# ----------------------------------------------------------- convenience class
+
+class Context:
+    """One exchange-matrix context bound to a system from ``synthetic``."""
+
+    def __init__(self, sysm, precision: str = "sliced", sparse: str = "auto", q0_term: bool = True,
+                 beta: float = 0.005, stream: Optional[int] = None, device: int = 0, work_bytes: int = 0):
+        opt = hfx_default_options()
+        opt.precision = {"fp64": HFX_PREC_FP64, "sliced": HFX_PREC_SLICED}[precision]
+        opt.sparse = {"auto": HFX_SPARSE_AUTO, "on": HFX_SPARSE_ON, "off": HFX_SPARSE_OFF}[sparse]
+        opt.q0_term = int(bool(q0_term))
+        opt.beta = float(beta)
+        opt.stream = stream
+        opt.device = int(device)
+        opt.work_bytes = int(work_bytes)
+        self.sys = sysm
+        self.ctx = hfx_create(sysm.lattice, sysm.pos_frac, sysm.rmt, sysm.lmax, sysm.Lmax, sysm.P, sysm.mesh, opt)
+
+    def load_system(self, kpoints: bool = True, coulomb: bool = True, radial: bool = True):
+        s = self.sys
+        if radial:
+            for a in range(s.n_atoms):
+                hfx_set_radial(self.ctx, a, s.R[a], s.mu[a])
+        if kpoints:
+            self.set_kpoints()
+        if coulomb:
+            for iq in range(s.n_k):
+                hfx_set_coulomb(self.ctx, iq, s.Gaux[iq], s.v[iq])
+
+    def set_kpoints(self):
+        s = self.sys
+        for ik in range(s.n_k):
+            hfx_set_kpoint(self.ctx, ik, int(s.n_bands[ik]), int(s.n_occ[ik]), s.Gk[ik], s.c[ik], s.A[ik])
+
+    def build_all(self, keep_products: bool = False) -> dict:
+        return hfx_build_all(self.ctx, keep_products)
+
+    def exchange(self, ik: int) -> np.ndarray:
+        return hfx_get_exchange(self.ctx, ik, int(self.sys.n_bands[ik]))
+
+    def build_exchange(self, ik: int) -> np.ndarray:
+        return hfx_build_exchange(self.ctx, ik, int(self.sys.n_bands[ik]))
+
+    def energy(self) -> float:
+        return hfx_get_energy(self.ctx)
+
+    def q0_bracket(self) -> float:
+        return hfx_get_q0_bracket(self.ctx)
+
+    def products(self, ik: int, iq: int, ikp: int) -> np.ndarray:
+        s = self.sys
+        return hfx_get_products(self.ctx, ik, iq, (s.n_aux(iq), int(s.n_occ[ikp]), int(s.n_bands[ik])))
+
+    def set_products(self, ik: int, iq: int, Z):
+        hfx_set_products(self.ctx, ik, iq, Z)
+
+    def close(self):
+        if self.ctx:
+            hfx_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
