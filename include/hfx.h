@@ -198,6 +198,34 @@ HFX_API int hfx_get_energy(hfx_ctx *ctx, double *Ex);
  *     - (4 pi / (N_k Omega)) sum_{q, G: 0<|q+G|<=q0} e^{-beta|q+G|^2}/|q+G|^2. */
 HFX_API int hfx_get_q0_bracket(hfx_ctx *ctx, double *b);
 
+/* Allocation-free q->0 bracket (no counterpart in the paper: an interface
+ * choice of this library).  Computes the same number as hfx_get_q0_bracket,
+ * b of Eq. (div final), but needs no context and allocates no device memory,
+ * for callers that cannot allocate at that point: processes whose device
+ * memory is entirely owned by another allocator (for example a framework's
+ * caching pool), and code that must avoid the device-wide synchronisation
+ * that cudaMalloc/cudaFree may perform.
+ *   lattice      [9] rows a_i (bohr)
+ *   mesh         [3] k mesh, each 1..64
+ *   beta         Eq. (F(q)) parameter in (0, 1)
+ *   bracket_dev  DEVICE pointer to one double owned by the caller; written
+ *                asynchronously on `stream`
+ *   stream       cudaStream_t (NULL: legacy default stream), current device
+ * The partial sums of the reduction live in a fixed 512 KiB device array
+ * inside the library (65536 doubles): each GPU that loads the library holds
+ * it until the process exits.  Sizes needing more partial sums than that
+ * (k points x (2 ceil(q0 |a_1| / 2 pi) + 5) > 65536) return HFX_EUNSUPPORTED.
+ * The first call on a device resolves the array's device address (one-time
+ * set-up); make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (different streams, or devices
+ * sharing nothing but the same call site) race on it and must be ordered by
+ * the caller.  Every partial sum is written before it is read, so nothing
+ * needs clearing between calls.  Errors: HFX_EINVAL (bad pointer, mesh or
+ * beta), HFX_ENONFINITE, HFX_EUNSUPPORTED, HFX_EDEVICE (no device or launch
+ * failure). */
+HFX_API int hfx_q0_bracket_noalloc(const double *lattice, const int *mesh, double beta, double *bracket_dev,
+                                   void *stream);
+
 /* Release every host and device resource of the context (NULL is a no-op). */
 HFX_API void hfx_destroy(hfx_ctx *ctx);
 

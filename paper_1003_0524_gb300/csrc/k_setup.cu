@@ -1,6 +1,8 @@
 // k_setup.cu -- once-per-context and once-per-SCF-cycle kernels, all FP64:
 // Gaunt table, multipole transforms, step function, Coulomb-matrix transform,
 // split embedding of the transformed Coulomb matrix, q->0 bracket.
+#include <cmath>
+
 #include "hfx_internal.cuh"
 
 namespace hfx {
@@ -414,3 +416,90 @@ size_t q0_partial_count(const int mesh[3], double beta, const double *lattice) {
 }
 
 }  // namespace hfx
+
+// =====================================================================
+// Allocation-free variant of the q->0 bracket.
+//
+// Some callers cannot allocate device memory at the point where they need
+// this number: processes whose device memory is entirely owned by another
+// allocator (for example a framework's caching pool that has reserved the
+// device), and code paths that must not trigger the implicit device-wide
+// synchronisation that cudaMalloc/cudaFree may perform.  For them the
+// per-slab partial sums of the reduction live in the fixed array below
+// instead of a cudaMalloc'd buffer.  The array is a file-scope device
+// variable: every GPU that loads this library holds it (512 KiB) until the
+// process exits, and every call shares it.
+// =====================================================================
+namespace hfx {
+namespace {
+
+constexpr int kQ0ScratchMax = 65536;   // partial sums (doubles) the array holds
+static __device__ __align__(256) double g_q0_scratch[kQ0ScratchMax];
+
+// Device address of g_q0_scratch, resolved once per device.  In host code
+// the name g_q0_scratch is only a host-side stand-in, never a device address.
+constexpr int kMaxDevices = 64;
+double *g_q0_scratch_dev[kMaxDevices] = {nullptr};
+
+__global__ void q0_final_to_kernel(const double *partial, int n, double *out, double beta, double q0, double nk,
+                                   double omega) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = erf(sqrt(beta) * q0) / sqrt(kPi * beta) - 4.0 * kPi / (nk * omega) * red[0];
+}
+
+}  // namespace
+
+}  // namespace hfx
+
+extern "C" int hfx_q0_bracket_noalloc(const double *lattice, const int *mesh, double beta, double *bracket_dev,
+                                      void *stream) {
+    using namespace hfx;
+    if (!lattice || !mesh || !bracket_dev || !(beta > 0.0 && beta < 1.0)) return HFX_EINVAL;
+    for (int i = 0; i < 3; ++i)
+        if (mesh[i] < 1 || mesh[i] > 64) return HFX_EINVAL;
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(lattice[i])) return HFX_ENONFINITE;
+    const double *a = lattice;
+    double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
+    if (!(fabs(det) > 1e-9)) return HFX_EINVAL;
+    // reciprocal rows b_i = 2 pi (A^{-1})^T, evaluated as in hfx_create
+    double inv[9], B[9];
+    inv[0] = (a[4] * a[8] - a[5] * a[7]) / det; inv[1] = (a[2] * a[7] - a[1] * a[8]) / det; inv[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+    inv[3] = (a[5] * a[6] - a[3] * a[8]) / det; inv[4] = (a[0] * a[8] - a[2] * a[6]) / det; inv[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+    inv[6] = (a[3] * a[7] - a[4] * a[6]) / det; inv[7] = (a[1] * a[6] - a[0] * a[7]) / det; inv[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) B[3 * i + j] = 2.0 * M_PI * inv[3 * j + i];
+    size_t nslab = q0_partial_count(mesh, beta, lattice);
+    if (nslab > (size_t)kQ0ScratchMax) return HFX_EUNSUPPORTED;   // k mesh x G box too large for the fixed array
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HFX_EDEVICE;
+    if (!g_q0_scratch_dev[dev]) {
+        // one-time set-up on this device (the device is current here)
+        double *ptr = nullptr;
+        if (cudaGetSymbolAddress((void **)&ptr, g_q0_scratch) != cudaSuccess || !ptr) return HFX_EDEVICE;
+        g_q0_scratch_dev[dev] = ptr;
+    }
+    double *partial = g_q0_scratch_dev[dev];
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double q0 = sqrt(-log(beta) / beta);
+    int bnd[3];
+    for (int i = 0; i < 3; ++i) {
+        double an = sqrt(lattice[3 * i] * lattice[3 * i] + lattice[3 * i + 1] * lattice[3 * i + 1] +
+                         lattice[3 * i + 2] * lattice[3 * i + 2]);
+        bnd[i] = (int)ceil(q0 * an / (2.0 * kPi)) + 2;
+    }
+    int nk = mesh[0] * mesh[1] * mesh[2];
+    // every partial sum [0, nslab) is written before it is read: nothing to clear
+    q0_partial_kernel<<<(unsigned)nslab, 256, 0, st>>>(partial, mesh[0], mesh[1], mesh[2], B[0], B[1], B[2], B[3], B[4],
+                                                       B[5], B[6], B[7], B[8], beta, q0, bnd[0], bnd[1], bnd[2]);
+    q0_final_to_kernel<<<1, 256, 0, st>>>(partial, (int)nslab, bracket_dev, beta, q0, (double)nk, fabs(det));
+    return cudaGetLastError() == cudaSuccess ? HFX_OK : HFX_EDEVICE;
+}

@@ -33,7 +33,7 @@ EXPORTS = (
     "hfx_default_options", "hfx_create", "hfx_set_radial", "hfx_set_kpoint", "hfx_set_coulomb",
     "hfx_set_products", "hfx_get_products", "hfx_build_all", "hfx_build_exchange", "hfx_get_exchange",
     "hfx_exchange_device_ptr", "hfx_get_energy", "hfx_get_q0_bracket", "hfx_destroy", "hfx_strerror",
-    "hfx_last_error", "hfx_version",
+    "hfx_last_error", "hfx_version", "hfx_q0_bracket_noalloc",
 )
 
 
@@ -145,6 +145,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.hfx_last_error.argtypes = [vp]
     L.hfx_version.restype = ctypes.c_char_p
     L.hfx_version.argtypes = []
+    L.hfx_q0_bracket_noalloc.restype = ip
+    L.hfx_q0_bracket_noalloc.argtypes = [vp, vp, dp, vp, vp]
     _lib = L
     return L
 
@@ -258,6 +260,16 @@ def hfx_get_q0_bracket(ctx) -> float:
     b = ctypes.c_double()
     _check(ctx, load().hfx_get_q0_bracket(ctx, ctypes.byref(b)))
     return float(b.value)
+
+
+def hfx_q0_bracket_noalloc(lattice, mesh, beta: float, bracket_dev_ptr: int, stream: Optional[int] = None):
+    """Allocation-free q->0 bracket: writes one double to the caller-owned
+    device address ``bracket_dev_ptr`` (see include/hfx.h)."""
+    lat = _c(lattice, np.float64).ravel()
+    m = _c(mesh, np.int32).ravel()
+    code = load().hfx_q0_bracket_noalloc(lat.ctypes.data, m.ctypes.data, float(beta), int(bracket_dev_ptr), stream)
+    if code != HFX_OK:
+        raise HfxError(code, load().hfx_strerror(code).decode())
 
 
 def hfx_destroy(ctx):
