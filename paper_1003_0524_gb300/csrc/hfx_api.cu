@@ -362,8 +362,9 @@ void hfx_destroy(hfx_ctx *ctx) {
     for (auto *v : ctx->d_V) dfree(v);
     dfree(ctx->d_R); dfree(ctx->d_mu); dfree(ctx->d_T); dfree(ctx->d_gaunt); dfree(ctx->d_posf);
     dfree(ctx->d_err); dfree(ctx->d_Ex);
-    Scratch *all[] = {&ctx->s_theta, &ctx->s_thpsi, &ctx->s_B, &ctx->s_zc, &ctx->s_zs, &ctx->s_ys, &ctx->s_y64,
-                      &ctx->s_praw, &ctx->s_vacc, &ctx->s_pairs, &ctx->s_qd, &ctx->s_misc, &ctx->s_ap};
+    Scratch *all[] = {&ctx->s_theta, &ctx->s_thpsi, &ctx->s_B,    &ctx->s_zc,   &ctx->s_zs,   &ctx->s_ys,
+                      &ctx->s_y64,   &ctx->s_praw,  &ctx->s_vacc, &ctx->s_pairs, &ctx->s_qd,  &ctx->s_misc,
+                      &ctx->s_ap,    &ctx->s_aexp,  &ctx->s_xexp, &ctx->s_zipw};
     for (Scratch *s : all) dfree(s->p);
     delete ctx;
 }
@@ -769,12 +770,30 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
                       ctx->nlmp, N0, sparse, no_max, Zc, RSc, ctx->stream);
         const int rowbase_ipw = nmt;  // N0 + n_ch = N_MT in the sparse order as well
         cudaEvent_t ez0 = evs.make(ctx);
-        rc = launch_zipw<R>(d_pairs, d_kpair, nk, nb_max, d_qd, nq, reinterpret_cast<V *const *>(misc + o_T), geo.tlo,
-                            geo.tdim, reinterpret_cast<const double2 *const *>(misc + o_c),
-                            reinterpret_cast<const int *const *>(misc + o_G), reinterpret_cast<const int *>(misc + o_npw),
-                            npw_max, reinterpret_cast<const int *const *>(misc + o_Ga), reinterpret_cast<const int *>(misc + o_nb),
-                            ctx->omega, rowbase_ipw, Zc, RSc, ctx->stream);
-        if (rc) return set_err(ctx, rc, "interstitial kernel does not fit this size");
+        if (tc && sizeof(R) == 8) {
+            ZipwTcInput zin;
+            zin.kset = kset;
+            zin.qs = bt.qs;
+            zin.pairs = bt.pairs;
+            zin.d_pairs = d_pairs;
+            zin.d_ck = reinterpret_cast<const double2 *const *>(misc + o_c);
+            zin.d_Gk = reinterpret_cast<const int *const *>(misc + o_G);
+            zin.d_npw = reinterpret_cast<const int *>(misc + o_npw);
+            zin.d_nb = reinterpret_cast<const int *>(misc + o_nb);
+            zin.d_Tk = reinterpret_cast<const double2 *const *>(misc + o_T);
+            zin.nb_max = nb_max;
+            for (int x = 0; x < 3; ++x) { zin.tlo[x] = geo.tlo[x]; zin.tdim[x] = geo.tdim[x]; }
+            zin.d_Z = reinterpret_cast<double2 *>(Zc);
+            zin.RSc = RSc;
+            if ((rc = zipw_tc_prepare_and_launch(ctx, zin))) return rc;
+        } else {
+            rc = launch_zipw<R>(d_pairs, d_kpair, nk, nb_max, d_qd, nq, reinterpret_cast<V *const *>(misc + o_T), geo.tlo,
+                                geo.tdim, reinterpret_cast<const double2 *const *>(misc + o_c),
+                                reinterpret_cast<const int *const *>(misc + o_G), reinterpret_cast<const int *>(misc + o_npw),
+                                npw_max, reinterpret_cast<const int *const *>(misc + o_Ga), reinterpret_cast<const int *>(misc + o_nb),
+                                ctx->omega, rowbase_ipw, Zc, RSc, ctx->stream);
+            if (rc) return set_err(ctx, rc, "interstitial kernel does not fit this size");
+        }
         ev_zipw.push_back({ez0, evs.make(ctx)});
         nlaunch += 2;
         for (int i = 0; i < npairs; ++i) {

@@ -140,7 +140,7 @@ struct hfx_ctx {
 
     // scratch
     hfx::Scratch s_theta, s_thpsi, s_B, s_zc, s_zs, s_ys, s_y64, s_praw, s_vacc, s_pairs, s_qd,
-        s_misc, s_ap, s_aexp, s_xexp;
+        s_misc, s_ap, s_aexp, s_xexp, s_zipw;
 };
 
 namespace hfx {
@@ -225,6 +225,22 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
                     const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *h_pairs,
                     const PairDesc *d_pairs, int npairs, const QDesc *d_q, int NB, const long long *d_praw_off,
                     double *d_praw, void *d_tiles_buf, size_t tiles_cap);
+
+// ------------------------------------------------------------ interstitial projections on the tensor cores (k_zipw_tc.cu)
+struct ZipwTcInput {
+    std::vector<int> kset, qs;              // k points with pairs; q of the batch
+    std::vector<PairDesc> pairs;            // host copy of the batch pairs
+    const PairDesc *d_pairs;
+    const double2 *const *d_ck;             // per k: c [nb][npw]
+    const int *const *d_Gk;                 // per k: G [npw][3]
+    const int *d_npw, *d_nb;
+    const double2 *const *d_Tk;             // per k: T_n(K) [nb][box] (FP64)
+    int nb_max;
+    int tlo[3], tdim[3];                    // T box
+    double2 *d_Z;                           // projections [col][RSc]
+    long long RSc;
+};
+int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in);
 
 // ------------------------------------------------------------ kernels (finish, k_finish.cu)
 void launch_reduce_pairs(const PairDesc *d_pairs, const int *d_kstart, const int *d_klist_pairs, int nk_in_batch,

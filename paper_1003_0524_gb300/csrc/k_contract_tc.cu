@@ -29,169 +29,18 @@
 #include <algorithm>
 #include <string>
 
-#include "hfx_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace hfx {
 
+using namespace tc;
+
 namespace {
 
-constexpr unsigned long long kWaitNs = 2000000000ULL;  // 2 s
-
-// ------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
-}
-__device__ __forceinline__ uint32_t mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\tselp.b32 %0, 1, 0, P1;\n\t}"
-        : "=r"(ok)
-        : "r"(saddr(bar)), "r"(parity)
-        : "memory");
-    return ok;
-}
-// Bounded wait.  Returns false (and raises the CTA abort flag and the global
-// error word) if the phase did not complete in time or the CTA is aborting.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err,
-                                          int code) {
-    unsigned long long t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 63) == 63) {
-            if (*abort_flag) return false;
-            unsigned long long now = gtimer();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitNs) {
-                *abort_flag = 1;
-                atomicCAS(err, 0, code);
-                return false;
-            }
-        }
-    }
-}
-// Best-effort bounded wait used only while draining after an abort.
-__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
-    unsigned long long t0 = gtimer();
-    while (!mbar_try(bar, parity)) {
-        if (gtimer() - t0 > kWaitNs) return;
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
-            "r"(dst),
-        "l"((uint64_t)map), "r"(saddr(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor, K-major operand, 128-byte swizzle:
-// 8-row atoms of 1024 bytes (stride-byte-offset), leading offset unused.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// Instruction descriptor: BF16 x BF16 -> FP32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// ------------------------------------------------------------- slices
-constexpr int NPL = 4;      // slices per operand
-constexpr int NTERM = 10;   // slice products s_i t_j with i + j <= 3
+// ------------------------------------------------------------- slice terms
 __device__ __constant__ int kSA[NTERM] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
 __device__ __constant__ int kSB[NTERM] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
 __device__ __constant__ int kSW[NTERM] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
-
-// exponent e with max < 2^e (0 for an all-zero line)
-__device__ __forceinline__ int line_exp(double mx) {
-    if (!(mx > 0.0)) return 0;
-    int e;
-    frexp(mx, &e);
-    return e;
-}
-
-__device__ __forceinline__ void slice4(double x, int e, __nv_bfloat16 *o /* 4 */) {
-    double u = ldexp(x, -e);
-#pragma unroll
-    for (int i = 0; i < NPL; ++i) {
-        u *= 256.0;
-        double s = rint(u);
-        u -= s;
-        o[i] = __double2bfloat16(s);   // |s| <= 256: exact in BF16
-    }
-}
-
-// Combine the four exact class sums of one K group (units 2^(eA+eB-16)) and
-// add them, scaled by sc, into the compensated pair (hi, lo).
-__device__ __forceinline__ void class_accumulate(float a0, float a1, float a2, float a3, float sc, float &hi,
-                                                 float &lo) {
-    float c = fmaf(a3, 0x1p-8f, a2);
-    c = fmaf(c, 0x1p-8f, a1);
-    float x = a0 * sc;
-    float s = hi + x;
-    float bb = s - hi;
-    float er = (hi - (s - bb)) + (x - bb);
-    hi = s;
-    lo += er + c * (0x1p-8f * sc);
-}
 
 // ------------------------------------------------------------- column slicing
 // For every column of the batch: exponent over its rows (real and imaginary
@@ -672,6 +521,9 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
     }
 }
 
+}  // namespace
+
+namespace tc {
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -690,7 +542,7 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2-D BF16 tensor [rows][cols] (cols contiguous), box {64, box_rows}, 128-byte swizzle
-int make_map(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows) {
+int make_map_2d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_err(ctx, HFX_EDEVICE, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -715,7 +567,24 @@ int num_sms() {
     return n;
 }
 
-}  // namespace
+
+int make_map_5d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, const unsigned long long dims[5],
+                const unsigned long long strides_bytes[4], const unsigned int box[5], int swizzle_bytes) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_err(ctx, HFX_EDEVICE, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t d[5], st[4];
+    cuuint32_t b[5], es[5] = {1, 1, 1, 1, 1};
+    for (int i = 0; i < 5; ++i) { d[i] = dims[i]; b[i] = box[i]; }
+    for (int i = 0; i < 4; ++i) st[i] = strides_bytes[i];
+    CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                            : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                            : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(ptr), d, st, b, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_err(ctx, HFX_EDEVICE, "cuTensorMapEncodeTiled (5-D) failed (" + std::to_string((int)r) + ")");
+    return HFX_OK;
+}
+}  // namespace tc
 
 template <typename V>
 void launch_slice_cols(const V *d_Z, long long RSc, const QDesc *d_q, int nq, long long NC, long long maxcols, int N0,
@@ -766,8 +635,8 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
                                              cudaMemcpyHostToDevice, ctx->stream), "gemm1 tiles");
     if (rc) return rc;
     CUtensorMap mA, mB;
-    if ((rc = make_map(ctx, &mA, d_Ap_all, ap_rows, RS, G1_BM))) return rc;
-    if ((rc = make_map(ctx, &mB, d_ZS, (long long)NPL * NC, RS, G1_BN))) return rc;
+    if ((rc = make_map_2d(ctx, &mA, d_Ap_all, ap_rows, RS, G1_BM))) return rc;
+    if ((rc = make_map_2d(ctx, &mB, d_ZS, (long long)NPL * NC, RS, G1_BN))) return rc;
     G1Params p;
     p.tiles = reinterpret_cast<const G1Tile *>(d_tiles_buf);
     p.ntiles = (int)tiles.size();
@@ -810,8 +679,8 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
                                              cudaMemcpyHostToDevice, ctx->stream), "gemm2 tiles");
     if (rc) return rc;
     CUtensorMap mZ, mY;
-    if ((rc = make_map(ctx, &mZ, d_ZS, (long long)NPL * NC, RS, NB))) return rc;
-    if ((rc = make_map(ctx, &mY, d_YS, (long long)NPL * NC, RS, NB))) return rc;
+    if ((rc = make_map_2d(ctx, &mZ, d_ZS, (long long)NPL * NC, RS, NB))) return rc;
+    if ((rc = make_map_2d(ctx, &mY, d_YS, (long long)NPL * NC, RS, NB))) return rc;
     G2Params p;
     p.tiles = reinterpret_cast<const G2Tile *>(d_tiles_buf);
     p.ntiles = (int)tiles.size();

@@ -90,7 +90,12 @@ def test_split_matches_oracle(name):
         assert np.abs(V[k] - V[k].conj().T).max() <= 2 * TOL_SPLIT_ABS
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("sliced", 1e-12)])
+# the sliced build computes the interstitial projections on the tensor cores:
+# each operand line keeps 33 bits relative to its largest element (a band of
+# T_n over the whole step-function box), so a pair whose projections are small
+# compared with those maxima sees a few 1e-9 relative; the bar is 5e-9 of the
+# pair's largest projection (the MT part stays FP64).
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("sliced", 5e-9)])
 def test_projections_match_oracle(precision, tol):
     s = S.make_system(1, mesh=(2, 2, 2), nb=6, no=3)
     o = O.Oracle(s)
