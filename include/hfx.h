@@ -115,7 +115,8 @@ typedef struct {
     int n_batches;            /* q batches */
     int sparse_used;          /* 1 if the block-sparse form was used */
     int n_launches;           /* kernels launched by this build */
-    double ms_zipw;           /* interstitial projection kernel (all launches) */
+    double ms_zipw;           /* interstitial projection kernel (all launches; the GEMM
+                                 kernel alone in the sliced build) */
     double ms_apply;          /* Coulomb apply Y = v_t Z (dense block, all launches) */
     double ms_zhy;            /* Z^H Y contraction (all launches) */
     double flops_apply;       /* useful flops of the dense-block apply: 8 D^2 per column */

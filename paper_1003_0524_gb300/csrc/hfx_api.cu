@@ -364,7 +364,7 @@ void hfx_destroy(hfx_ctx *ctx) {
     dfree(ctx->d_err); dfree(ctx->d_Ex);
     Scratch *all[] = {&ctx->s_theta, &ctx->s_thpsi, &ctx->s_B,    &ctx->s_zc,   &ctx->s_zs,   &ctx->s_ys,
                       &ctx->s_y64,   &ctx->s_praw,  &ctx->s_vacc, &ctx->s_pairs, &ctx->s_qd,  &ctx->s_misc,
-                      &ctx->s_ap,    &ctx->s_aexp,  &ctx->s_xexp, &ctx->s_zipw};
+                      &ctx->s_ap,    &ctx->s_aexp,  &ctx->s_xexp, &ctx->s_zipw, &ctx->s_cgT, &ctx->s_cgZ};
     for (Scratch *s : all) dfree(s->p);
     delete ctx;
 }
@@ -603,10 +603,21 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
     for (int i = 0; i < nk; ++i) {
         if (!need_k[i]) continue;
         launch_bmat<R>(hA[i], ctx->d_R, ctx->d_T, ctx->d_gaunt, s.n_atoms, s.lmax, s.Lmax, P, hnb[i], sparse, hB[i], ctx->stream);
-        launch_thetapsi<R>(as<double2>(ctx->s_theta), geo.dlo, geo.ddim, geo.tlo, geo.tdim, hc[i], hG[i], hnb[i], hnpw[i],
-                           hT[i], ctx->stream);
+        if (!tc)
+            launch_thetapsi<R>(as<double2>(ctx->s_theta), geo.dlo, geo.ddim, geo.tlo, geo.tdim, hc[i], hG[i], hnb[i],
+                               hnpw[i], hT[i], ctx->stream);
     }
     if ((rc = cuda_check(ctx, cudaGetLastError(), "per-k kernels"))) return rc;
+    ZmtTcState zmt_state;
+    if (tc) {
+        // T_n(K) and the operand slices of Z^MT on the tensor cores, once per build
+        if ((rc = thetapsi_tc(ctx, kset, as<double2>(ctx->s_theta), geo.dlo, geo.ddim, geo.tlo, geo.tdim,
+                              reinterpret_cast<double2 *>(ctx->s_thpsi.p), toff)))
+            return rc;
+        std::vector<double2 *> hB2(nk);
+        for (int i = 0; i < nk; ++i) hB2[i] = reinterpret_cast<double2 *>(hB[i]);
+        if ((rc = zmt_tc_prepare(ctx, zmt_state, kset, hB2, RSc, N0, sparse))) return rc;
+    }
 
     // ---------------- q batches
     size_t budget = ctx->opt.work_bytes;
@@ -660,7 +671,7 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
     double flops = 0.0, fl_apply = 0.0, fl_zhy = 0.0, fl_zipw = 0.0;
     int npairs_total = 0;
     int nlaunch = 1 + 2 * (int)kset.size();  // theta + per-k B and Theta-psi
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_zipw, ev_apply, ev_zhy;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_zipw, ev_apply, ev_zhy, ev_zipw_gemm;
 
     for (Batch &bt : batches) {
         // columns and pairs
@@ -743,6 +754,12 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
                p_klp = place2(std::max<size_t>(1, klpairs.size()) * sizeof(int)), p_vb = place2(nq * sizeof(void *)),
                p_zg = place2(std::max(npairs, nq) * sizeof(ZGemmBatch)),
                p_tiles = place2((size_t)64 << 20);
+        // per-batch tables of the tensor-core Z^MT product: offsets per (k, pair), phases, tiles
+        const size_t zt_cap = tc ? rup((size_t)nk * (zmt_state.RB / 2) * 8, 256) + rup((size_t)nk * s.n_atoms * nk * 16, 256) +
+                                       (size_t)nk * s.n_atoms * ((size_t)(nb_max * ctx->nLM * P + 127) / 128) *
+                                           (size_t)(zmt_state.npairs_pad / 32 + 1) * 24 + 4096
+                                 : 256;
+        size_t p_zt = place2(zt_cap);
         if ((rc = scratch_reserve(ctx, ctx->s_pairs, o2))) return rc;
         char *dp = as<char>(ctx->s_pairs);
         PairDesc *d_pairs = reinterpret_cast<PairDesc *>(dp + p_pairs);
@@ -765,9 +782,14 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
 
         cudaEvent_t e0 = evs.make(ctx);
         // ---- stage 1: projections
-        launch_zmt<R>(d_pairs, npairs, d_qd, reinterpret_cast<V *const *>(misc + o_B),
-                      reinterpret_cast<const double2 *const *>(misc + o_A), ctx->d_posf, s.mesh, s.n_atoms, ctx->nLM, P,
-                      ctx->nlmp, N0, sparse, no_max, Zc, RSc, ctx->stream);
+        if (tc) {
+            if ((rc = zmt_tc_launch(ctx, zmt_state, bt.pairs, RSc, reinterpret_cast<double2 *>(Zc), dp + p_zt, zt_cap)))
+                return rc;
+        } else {
+            launch_zmt<R>(d_pairs, npairs, d_qd, reinterpret_cast<V *const *>(misc + o_B),
+                          reinterpret_cast<const double2 *const *>(misc + o_A), ctx->d_posf, s.mesh, s.n_atoms, ctx->nLM,
+                          P, ctx->nlmp, N0, sparse, no_max, Zc, RSc, ctx->stream);
+        }
         const int rowbase_ipw = nmt;  // N0 + n_ch = N_MT in the sparse order as well
         cudaEvent_t ez0 = evs.make(ctx);
         if (tc && sizeof(R) == 8) {
@@ -785,7 +807,12 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
             for (int x = 0; x < 3; ++x) { zin.tlo[x] = geo.tlo[x]; zin.tdim[x] = geo.tdim[x]; }
             zin.d_Z = reinterpret_cast<double2 *>(Zc);
             zin.RSc = RSc;
+            cudaEventCreate(&zin.ev_gemm0);
+            cudaEventCreate(&zin.ev_gemm1);
+            evs.ev.push_back(zin.ev_gemm0);
+            evs.ev.push_back(zin.ev_gemm1);
             if ((rc = zipw_tc_prepare_and_launch(ctx, zin))) return rc;
+            ev_zipw_gemm.push_back({zin.ev_gemm0, zin.ev_gemm1});
         } else {
             rc = launch_zipw<R>(d_pairs, d_kpair, nk, nb_max, d_qd, nq, reinterpret_cast<V *const *>(misc + o_T), geo.tlo,
                                 geo.tdim, reinterpret_cast<const double2 *const *>(misc + o_c),
@@ -949,7 +976,7 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
             for (auto &pr : v) { float x = 0.f; cudaEventElapsedTime(&x, pr.first, pr.second); tot += x; }
             return tot;
         };
-        st->ms_zipw = sum(ev_zipw);
+        st->ms_zipw = ev_zipw_gemm.empty() ? sum(ev_zipw) : sum(ev_zipw_gemm);
         st->ms_apply = sum(ev_apply);
         st->ms_zhy = sum(ev_zhy);
         st->flops_apply = fl_apply;

@@ -140,7 +140,7 @@ struct hfx_ctx {
 
     // scratch
     hfx::Scratch s_theta, s_thpsi, s_B, s_zc, s_zs, s_ys, s_y64, s_praw, s_vacc, s_pairs, s_qd,
-        s_misc, s_ap, s_aexp, s_xexp, s_zipw;
+        s_misc, s_ap, s_aexp, s_xexp, s_zipw, s_cgT, s_cgZ;
 };
 
 namespace hfx {
@@ -239,8 +239,28 @@ struct ZipwTcInput {
     int tlo[3], tdim[3];                    // T box
     double2 *d_Z;                           // projections [col][RSc]
     long long RSc;
+    cudaEvent_t ev_gemm0 = nullptr, ev_gemm1 = nullptr;   // recorded around the GEMM launch if set
 };
 int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in);
+
+// ------------------------------------------------------------ stage-1 products on the tensor cores (k_cgemm_tc.cu)
+// T_n(K) of every k of kset (Sec. III.B), written to d_T + toff[k] + n * box.
+int thetapsi_tc(hfx_ctx *ctx, const std::vector<int> &kset, const double2 *d_theta, const int dlo[3], const int ddim[3],
+                const int tlo[3], const int tdim[3], double2 *d_T, const std::vector<size_t> &toff);
+struct ZmtTcState {                         // operand slices of Z^MT, valid for one build
+    bool ready = false;
+    int Kh = 0, npairs_a = 0, npairs_pad = 0;
+    long long RA = 0, RB = 0;
+    std::vector<long long> blk_row0, blk_rows;   // [k][a]
+    std::vector<int> kbase, pk, pm;              // (k', m) pair list of every atom block
+    std::vector<std::pair<int, int>> blocks;     // (k, a) of the A blocks
+    size_t oA = 0, oB = 0, oae = 0, obe = 0, oro = 0, opk = 0, fixed_bytes = 0;
+};
+int zmt_tc_prepare(hfx_ctx *ctx, ZmtTcState &zs, const std::vector<int> &kset, const std::vector<double2 *> &hB,
+                   long long RSc, int N0, int sparse);
+// Z^MT of the pairs of one batch (Sec. III.A) into d_Z; d_tables: device scratch for per-batch tables.
+int zmt_tc_launch(hfx_ctx *ctx, const ZmtTcState &zs, const std::vector<PairDesc> &pairs, long long RSc, double2 *d_Z,
+                  void *d_tables, size_t tables_cap);
 
 // ------------------------------------------------------------ kernels (finish, k_finish.cu)
 void launch_reduce_pairs(const PairDesc *d_pairs, const int *d_kstart, const int *d_klist_pairs, int nk_in_batch,

@@ -59,14 +59,14 @@ __global__ void slice_cols_kernel(const V *__restrict__ Z, long long RSc, const 
         long long col = q.colbase + c;
         const V *z = Z + col * RSc;
         int nrow = N0 + q.D;
-        double mx = 0.0;
+        unsigned long long mx = 0;
         for (int r = lane; r < nrow; r += 32) {
             V v = z[r];
-            mx = fmax(mx, fmax(fabs((double)v.x), fabs((double)v.y)));
+            mx = max(mx, max(abs_bits((double)v.x), abs_bits((double)v.y)));
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        int e = line_exp(mx);
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int e = line_exp_bits(mx);
         if (lane == 0) xexp[col] = e;
         size_t base = (size_t)col * RS;
         for (int u = lane; u < HS; u += 32) {

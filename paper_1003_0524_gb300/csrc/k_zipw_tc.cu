@@ -527,7 +527,9 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     auto go = [&](auto kern, int nb) {
         size_t smem = (size_t)ZT_STAGES * NPL * (ZT_A_PLANE + 4 * nb * 32) + 1024;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (in.ev_gemm0) cudaEventRecord(in.ev_gemm0, st);
         kern<<<grid, 64 + 32 * ZT_EPI, smem, st>>>(mA, mT, p);
+        if (in.ev_gemm1) cudaEventRecord(in.ev_gemm1, st);
     };
     switch (NBt) {
     case 16: go(zipw_tc_kernel<16>, 16); break;

@@ -152,23 +152,52 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map
 constexpr int NPL = 4;      // slices per operand
 constexpr int NTERM = 10;   // slice products s_i t_j with i + j <= 3
 
-// exponent e with max < 2^e (0 for an all-zero line)
-__device__ __forceinline__ int line_exp(double mx) {
-    if (!(mx > 0.0)) return 0;
-    int e;
-    frexp(mx, &e);
-    return e;
+// The slicing below runs on the integer units: GB300's FP64 pipe is far too
+// narrow for a pass over every element of the projections.
+
+// |x| as an integer that orders like |x| (non-negative doubles order like
+// their bit patterns)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
 }
 
+// exponent e with max < 2^e, from abs_bits(max) (0 for an all-zero line)
+__device__ __forceinline__ int line_exp_bits(unsigned long long b) {
+    if (b == 0) return 0;
+    int E = (int)(b >> 52);
+    return E == 0 ? -1021 : E - 1022;
+}
+
+__device__ __forceinline__ int line_exp(double mx) { return line_exp_bits(abs_bits(mx)); }
+
+// x (|x| < 2^e) as four balanced base-256 digits s_0..s_3 of
+// N = round(x 2^(32-e)) (nearest, ties to even): x ~ sum_i s_i 2^(e-8(i+1)),
+// |s_0| <= 256, |s_1..3| <= 128, each exact in BF16.
 __device__ __forceinline__ void slice4(double x, int e, __nv_bfloat16 *o /* 4 */) {
-    double u = ldexp(x, -e);
-#pragma unroll
-    for (int i = 0; i < NPL; ++i) {
-        u *= 256.0;
-        double s = rint(u);
-        u -= s;
-        o[i] = __double2bfloat16(s);   // |s| <= 256: exact in BF16
+    long long bits = __double_as_longlong(x);
+    int E = (int)((bits >> 52) & 0x7ff);
+    long long N = 0;
+    if (E != 0) {   // zeros and subnormals give 0
+        unsigned long long m = ((unsigned long long)bits & 0xfffffffffffffULL) | (1ULL << 52);
+        int sh = 1043 + e - E;   // N = m 2^-sh; sh >= 21 because |x| < 2^e
+        unsigned long long q = 0;
+        if (sh < 64) {
+            q = m >> sh;
+            unsigned long long rem = m & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
+            if (rem > half || (rem == half && (q & 1))) ++q;
+        }
+        N = bits < 0 ? -(long long)q : (long long)q;
     }
+    long long d3 = ((N + 128) & 255) - 128;
+    N = (N - d3) >> 8;
+    long long d2 = ((N + 128) & 255) - 128;
+    N = (N - d2) >> 8;
+    long long d1 = ((N + 128) & 255) - 128;
+    N = (N - d1) >> 8;
+    o[0] = __float2bfloat16_rn((float)N);
+    o[1] = __float2bfloat16_rn((float)d1);
+    o[2] = __float2bfloat16_rn((float)d2);
+    o[3] = __float2bfloat16_rn((float)d3);
 }
 
 // Combine the four exact class sums of one K group (units 2^(eA+eB-16)) and
