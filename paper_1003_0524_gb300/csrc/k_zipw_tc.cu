@@ -5,13 +5,17 @@
 // For a fixed k and a fixed shift W = G - G0, every (k', m) row of every pair
 // (k, q) that needs this W is one row of a GEMM
 //   Z[(k', m), n] = sum_{G1} C[(k', m), G1] T_k[n](W + G1),   C = conj(c),
-// whose reduction index G1 runs over a common box organised in (x, y) lines
-// of 16 z values.  A = C (fixed per k', loaded by 2-D TMA, 128-byte swizzle);
-// B = T_k shifted by W, one TMA box of 16 z x all bands per line (32-byte
-// swizzle), read from eight z-shifted copies so that every TMA start
-// coordinate is 16-byte aligned.  Complex arithmetic uses the real embedding;
-// all operands are fixed-point slices (tc_ptx.cuh) with exact class sums on
-// the tensor cores and compensated combination on the CUDA cores.
+// whose reduction index G1 runs over the plane waves of all k' in segments of
+// 8 consecutive z values along the (x, y) lines of the plane-wave spheres.
+//
+// Operands (fixed-point slices of tc_ptx.cuh, real embedding of the complex
+// product with the real and imaginary outputs side by side in N):
+//   A row (k', m) = [ Re C | Im C ]                       (128-byte swizzle, 2-D TMA)
+//   B columns     = [ T_r ; -T_i ] (real out), [ T_i ; T_r ] (imag out)
+// B is loaded per segment as one 8-z box of both output blocks (no swizzle,
+// 5-D TMA straight from the sliced T box).  A TMA box must start on a 16-byte
+// boundary in z, so the segment grid of the lines is aligned per z phase of W:
+// the C slices come in eight phase variants, T in one copy.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -24,61 +28,72 @@ using namespace tc;
 
 namespace {
 
-__device__ __constant__ int kIA[NTERM] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-__device__ __constant__ int kIB[NTERM] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
-__device__ __constant__ int kIW[NTERM] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
+constexpr int ZT_BM = 128;
+constexpr int ZT_A_PLANE = 128 * 64 * 2;   // 16 KB: 128 rows x 64 K
+constexpr int ZT_GROUP = 4;                // 64-K chunks per exact group (256)
+constexpr int ZT_STAGES = 2;
+constexpr int ZT_EPI = 8;
+constexpr int ZT_NPH = 8;                  // z phases of the segment grid
+constexpr int ZT_NPART = 4;                // T parts: Re, Im, -Im, Re
+
+// slice-product term t: weight class w, slice of A, slice of B (a + b = w)
+__device__ __forceinline__ constexpr int term_w(int t) { return t < 1 ? 0 : t < 3 ? 1 : t < 6 ? 2 : 3; }
+__device__ __forceinline__ constexpr int term_a(int t) { return t - term_w(t) * (term_w(t) + 1) / 2; }
+__device__ __forceinline__ constexpr int term_b(int t) { return term_w(t) - term_a(t); }
+
+__device__ __forceinline__ double scale2(double d, int k) {
+    long long b = __double_as_longlong(d);
+    if ((b << 1) == 0) return d;
+    return __longlong_as_double(b + ((long long)k << 52));
+}
 
 // ------------------------------------------------------------- C slices
-// One block per row r = (k', m): exponent over |Re c|, |Im c| of the row,
-// then the real embedding rows Re r = [Re C | -Im C] and Im r = [Im C | Re C]
-// (C = conj c) scattered onto the line layout K = line * 16 + (z - gz0).
+// One block per row r = (k', m): exponent over |Re c|, |Im c| of the row, then
+// [Re C | Im C] = [c_r | -c_i] at K = segment * 8 + (z - z0) in every phase.
 __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int *const *__restrict__ Gk,
                                 const int *__restrict__ npw_k, const int *__restrict__ rowk, const int *__restrict__ rowm,
-                                const int *__restrict__ line_of, int gx0, int gy0, int gz0, int By, int KH, int Rpad,
+                                const int *__restrict__ line_of, int gx0, int gy0, int By, int nL,
+                                const int *__restrict__ segstart, const int *__restrict__ segz0, int Kh, int Rpad,
                                 __nv_bfloat16 *__restrict__ A, int *__restrict__ aexp) {
     int r = blockIdx.x;
     int kp = rowk[r], m = rowm[r];
     int npw = npw_k[kp];
     const double2 *c = ck[kp] + (size_t)m * npw;
     const int *G = Gk[kp];
-    long long W2 = 2LL * KH;                    // row length
-    long long plane = 2LL * Rpad * W2;
-    __shared__ double red[256];
-    double mx = 0.0;
-    for (int i = threadIdx.x; i < npw; i += blockDim.x) mx = fmax(mx, fmax(fabs(c[i].x), fabs(c[i].y)));
+    const long long W2 = 2LL * Kh;
+    __shared__ unsigned long long red[256];
+    unsigned long long mx = 0;
+    for (int i = threadIdx.x; i < npw; i += blockDim.x) mx = max(mx, max(abs_bits(c[i].x), abs_bits(c[i].y)));
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + st]);
+        if (threadIdx.x < st) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + st]);
         __syncthreads();
     }
-    int e = line_exp(red[0]);
-    if (threadIdx.x == 0) {
-        aexp[r] = e;
-        aexp[Rpad + r] = e;
-    }
+    int e = line_exp_bits(red[0]);
+    if (threadIdx.x == 0) aexp[r] = e;
     // the whole A buffer is zeroed before this kernel: only the plane waves are written
     for (int i = threadIdx.x; i < npw; i += blockDim.x) {
         int li = line_of[(G[3 * i] - gx0) * By + (G[3 * i + 1] - gy0)];
-        long long K = (long long)li * 16 + (G[3 * i + 2] - gz0);
-        double cr = c[i].x, ci = c[i].y;   // C = conj c = (cr, -ci)
-        __nv_bfloat16 s[NPL];
-        // Re row: [Re C | -Im C] = [cr | ci]
-        slice4(cr, e, s);
-        for (int p = 0; p < NPL; ++p) A[p * plane + (long long)r * W2 + K] = s[p];
-        slice4(ci, e, s);
-        for (int p = 0; p < NPL; ++p) A[p * plane + (long long)r * W2 + KH + K] = s[p];
-        // Im row: [Im C | Re C] = [-ci | cr]
-        slice4(-ci, e, s);
-        for (int p = 0; p < NPL; ++p) A[p * plane + (long long)(Rpad + r) * W2 + K] = s[p];
-        slice4(cr, e, s);
-        for (int p = 0; p < NPL; ++p) A[p * plane + (long long)(Rpad + r) * W2 + KH + K] = s[p];
+        int z = G[3 * i + 2];
+        __nv_bfloat16 sr[NPL], si[NPL];
+        slice4(c[i].x, e, sr);
+        slice4(-c[i].y, e, si);
+        for (int ph = 0; ph < ZT_NPH; ++ph) {
+            long long K = (long long)segstart[ph * nL + li] * 8 + (z - segz0[ph * nL + li]);
+#pragma unroll
+            for (int p = 0; p < NPL; ++p) {
+                __nv_bfloat16 *row = A + ((long long)(ph * NPL + p) * Rpad + r) * W2;
+                row[K] = sr[p];
+                row[Kh + K] = si[p];
+            }
+        }
     }
 }
 
 // ------------------------------------------------------------- T slices
-// Grid (n, k): exponent of band n of T_k over the box, then eight z-shifted
-// copies Tp[k][s][p][ri][n][X][Y][z] = slice_p(part_ri(T_k[n](X, Y, z + s))).
+// Grid (n, k): exponent of band n of T_k over the box, then the four parts
+// Tp[k][p][part][n][X][Y][z] = slice_p(Re T, Im T, -Im T, Re T).
 __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int *__restrict__ nb_k, int td0, int td1,
                                 int td2, int Zp, int nbmax, const int *__restrict__ kslot, __nv_bfloat16 *__restrict__ Tp,
                                 int *__restrict__ eT) {
@@ -87,33 +102,32 @@ __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int
     if (slot < 0 || n >= nb_k[k]) return;
     long long box = (long long)td0 * td1 * td2;
     const double2 *T = Tk[k] + (size_t)n * box;
-    __shared__ double red[256];
-    double mx = 0.0;
-    for (long long i = threadIdx.x; i < box; i += blockDim.x) mx = fmax(mx, fmax(fabs(T[i].x), fabs(T[i].y)));
+    __shared__ unsigned long long red[256];
+    unsigned long long mx = 0;
+    for (long long i = threadIdx.x; i < box; i += blockDim.x) mx = max(mx, max(abs_bits(T[i].x), abs_bits(T[i].y)));
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + st]);
+        if (threadIdx.x < st) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + st]);
         __syncthreads();
     }
-    int e = line_exp(red[0]);
+    int e = line_exp_bits(red[0]);
     if (threadIdx.x == 0) eT[(size_t)k * nbmax + n] = e;
-    long long lines = (long long)td0 * td1;
-    long long bandsz = lines * Zp;
-    for (long long i = threadIdx.x; i < 8 * lines * Zp; i += blockDim.x) {
+    const long long lines = (long long)td0 * td1;
+    const long long bandsz = lines * Zp;
+    for (long long i = threadIdx.x; i < bandsz; i += blockDim.x) {
         int z = (int)(i % Zp);
-        long long xy = (i / Zp) % lines;
-        int s = (int)(i / (Zp * lines));
-        int zz = z + s;
-        double2 v = (zz < td2) ? T[xy * td2 + zz] : make_double2(0.0, 0.0);
+        long long xy = i / Zp;
+        double2 v = (z < td2) ? T[xy * td2 + z] : make_double2(0.0, 0.0);
         __nv_bfloat16 sr[NPL], si[NPL];
         slice4(v.x, e, sr);
         slice4(v.y, e, si);
+#pragma unroll
         for (int p = 0; p < NPL; ++p) {
-            // rest index ((slot*8 + s)*4 + p)*2 + ri, then [n][X][Y][Zp]
-            long long rr = (((long long)slot * 8 + s) * NPL + p) * 2;
-            Tp[((rr + 0) * nbmax + n) * bandsz + xy * Zp + z] = sr[p];
-            Tp[((rr + 1) * nbmax + n) * bandsz + xy * Zp + z] = si[p];
+            long long R0 = ((long long)slot * NPL + p) * ZT_NPART;
+            __nv_bfloat16 part[ZT_NPART] = {sr[p], si[p], __hneg(si[p]), sr[p]};
+#pragma unroll
+            for (int q = 0; q < ZT_NPART; ++q) Tp[((R0 + q) * nbmax + n) * bandsz + i] = part[q];
         }
     }
 }
@@ -126,40 +140,36 @@ struct ZPairInfo { int pair; int g0x, g0y, g0z; };
 struct ZParams {
     const ZTile *tiles;
     int ntiles;
-    const int *wxyz;              // [nw][3] shifts W
+    const int4 *wxyz;             // [nw] shift W (x, y, z) and its z phase (w)
     const ZPairInfo *pinfo;       // [nk][nk] by (k, k')
     const PairDesc *pairs;
     const int *gtab;              // [nq][ax][ay][az] aux index or -1
     int ax0, ay0, az0, ad0, ad1, ad2;
     const int *rowk, *rowm;       // rows of A (k', m)
     const int *aexp, *eT;         // row exponents, [k][n] band exponents
-    const int *kslot;             // k -> slot of its T copies
-    const int *line_x, *line_y;   // absolute G1 (x, y) of every line
+    const int *kslot;             // k -> slot of its T slices
+    const int4 *segs;             // [phase][segment] (x, y, z0, -)
+    int nsegp_max;
+    int nchunk[ZT_NPH];           // 64-K chunks per K half, per phase
     double2 *Z;
     long long RSc;
-    int nmt, nk, R, Rpad, H, KH, nbmax, gz0, tlo0, tlo1, tlo2;
+    int nmt, nk, R, Rpad, Kh, nbmax, tlo0, tlo1, tlo2;
     double rs;                    // Omega^{-1/2}
     int *err;
 };
 
-constexpr int ZT_BM = 128;
-constexpr int ZT_A_PLANE = 128 * 64 * 2;   // 16 KB
-constexpr int ZT_GROUP = 4;                // 64-K chunks per exact group (256)
-constexpr int ZT_STAGES = 2;
-constexpr int ZT_EPI = 8;
-
-// warp 0: TMA; warp 1: MMA; warps 2..9: epilogue (lane quarter, column half)
+// warp 0: TMA; warp 1: MMA; warps 2..9: epilogue (lane quarter, real/imaginary output)
 template <int NB>
 __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                       const __grid_constant__ CUtensorMap tmT, ZParams p) {
-    constexpr int LINEB = NB * 32;                       // one line box: NB rows x 16 z
-    constexpr int B_PLANE = 4 * LINEB;                   // four lines per chunk
+    constexpr int N = 2 * NB;                            // real and imaginary output columns
+    constexpr int SEGB = N * 16;                         // one segment: N rows x 8 z
+    constexpr int B_PLANE = 8 * SEGB;                    // eight segments per 64-K chunk
     constexpr int STAGE = NPL * (ZT_A_PLANE + B_PLANE);
-    constexpr int CW = NB / 2;
     extern __shared__ __align__(1024) unsigned char zt_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(zt_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
-    __shared__ uint64_t full_bar[ZT_STAGES], empty_bar[ZT_STAGES], tfull_bar[2], tempty_bar[2];
+    __shared__ uint64_t full_bar[ZT_STAGES], empty_bar[ZT_STAGES], tfull_bar, tempty_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -168,10 +178,8 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&tfull_bar[b], 1);
-            mbar_init(&tempty_bar[b], ZT_EPI);
-        }
+        mbar_init(&tfull_bar, 1);
+        mbar_init(&tempty_bar, ZT_EPI);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -180,7 +188,6 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
     __syncthreads();
     tc_fence_after();
     uint32_t tmem = tmem_slot;
-    const int nchunk = 2 * p.H;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -188,28 +195,29 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             uint32_t ph = 0;
             int issued = 0;
             for (int t = blockIdx.x; t < p.ntiles && !abort_flag; t += gridDim.x) {
-                ZTile tl = p.tiles[t];
-                int Wx = p.wxyz[3 * tl.w], Wy = p.wxyz[3 * tl.w + 1], Wz = p.wxyz[3 * tl.w + 2];
-                int zs = Wz + p.gz0 - p.tlo2;            // >= 0
-                int shift = zs & 7, z0 = zs - shift;
-                int slot = p.kslot[tl.k];
+                const ZTile tl = p.tiles[t];
+                const int4 W = p.wxyz[tl.w];
+                const int phz = W.w, nch = p.nchunk[phz];
+                const int slot = p.kslot[tl.k];
+                const int4 *sg = p.segs + (size_t)phz * p.nsegp_max;
                 bool stop = false;
-                for (int c = 0; c < nchunk; ++c) {
+                for (int c = 0; c < 2 * nch; ++c) {
                     if (!mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma)) { stop = true; break; }
-                    int ri = c >= p.H;
-                    int cl = ri ? c - p.H : c;
-                    int ax = (ri ? p.KH : 0) + cl * 64;
+                    const int h = c >= nch, cl = h ? c - nch : c;
                     unsigned char *st = stages + (size_t)s * STAGE;
                     mbar_expect_tx(&full_bar[s], STAGE);
-                    for (int pl = 0; pl < NPL; ++pl) {
-                        tma_load_2d(saddr(st + pl * ZT_A_PLANE), &tmA, &full_bar[s], ax, pl * 2 * p.Rpad + tl.mrow);
-                        int rest = ((slot * 8 + shift) * NPL + pl) * 2 + ri;
-                        for (int j = 0; j < 4; ++j) {
-                            int li = cl * 4 + j;
-                            int X = Wx + p.line_x[li] - p.tlo0, Y = Wy + p.line_y[li] - p.tlo1;
-                            tma_load_5d(saddr(st + NPL * ZT_A_PLANE + pl * B_PLANE + j * LINEB), &tmT, &full_bar[s], z0, Y,
-                                        X, tl.nblk * NB, rest);
-                        }
+#pragma unroll
+                    for (int pl = 0; pl < NPL; ++pl)
+                        tma_load_2d(saddr(st + pl * ZT_A_PLANE), &tmA, &full_bar[s], h * p.Kh + cl * 64,
+                                    (phz * NPL + pl) * p.Rpad + tl.mrow);
+#pragma unroll 1
+                    for (int j = 0; j < 8; ++j) {
+                        const int4 sj = sg[cl * 8 + j];
+                        const int X = W.x + sj.x - p.tlo0, Y = W.y + sj.y - p.tlo1, Z = W.z + sj.z - p.tlo2;
+#pragma unroll
+                        for (int pl = 0; pl < NPL; ++pl)
+                            tma_load_5d(saddr(st + NPL * ZT_A_PLANE + pl * B_PLANE + j * SEGB), &tmT, &full_bar[s], Z, Y, X,
+                                        tl.nblk * NB, (slot * NPL + pl) * ZT_NPART + 2 * h);
                     }
                     ++issued;
                     if (++s == ZT_STAGES) { s = 0; ph ^= 1; }
@@ -223,111 +231,97 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
     } else if (warp == 1) {
         if (lane == 0) {
             int s = 0;
-            uint32_t ph = 0;
-            int buf = 0;
-            uint32_t buf_ph[2] = {0, 0};
-            constexpr uint32_t idesc = idesc_bf16(ZT_BM, NB);
+            uint32_t ph = 0, eph = 0;
+            constexpr uint32_t idesc = idesc_bf16(ZT_BM, N);
             bool ok = true;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+                const int nchunk = 2 * p.nchunk[p.wxyz[p.tiles[t].w].w];
                 for (int g0 = 0; g0 < nchunk && ok; g0 += ZT_GROUP) {
-                    if (!mbar_wait(&tempty_bar[buf], buf_ph[buf] ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
+                    if (!mbar_wait(&tempty_bar, eph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                     tc_fence_after();
-                    uint32_t dt = tmem + buf * (NPL * NB);
-                    int started = 0;
                     for (int c = g0; c < min(nchunk, g0 + ZT_GROUP); ++c) {
                         if (!mbar_wait(&full_bar[s], ph, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                         tc_fence_after();
                         unsigned char *st = stages + (size_t)s * STAGE;
-                        uint32_t a0 = saddr(st), b0 = saddr(st + NPL * ZT_A_PLANE);
-                        for (int tm = 0; tm < NTERM; ++tm) {
-                            int w = kIW[tm];
-                            uint64_t da = desc_sw128(a0 + kIA[tm] * ZT_A_PLANE);
+                        const uint32_t a0 = saddr(st), b0 = saddr(st + NPL * ZT_A_PLANE);
+                        const bool first = c == g0;
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                uint64_t db = desc_sw32(b0 + kIB[tm] * B_PLANE + j * LINEB);
-                                umma_bf16(dt + w * NB, da + 2 * j, db, idesc, ((started >> w) & 1) ? 1u : 0u);
-                                started |= 1 << w;
+                        for (int tm = 0; tm < NTERM; ++tm) {
+                            const uint64_t da = desc_sw128(a0 + term_a(tm) * ZT_A_PLANE);
+                            const bool lead = tm == 0 || tm == 1 || tm == 3 || tm == 6;
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                // K step ks: segments 2 ks and 2 ks + 1
+                                const uint64_t db = desc_ns(b0 + term_b(tm) * B_PLANE + 2 * ks * SEGB, SEGB, 128);
+                                umma_bf16(tmem + term_w(tm) * N, da + 2 * ks, db, idesc, (first && lead && ks == 0) ? 0u : 1u);
                             }
                         }
                         umma_commit(&empty_bar[s]);
                         if (++s == ZT_STAGES) { s = 0; ph ^= 1; }
                     }
                     if (!ok) break;
-                    umma_commit(&tfull_bar[buf]);
-                    buf_ph[buf] ^= 1;
-                    buf ^= 1;
+                    umma_commit(&tfull_bar);
+                    eph ^= 1;
                 }
             }
         }
     } else {
-        int e = warp - 2;
-        int quarter = warp % 4, half = e / 4;
-        int buf = 0;
-        uint32_t buf_ph[2] = {0, 0};
+        const int e = warp - 2;
+        const int quarter = warp % 4, half = e / 4;   // half 0: real output columns, 1: imaginary
+        uint32_t eph = 0;
         bool ok = true;
-        int ngroups = (nchunk + ZT_GROUP - 1) / ZT_GROUP;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-            ZTile tl = p.tiles[t];
-            float hi[CW], lo[CW];
+            const ZTile tl = p.tiles[t];
+            const int4 W = p.wxyz[tl.w];
+            const int ngroups = (2 * p.nchunk[W.w] + ZT_GROUP - 1) / ZT_GROUP;
+            float hi[NB], lo[NB];
 #pragma unroll
-            for (int j = 0; j < CW; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int j = 0; j < NB; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
             for (int g = 0; g < ngroups; ++g) {
-                if (!mbar_wait(&tfull_bar[buf], buf_ph[buf], &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
+                if (!mbar_wait(&tfull_bar, eph, &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
                 tc_fence_after();
-                uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (NPL * NB) + half * CW;
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + half * NB;
 #pragma unroll
-                for (int c0 = 0; c0 < CW; c0 += 8) {
-                    uint32_t x[8], y[8];
-                    float cc[8];
-                    tmem_ld8(tb + 3 * NB + c0, x);
-                    tmem_ld8(tb + 2 * NB + c0, y);
+                for (int c0 = 0; c0 < NB; c0 += 8) {
+                    uint32_t a0[8], a1[8], a2[8], a3[8];
+                    tmem_ld8(tb + 0 * N + c0, a0);
+                    tmem_ld8(tb + 1 * N + c0, a1);
+                    tmem_ld8(tb + 2 * N + c0, a2);
+                    tmem_ld8(tb + 3 * N + c0, a3);
                     tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) cc[j] = fmaf(__uint_as_float(x[j]), 0x1p-8f, __uint_as_float(y[j]));
-                    tmem_ld8(tb + 1 * NB + c0, x);
-                    tmem_ld8(tb + 0 * NB + c0, y);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float c1 = fmaf(cc[j], 0x1p-8f, __uint_as_float(x[j]));
-                        float a0 = __uint_as_float(y[j]);
-                        float s2 = hi[c0 + j] + a0;
-                        float bb = s2 - hi[c0 + j];
-                        float er = (hi[c0 + j] - (s2 - bb)) + (a0 - bb);
-                        hi[c0 + j] = s2;
-                        lo[c0 + j] += er + c1 * 0x1p-8f;
+                    if (c0 + 8 >= NB) {   // everything read: hand the accumulators back to the MMA warp
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tempty_bar);
                     }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        class_accumulate(__uint_as_float(a0[j]), __uint_as_float(a1[j]), __uint_as_float(a2[j]),
+                                         __uint_as_float(a3[j]), 1.0f, hi[c0 + j], lo[c0 + j]);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty_bar[buf]);
-                buf_ph[buf] ^= 1;
-                buf ^= 1;
+                eph ^= 1;
             }
             if (!ok) break;
-            int row = tl.mrow + quarter * 32 + lane;
-            bool im = row >= p.Rpad;
-            int r = im ? row - p.Rpad : row;
+            const int r = tl.mrow + quarter * 32 + lane;
             if (r < p.R) {
-                int kp = p.rowk[r], m = p.rowm[r];
-                ZPairInfo pi = p.pinfo[(size_t)tl.k * p.nk + kp];
+                const int kp = p.rowk[r], m = p.rowm[r];
+                const ZPairInfo pi = p.pinfo[(size_t)tl.k * p.nk + kp];
                 if (pi.pair >= 0) {
                     const PairDesc pr = p.pairs[pi.pair];
-                    int Gx = p.wxyz[3 * tl.w] + pi.g0x - p.ax0, Gy = p.wxyz[3 * tl.w + 1] + pi.g0y - p.ay0,
-                        Gz = p.wxyz[3 * tl.w + 2] + pi.g0z - p.az0;
+                    const int Gx = W.x + pi.g0x - p.ax0, Gy = W.y + pi.g0y - p.ay0, Gz = W.z + pi.g0z - p.az0;
                     int g = -1;
                     if (Gx >= 0 && Gx < p.ad0 && Gy >= 0 && Gy < p.ad1 && Gz >= 0 && Gz < p.ad2)
                         g = p.gtab[(((size_t)pr.qslot * p.ad0 + Gx) * p.ad1 + Gy) * p.ad2 + Gz];
                     if (g >= 0) {
-                        int ea = p.aexp[row] - 16;
+                        const int ea = p.aexp[r] - 16;
+                        const int *eTk = p.eT + (size_t)tl.k * p.nbmax;
 #pragma unroll
-                        for (int j = 0; j < CW; ++j) {
-                            int n = tl.nblk * NB + half * CW + j;
+                        for (int j = 0; j < NB; ++j) {
+                            const int n = tl.nblk * NB + j;
                             if (n < pr.nb) {
-                                double v = ldexp((double)hi[j] + (double)lo[j], ea + p.eT[(size_t)tl.k * p.nbmax + n]) * p.rs;
+                                double v = scale2((double)hi[j] + (double)lo[j], ea + eTk[n]) * p.rs;
                                 long long col = pr.col0 + (long long)m * pr.nb + n;
-                                double *dst = reinterpret_cast<double *>(p.Z + col * p.RSc + p.nmt + g);
-                                dst[im ? 1 : 0] = v;
+                                reinterpret_cast<double *>(p.Z + col * p.RSc + p.nmt + g)[half] = v;
                             }
                         }
                     }
@@ -343,14 +337,25 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
     }
 }
 
+// band block: a multiple of 8 (the output width 2 NB is a multiple of 16),
+// at most 40 (two pipeline stages in shared memory), fewest padded bands
+int pick_nb(int nb_max) {
+    int best = 8, best_tot = 1 << 30;
+    for (int nb = 8; nb <= 40; nb += 8) {
+        int tot = (nb_max + nb - 1) / nb * nb;
+        if (tot < best_tot || (tot == best_tot && nb > best)) { best = nb; best_tot = tot; }
+    }
+    return best;
+}
+
 }  // namespace
 
-// Host side: geometry, slices, shift lists, tiles and launch for one batch.
+// Host side: segment grid, slices, shift lists, tiles and launch for one batch.
 int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     cudaStream_t st = ctx->stream;
     int rc;
     const int nk = ctx->nk;
-    // ---- G1 box and lines over every k' plane-wave list
+    // ---- G1 lines (x, y) with their z ranges over every k' plane-wave list
     int gmin[3] = {1 << 29, 1 << 29, 1 << 29}, gmax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
     for (auto &k : ctx->kp)
         for (size_t i = 0; i < k.G.size(); ++i) {
@@ -358,32 +363,60 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
             gmin[x] = std::min(gmin[x], k.G[i]);
             gmax[x] = std::max(gmax[x], k.G[i]);
         }
-    int Bx = gmax[0] - gmin[0] + 1, By = gmax[1] - gmin[1] + 1, Bz = gmax[2] - gmin[2] + 1;
-    if (Bz > 16) return set_err(ctx, HFX_EUNSUPPORTED, "plane-wave sphere wider than 16 along b_3");
-    std::vector<int> line_of((size_t)Bx * By, -1), lx, ly;
+    if (gmin[0] > gmax[0]) return HFX_OK;
+    const int Bx = gmax[0] - gmin[0] + 1, By = gmax[1] - gmin[1] + 1;
+    std::vector<int> zlo((size_t)Bx * By, 1 << 29), zhi((size_t)Bx * By, -(1 << 29));
     for (auto &k : ctx->kp)
-        for (size_t i = 0; i < k.G.size(); i += 3) line_of[(size_t)(k.G[i] - gmin[0]) * By + (k.G[i + 1] - gmin[1])] = 0;
+        for (size_t i = 0; i + 2 < k.G.size(); i += 3) {
+            size_t b = (size_t)(k.G[i] - gmin[0]) * By + (k.G[i + 1] - gmin[1]);
+            zlo[b] = std::min(zlo[b], k.G[i + 2]);
+            zhi[b] = std::max(zhi[b], k.G[i + 2]);
+        }
+    std::vector<int> line_of((size_t)Bx * By, -1), lx, ly, lzlo, lzhi;
     for (int x = 0; x < Bx; ++x)
-        for (int y = 0; y < By; ++y)
-            if (line_of[(size_t)x * By + y] == 0) {
-                line_of[(size_t)x * By + y] = (int)lx.size();
-                lx.push_back(gmin[0] + x);
-                ly.push_back(gmin[1] + y);
-            }
-    int nL = (int)lx.size(), nLp = (nL + 3) / 4 * 4;
-    while ((int)lx.size() < nLp) { lx.push_back(lx[0]); ly.push_back(ly[0]); }
-    int KH = nLp * 16, H = nLp / 4;
-    // ---- rows (k', m) of every k' that some pair of the batch uses
+        for (int y = 0; y < By; ++y) {
+            size_t b = (size_t)x * By + y;
+            if (zlo[b] > zhi[b]) continue;
+            line_of[b] = (int)lx.size();
+            lx.push_back(gmin[0] + x);
+            ly.push_back(gmin[1] + y);
+            lzlo.push_back(zlo[b]);
+            lzhi.push_back(zhi[b]);
+        }
+    const int nL = (int)lx.size();
+    // segment grid per z phase: segments of a line start at z0 = ph (mod 8)
+    std::vector<int> segstart((size_t)ZT_NPH * nL), segz0((size_t)ZT_NPH * nL), nseg(ZT_NPH);
+    std::vector<std::vector<int4>> segs(ZT_NPH);
+    for (int ph = 0; ph < ZT_NPH; ++ph) {
+        for (int l = 0; l < nL; ++l) {
+            int z0 = lzlo[l] - (((lzlo[l] - ph) % 8) + 8) % 8;
+            segstart[(size_t)ph * nL + l] = (int)segs[ph].size();
+            segz0[(size_t)ph * nL + l] = z0;
+            for (int z = z0; z <= lzhi[l]; z += 8) segs[ph].push_back(make_int4(lx[l], ly[l], z, 0));
+        }
+        nseg[ph] = (int)segs[ph].size();
+    }
+    int nsegp_max = 0;
+    for (int ph = 0; ph < ZT_NPH; ++ph) nsegp_max = std::max(nsegp_max, (nseg[ph] + 7) / 8 * 8);
+    const int Kh = nsegp_max * 8;
+    std::vector<int4> segtab((size_t)ZT_NPH * nsegp_max);
+    int nchunk[ZT_NPH];
+    for (int ph = 0; ph < ZT_NPH; ++ph) {
+        nchunk[ph] = (nseg[ph] + 7) / 8;
+        for (int s2 = 0; s2 < nsegp_max; ++s2)
+            segtab[(size_t)ph * nsegp_max + s2] = s2 < nseg[ph] ? segs[ph][s2] : segs[ph][0];   // padding: any valid box
+    }
+    // ---- rows (k', m) of every k'
     std::vector<int> rowk, rowm, rowbase(nk, -1);
     for (int kp = 0; kp < nk; ++kp) {
         rowbase[kp] = (int)rowk.size();
         for (int m = 0; m < ctx->kp[kp].no; ++m) { rowk.push_back(kp); rowm.push_back(m); }
     }
-    int R = (int)rowk.size();
+    const int R = (int)rowk.size();
     if (R == 0) return HFX_OK;
-    int Rpad = (R + 127) / 128 * 128;
-    int NBt = std::min(64, (in.nb_max + 15) / 16 * 16);
-    int nblk = (in.nb_max + NBt - 1) / NBt;
+    const int Rpad = (R + ZT_BM - 1) / ZT_BM * ZT_BM;
+    const int NBt = pick_nb(in.nb_max);
+    const int nblk = (in.nb_max + NBt - 1) / NBt;
     // ---- aux lookup tables over the batch's q
     int amin[3] = {1 << 29, 1 << 29, 1 << 29}, amax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
     for (int iq : in.qs)
@@ -397,7 +430,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         if (amin[x] > amax[x]) amin[x] = amax[x] = 0;
         ad[x] = amax[x] - amin[x] + 1;
     }
-    int nq = (int)in.qs.size();
+    const int nq = (int)in.qs.size();
     std::vector<int> gtab((size_t)nq * ad[0] * ad[1] * ad[2], -1);
     for (int s = 0; s < nq; ++s) {
         const std::vector<int> &G = ctx->qp[in.qs[s]].G;
@@ -411,93 +444,92 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         pinfo[(size_t)pr.ik * nk + pr.ikp] = ZPairInfo{i, pr.g0[0], pr.g0[1], pr.g0[2]};
     }
     // W = G - G0 lies in [amin, amax + 1]
-    int wd[3] = {ad[0] + 1, ad[1] + 1, ad[2] + 1};
-    size_t wvol = (size_t)wd[0] * wd[1] * wd[2];
-    int nmt_tiles = 2 * Rpad / ZT_BM;
-    std::vector<int> wxyz;
+    const int wd[3] = {ad[0] + 1, ad[1] + 1, ad[2] + 1};
+    const size_t wvol = (size_t)wd[0] * wd[1] * wd[2];
+    const int nmtile = Rpad / ZT_BM;
+    std::vector<int4> wxyz;
     std::vector<ZTile> tiles;
     std::vector<unsigned char> need;
     std::vector<int> kslot(nk, -1);
     int nslot = 0;
     for (int ik : in.kset) {
         kslot[ik] = nslot++;
-        need.assign(wvol * nmt_tiles, 0);
-        for (int i = 0; i < (int)in.pairs.size(); ++i) {
-            const PairDesc &pr = in.pairs[i];
+        need.assign(wvol * nmtile, 0);
+        for (const PairDesc &pr : in.pairs) {
             if (pr.ik != ik || pr.no == 0) continue;
             const std::vector<int> &G = ctx->qp[pr.iq].G;
-            int r0 = rowbase[pr.ikp], r1 = r0 + pr.no;
-            int t0 = r0 / ZT_BM, t1 = (r1 - 1) / ZT_BM;
+            const int t0 = rowbase[pr.ikp] / ZT_BM, t1 = (rowbase[pr.ikp] + pr.no - 1) / ZT_BM;
             for (size_t g = 0; g < G.size() / 3; ++g) {
                 int w0 = G[3 * g] - pr.g0[0] - amin[0], w1 = G[3 * g + 1] - pr.g0[1] - amin[1], w2 = G[3 * g + 2] - pr.g0[2] - amin[2];
                 size_t wi = ((size_t)w0 * wd[1] + w1) * wd[2] + w2;
-                for (int t = t0; t <= t1; ++t) {
-                    need[wi * nmt_tiles + t] = 1;                    // real rows
-                    need[wi * nmt_tiles + t + Rpad / ZT_BM] = 1;     // imaginary rows
-                }
+                for (int t = t0; t <= t1; ++t) need[wi * nmtile + t] = 1;
             }
         }
         for (size_t wi = 0; wi < wvol; ++wi) {
             bool any = false;
-            for (int t = 0; t < nmt_tiles; ++t) any |= need[wi * nmt_tiles + t] != 0;
+            for (int t = 0; t < nmtile; ++t) any |= need[wi * nmtile + t] != 0;
             if (!any) continue;
-            int widx = (int)(wxyz.size() / 3);
-            int w2 = (int)(wi % wd[2]), w1 = (int)((wi / wd[2]) % wd[1]), w0 = (int)(wi / ((size_t)wd[1] * wd[2]));
-            wxyz.push_back(w0 + amin[0]);
-            wxyz.push_back(w1 + amin[1]);
-            wxyz.push_back(w2 + amin[2]);
-            for (int t = 0; t < nmt_tiles; ++t)
-                if (need[wi * nmt_tiles + t])
+            const int widx = (int)wxyz.size();
+            const int w2 = (int)(wi % wd[2]), w1 = (int)((wi / wd[2]) % wd[1]), w0 = (int)(wi / ((size_t)wd[1] * wd[2]));
+            const int Wz = w2 + amin[2];
+            // z phase: the T z index of every segment start is a multiple of 8
+            wxyz.push_back(make_int4(w0 + amin[0], w1 + amin[1], Wz, (((in.tlo[2] - Wz) % 8) + 8) % 8));
+            for (int t = 0; t < nmtile; ++t)
+                if (need[wi * nmtile + t])
                     for (int b = 0; b < nblk; ++b) tiles.push_back(ZTile{ik, widx, t * ZT_BM, b});
         }
     }
     if (tiles.empty()) return HFX_OK;
     // ---- device buffers (scratch s_zipw)
     const int Zp = (in.tdim[2] + 7) / 8 * 8;
-    size_t bandsz = (size_t)in.tdim[0] * in.tdim[1] * Zp;
-    size_t tp_elems = (size_t)nslot * 8 * NPL * 2 * in.nb_max * bandsz;
-    size_t a_elems = (size_t)NPL * 2 * Rpad * 2 * KH;
+    const size_t bandsz = (size_t)in.tdim[0] * in.tdim[1] * Zp;
+    const size_t tp_elems = (size_t)nslot * NPL * ZT_NPART * in.nb_max * bandsz;
+    const size_t a_elems = (size_t)ZT_NPH * NPL * Rpad * 2 * Kh;
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
-    size_t o_tp = place(tp_elems * 2), o_a = place(a_elems * 2), o_aexp = place((size_t)2 * Rpad * 4),
-           o_eT = place((size_t)nk * in.nb_max * 4), o_rowk = place((size_t)R * 4), o_rowm = place((size_t)R * 4),
-           o_line = place((size_t)Bx * By * 4), o_lx = place((size_t)nLp * 4), o_ly = place((size_t)nLp * 4),
-           o_gtab = place(gtab.size() * 4), o_pinfo = place(pinfo.size() * sizeof(ZPairInfo)),
-           o_w = place(wxyz.size() * 4), o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4);
+    const size_t o_tp = place(tp_elems * 2), o_a = place(a_elems * 2), o_aexp = place((size_t)Rpad * 4),
+                 o_eT = place((size_t)nk * in.nb_max * 4), o_rowk = place((size_t)R * 4), o_rowm = place((size_t)R * 4),
+                 o_line = place(line_of.size() * 4), o_sst = place(segstart.size() * 4), o_sz0 = place(segz0.size() * 4),
+                 o_seg = place(segtab.size() * sizeof(int4)), o_gtab = place(gtab.size() * 4),
+                 o_pinfo = place(pinfo.size() * sizeof(ZPairInfo)), o_w = place(wxyz.size() * sizeof(int4)),
+                 o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4);
     if ((rc = scratch_reserve(ctx, ctx->s_zipw, off))) return rc;
     char *b = reinterpret_cast<char *>(ctx->s_zipw.p);
     auto up = [&](size_t o, const void *src, size_t bytes) {
         return cuda_check(ctx, cudaMemcpyAsync(b + o, src, bytes, cudaMemcpyHostToDevice, st), "zipw tables");
     };
     if ((rc = up(o_rowk, rowk.data(), R * 4)) || (rc = up(o_rowm, rowm.data(), R * 4)) ||
-        (rc = up(o_line, line_of.data(), line_of.size() * 4)) || (rc = up(o_lx, lx.data(), nLp * 4)) ||
-        (rc = up(o_ly, ly.data(), nLp * 4)) || (rc = up(o_gtab, gtab.data(), gtab.size() * 4)) ||
-        (rc = up(o_pinfo, pinfo.data(), pinfo.size() * sizeof(ZPairInfo))) || (rc = up(o_w, wxyz.data(), wxyz.size() * 4)) ||
+        (rc = up(o_line, line_of.data(), line_of.size() * 4)) || (rc = up(o_sst, segstart.data(), segstart.size() * 4)) ||
+        (rc = up(o_sz0, segz0.data(), segz0.size() * 4)) || (rc = up(o_seg, segtab.data(), segtab.size() * sizeof(int4))) ||
+        (rc = up(o_gtab, gtab.data(), gtab.size() * 4)) ||
+        (rc = up(o_pinfo, pinfo.data(), pinfo.size() * sizeof(ZPairInfo))) ||
+        (rc = up(o_w, wxyz.data(), wxyz.size() * sizeof(int4))) ||
         (rc = up(o_tiles, tiles.data(), tiles.size() * sizeof(ZTile))) || (rc = up(o_kslot, kslot.data(), nk * 4)))
         return rc;
     __nv_bfloat16 *Tp = reinterpret_cast<__nv_bfloat16 *>(b + o_tp), *A = reinterpret_cast<__nv_bfloat16 *>(b + o_a);
     int *aexp = reinterpret_cast<int *>(b + o_aexp), *eT = reinterpret_cast<int *>(b + o_eT);
-    cudaMemsetAsync(aexp, 0, (size_t)2 * Rpad * 4, st);
+    cudaMemsetAsync(aexp, 0, (size_t)Rpad * 4, st);
     cudaMemsetAsync(A, 0, a_elems * 2, st);
     c_slices_kernel<<<R, 256, 0, st>>>(in.d_ck, in.d_Gk, in.d_npw, reinterpret_cast<int *>(b + o_rowk),
                                        reinterpret_cast<int *>(b + o_rowm), reinterpret_cast<int *>(b + o_line), gmin[0], gmin[1],
-                                       gmin[2], By, KH, Rpad, A, aexp);
+                                       By, nL, reinterpret_cast<int *>(b + o_sst), reinterpret_cast<int *>(b + o_sz0), Kh, Rpad, A,
+                                       aexp);
     t_slices_kernel<<<dim3(in.nb_max, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], Zp, in.nb_max,
                                                          reinterpret_cast<int *>(b + o_kslot), Tp, eT);
     if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw slices"))) return rc;
     // ---- tensor maps
     CUtensorMap mA, mT;
-    if ((rc = make_map_2d(ctx, &mA, A, (long long)NPL * 2 * Rpad, 2LL * KH, ZT_BM))) return rc;
+    if ((rc = make_map_2d(ctx, &mA, A, (long long)ZT_NPH * NPL * Rpad, 2LL * Kh, ZT_BM))) return rc;
     unsigned long long dims[5] = {(unsigned long long)Zp, (unsigned long long)in.tdim[1], (unsigned long long)in.tdim[0],
-                                  (unsigned long long)in.nb_max, (unsigned long long)nslot * 8 * NPL * 2};
+                                  (unsigned long long)in.nb_max, (unsigned long long)nslot * NPL * ZT_NPART};
     unsigned long long strides[4] = {(unsigned long long)Zp * 2, (unsigned long long)Zp * in.tdim[1] * 2,
                                      (unsigned long long)bandsz * 2, (unsigned long long)bandsz * in.nb_max * 2};
-    unsigned int box[5] = {16, 1, 1, (unsigned int)NBt, 1};
-    if ((rc = make_map_5d(ctx, &mT, Tp, dims, strides, box, 32))) return rc;
+    unsigned int box[5] = {8, 1, 1, (unsigned int)NBt, 2};
+    if ((rc = make_map_5d(ctx, &mT, Tp, dims, strides, box, 0))) return rc;
     ZParams p;
     p.tiles = reinterpret_cast<ZTile *>(b + o_tiles);
     p.ntiles = (int)tiles.size();
-    p.wxyz = reinterpret_cast<int *>(b + o_w);
+    p.wxyz = reinterpret_cast<int4 *>(b + o_w);
     p.pinfo = reinterpret_cast<ZPairInfo *>(b + o_pinfo);
     p.pairs = in.d_pairs;
     p.gtab = reinterpret_cast<int *>(b + o_gtab);
@@ -508,34 +540,42 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     p.aexp = aexp;
     p.eT = eT;
     p.kslot = reinterpret_cast<int *>(b + o_kslot);
-    p.line_x = reinterpret_cast<int *>(b + o_lx);
-    p.line_y = reinterpret_cast<int *>(b + o_ly);
+    p.segs = reinterpret_cast<int4 *>(b + o_seg);
+    p.nsegp_max = nsegp_max;
+    for (int ph = 0; ph < ZT_NPH; ++ph) p.nchunk[ph] = nchunk[ph];
     p.Z = in.d_Z;
     p.RSc = in.RSc;
     p.nmt = ctx->nmt;
     p.nk = nk;
     p.R = R;
     p.Rpad = Rpad;
-    p.H = H;
-    p.KH = KH;
+    p.Kh = Kh;
     p.nbmax = in.nb_max;
-    p.gz0 = gmin[2];
     p.tlo0 = in.tlo[0]; p.tlo1 = in.tlo[1]; p.tlo2 = in.tlo[2];
     p.rs = 1.0 / sqrt(ctx->omega);
     p.err = ctx->d_err;
-    int grid = std::min<int>(num_sms(), p.ntiles);
+    const int grid = std::min<int>(num_sms(), p.ntiles);
+    // the whole opt-in shared memory: the pipeline stages plus a guard region
+    // past the last stage that no descriptor of the B operand can reach beyond
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     auto go = [&](auto kern, int nb) {
-        size_t smem = (size_t)ZT_STAGES * NPL * (ZT_A_PLANE + 4 * nb * 32) + 1024;
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, kern);
+        size_t smem = std::max<size_t>((size_t)ZT_STAGES * NPL * (ZT_A_PLANE + 8 * 2 * nb * 16) + 1024,
+                                       (size_t)smem_max - fa.sharedSizeBytes);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (in.ev_gemm0) cudaEventRecord(in.ev_gemm0, st);
         kern<<<grid, 64 + 32 * ZT_EPI, smem, st>>>(mA, mT, p);
         if (in.ev_gemm1) cudaEventRecord(in.ev_gemm1, st);
     };
     switch (NBt) {
+    case 8: go(zipw_tc_kernel<8>, 8); break;
     case 16: go(zipw_tc_kernel<16>, 16); break;
+    case 24: go(zipw_tc_kernel<24>, 24); break;
     case 32: go(zipw_tc_kernel<32>, 32); break;
-    case 48: go(zipw_tc_kernel<48>, 48); break;
-    default: go(zipw_tc_kernel<64>, 64); break;
+    default: go(zipw_tc_kernel<40>, 40); break;
     }
     return cuda_check(ctx, cudaGetLastError(), "zipw tensor-core kernel");
 }

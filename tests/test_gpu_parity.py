@@ -90,12 +90,15 @@ def test_split_matches_oracle(name):
         assert np.abs(V[k] - V[k].conj().T).max() <= 2 * TOL_SPLIT_ABS
 
 
-# the sliced build computes the interstitial projections on the tensor cores:
-# each operand line keeps 33 bits relative to its largest element (a band of
-# T_n over the whole step-function box), so a pair whose projections are small
-# compared with those maxima sees a few 1e-9 relative; the bar is 5e-9 of the
-# pair's largest projection (the MT part stays FP64).
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("sliced", 5e-9)])
+# In the sliced build every projection is a slice product: each operand line
+# is kept to 2^-32 of its largest element, so one product over K terms is off
+# by up to ~K 2^-32 of (largest |a|)(largest |b|).  Z^MT is one product
+# (K = 50); Z^IPW is a product with T_n, which is itself a product of Theta
+# and c (K ~ 500) and is re-sliced against the largest |T_n| of the whole box.
+# Relative to the pair's largest projection, which is much smaller than those
+# operand maxima, this gives a few 1e-9 (measured up to 5e-9 for Z^IPW, 1e-9
+# for Z^MT); the bar is 1e-8.
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("sliced", 1e-8)])
 def test_projections_match_oracle(precision, tol):
     s = S.make_system(1, mesh=(2, 2, 2), nb=6, no=3)
     o = O.Oracle(s)
