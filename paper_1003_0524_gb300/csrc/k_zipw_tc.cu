@@ -12,10 +12,11 @@
 // product with the real and imaginary outputs side by side in N):
 //   A row (k', m) = [ Re C | Im C ]                       (128-byte swizzle, 2-D TMA)
 //   B columns     = [ T_r ; -T_i ] (real out), [ T_i ; T_r ] (imag out)
-// B is loaded per segment as one 8-z box of both output blocks (no swizzle,
-// 5-D TMA straight from the sliced T box).  A TMA box must start on a 16-byte
-// boundary in z, so the segment grid of the lines is aligned per z phase of W:
-// the C slices come in eight phase variants, T in one copy.
+// The sliced T box is stored in blocks of 8 z with both parts of an output
+// block and all bands of a band block contiguous, so the B operand of one
+// segment is a single 1-D bulk copy (no swizzle).  The segments of the lines
+// are aligned to those z blocks per z phase of W: the C slices come in eight
+// phase variants, T in one copy.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -92,19 +93,23 @@ __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int
 }
 
 // ------------------------------------------------------------- T slices
-// Grid (n, k): exponent of band n of T_k over the box, then the four parts
-// Tp[k][p][part][n][X][Y][z] = slice_p(Re T, Im T, -Im T, Re T).
+// Grid (n, k) over the padded band range: exponent of band n of T_k over the
+// box, then the four parts (Re T, Im T, -Im T, Re T) of every plane p into
+//   Tq[k][p][X][Y][zb][h][b][part & 1][j][z & 7],  part = 2 h + (part & 1),
+// n = b NB + j, z = 8 zb + (z & 7); bands past nb(k) and z past the box are 0.
 __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int *__restrict__ nb_k, int td0, int td1,
-                                int td2, int Zp, int nbmax, const int *__restrict__ kslot, __nv_bfloat16 *__restrict__ Tp,
-                                int *__restrict__ eT) {
+                                int td2, int nzb, int NB, int nblk, int nbmax, const int *__restrict__ kslot,
+                                __nv_bfloat16 *__restrict__ Tq, int *__restrict__ eT) {
     int n = blockIdx.x, k = blockIdx.y;
     int slot = kslot[k];
-    if (slot < 0 || n >= nb_k[k]) return;
+    if (slot < 0) return;
+    const bool live = n < nb_k[k];
     long long box = (long long)td0 * td1 * td2;
-    const double2 *T = Tk[k] + (size_t)n * box;
+    const double2 *T = live ? Tk[k] + (size_t)n * box : nullptr;
     __shared__ unsigned long long red[256];
     unsigned long long mx = 0;
-    for (long long i = threadIdx.x; i < box; i += blockDim.x) mx = max(mx, max(abs_bits(T[i].x), abs_bits(T[i].y)));
+    if (live)
+        for (long long i = threadIdx.x; i < box; i += blockDim.x) mx = max(mx, max(abs_bits(T[i].x), abs_bits(T[i].y)));
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
@@ -112,22 +117,28 @@ __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int
         __syncthreads();
     }
     int e = line_exp_bits(red[0]);
-    if (threadIdx.x == 0) eT[(size_t)k * nbmax + n] = e;
-    const long long lines = (long long)td0 * td1;
-    const long long bandsz = lines * Zp;
-    for (long long i = threadIdx.x; i < bandsz; i += blockDim.x) {
-        int z = (int)(i % Zp);
-        long long xy = i / Zp;
-        double2 v = (z < td2) ? T[xy * td2 + z] : make_double2(0.0, 0.0);
+    if (threadIdx.x == 0 && n < nbmax) eT[(size_t)k * nbmax + n] = e;
+    const int b = n / NB, j = n % NB;
+    const long long zspan = (long long)nzb * 8;
+    const long long npts = (long long)td0 * td1 * zspan;
+    const long long blk = 2LL * NB * 8;                       // one (h, b) block: 2 parts x NB bands x 8 z
+    for (long long i = threadIdx.x; i < npts; i += blockDim.x) {
+        int z = (int)(i % zspan);
+        long long xy = i / zspan;
+        double2 v = (live && z < td2) ? T[xy * td2 + z] : make_double2(0.0, 0.0);
         __nv_bfloat16 sr[NPL], si[NPL];
         slice4(v.x, e, sr);
         slice4(v.y, e, si);
+        const int zb = z >> 3, z8 = z & 7;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
-            long long R0 = ((long long)slot * NPL + p) * ZT_NPART;
             __nv_bfloat16 part[ZT_NPART] = {sr[p], si[p], __hneg(si[p]), sr[p]};
+            long long cell = (((long long)slot * NPL + p) * td0 * td1 + xy) * nzb + zb;   // (k, p, X, Y, zb)
 #pragma unroll
-            for (int q = 0; q < ZT_NPART; ++q) Tp[((R0 + q) * nbmax + n) * bandsz + i] = part[q];
+            for (int q = 0; q < ZT_NPART; ++q) {
+                long long o = ((cell * 2 + (q >> 1)) * nblk + b) * blk + ((long long)(q & 1) * NB + j) * 8 + z8;
+                Tq[o] = part[q];
+            }
         }
     }
 }
@@ -148,8 +159,10 @@ struct ZParams {
     const int *rowk, *rowm;       // rows of A (k', m)
     const int *aexp, *eT;         // row exponents, [k][n] band exponents
     const int *kslot;             // k -> slot of its T slices
-    const int4 *segs;             // [phase][segment] (x, y, z0, -)
+    const int *segoff;            // [phase][segment] cell offset of the segment's T block
     int nsegp_max;
+    const __nv_bfloat16 *Tq;      // sliced T blocks (t_slices_kernel layout)
+    int td0, td1, nzb, nblk;
     int nchunk[ZT_NPH];           // 64-K chunks per K half, per phase
     double2 *Z;
     long long RSc;
@@ -161,7 +174,7 @@ struct ZParams {
 // warp 0: TMA; warp 1: MMA; warps 2..9: epilogue (lane quarter, real/imaginary output)
 template <int NB>
 __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                                      const __grid_constant__ CUtensorMap tmT, ZParams p) {
+                                                                      ZParams p) {
     constexpr int N = 2 * NB;                            // real and imaginary output columns
     constexpr int SEGB = N * 16;                         // one segment: N rows x 8 z
     constexpr int B_PLANE = 8 * SEGB;                    // eight segments per 64-K chunk
@@ -190,43 +203,50 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
     uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {
-            int s = 0;
-            uint32_t ph = 0;
-            int issued = 0;
-            for (int t = blockIdx.x; t < p.ntiles && !abort_flag; t += gridDim.x) {
-                const ZTile tl = p.tiles[t];
-                const int4 W = p.wxyz[tl.w];
-                const int phz = W.w, nch = p.nchunk[phz];
-                const int slot = p.kslot[tl.k];
-                const int4 *sg = p.segs + (size_t)phz * p.nsegp_max;
-                bool stop = false;
-                for (int c = 0; c < 2 * nch; ++c) {
-                    if (!mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma)) { stop = true; break; }
-                    const int h = c >= nch, cl = h ? c - nch : c;
-                    unsigned char *st = stages + (size_t)s * STAGE;
-                    mbar_expect_tx(&full_bar[s], STAGE);
-#pragma unroll
-                    for (int pl = 0; pl < NPL; ++pl)
-                        tma_load_2d(saddr(st + pl * ZT_A_PLANE), &tmA, &full_bar[s], h * p.Kh + cl * 64,
-                                    (phz * NPL + pl) * p.Rpad + tl.mrow);
-#pragma unroll 1
-                    for (int j = 0; j < 8; ++j) {
-                        const int4 sj = sg[cl * 8 + j];
-                        const int X = W.x + sj.x - p.tlo0, Y = W.y + sj.y - p.tlo1, Z = W.z + sj.z - p.tlo2;
-#pragma unroll
-                        for (int pl = 0; pl < NPL; ++pl)
-                            tma_load_5d(saddr(st + NPL * ZT_A_PLANE + pl * B_PLANE + j * SEGB), &tmT, &full_bar[s], Z, Y, X,
-                                        tl.nblk * NB, (slot * NPL + pl) * ZT_NPART + 2 * h);
-                    }
-                    ++issued;
-                    if (++s == ZT_STAGES) { s = 0; ph ^= 1; }
+        // producer warp: lane 0 waits for the stage and arms its barrier, then
+        // lanes 0..3 load the four A planes and lane l the B segment l % 8 of plane l / 8
+        int s = 0;
+        uint32_t ph = 0;
+        int issued = 0;
+        const int bpl = lane >> 3, bj = lane & 7;
+        const long long plane_cells = (long long)p.td0 * p.td1 * p.nzb;
+        const long long cellb = 2LL * p.nblk * SEGB;
+        const char *tq = reinterpret_cast<const char *>(p.Tq);
+        for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+            const ZTile tl = p.tiles[t];
+            const int4 W = p.wxyz[tl.w];
+            const int phz = W.w, nch = p.nchunk[phz];
+            const int slot = p.kslot[tl.k];
+            const int *so = p.segoff + (size_t)phz * p.nsegp_max;
+            // T block cell of a segment = (k, p) plane + tile shift + segment offset;
+            // X, Y inside the T box and z a whole block inside it by construction
+            const long long tb = ((long long)(W.x - p.tlo0) * p.td1 + (W.y - p.tlo1)) * p.nzb + ((W.z + phz - p.tlo2) >> 3);
+            const long long pbase = ((long long)slot * NPL + bpl) * plane_cells + tb;
+            bool stop = false;
+            for (int c = 0; c < 2 * nch; ++c) {
+                int ok = 1;
+                if (lane == 0) {
+                    ok = mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma) ? 1 : 0;
+                    if (ok) mbar_expect_tx(&full_bar[s], STAGE);
                 }
-                if (stop) break;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) { stop = true; break; }
+                const int h = c >= nch, cl = h ? c - nch : c;
+                unsigned char *st = stages + (size_t)s * STAGE;
+                if (lane < NPL)
+                    tma_load_2d(saddr(st + lane * ZT_A_PLANE), &tmA, &full_bar[s], h * p.Kh + cl * 64,
+                                (phz * NPL + lane) * p.Rpad + tl.mrow);
+                const long long hb = ((long long)h * p.nblk + tl.nblk) * SEGB;
+                bulk_load(saddr(st + NPL * ZT_A_PLANE + bpl * B_PLANE + bj * SEGB), tq + (pbase + so[cl * 8 + bj]) * cellb + hb,
+                          SEGB, &full_bar[s]);
+                ++issued;
+                if (++s == ZT_STAGES) { s = 0; ph ^= 1; }
             }
-            if (abort_flag) {
-                for (int i = 0; i < ZT_STAGES && i < issued; ++i) mbar_drain(&full_bar[i], 0), mbar_drain(&full_bar[i], 1);
-            }
+            if (stop) break;
+        }
+        __syncwarp();
+        if (lane == 0 && abort_flag) {
+            for (int i = 0; i < ZT_STAGES && i < issued; ++i) mbar_drain(&full_bar[i], 0), mbar_drain(&full_bar[i], 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -266,38 +286,48 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             }
         }
     } else {
+        // epilogue warp (quarter, cs): TMEM lanes of its quarter, bands
+        // [cs NB/2, (cs + 1) NB/2) of the block, real and imaginary columns of each
+        constexpr int NH = NB / 2;                     // a multiple of 4
         const int e = warp - 2;
-        const int quarter = warp % 4, half = e / 4;   // half 0: real output columns, 1: imaginary
+        const int quarter = warp % 4, cs = e / 4;
         uint32_t eph = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             const ZTile tl = p.tiles[t];
             const int4 W = p.wxyz[tl.w];
             const int ngroups = (2 * p.nchunk[W.w] + ZT_GROUP - 1) / ZT_GROUP;
-            float hi[NB], lo[NB];
+            float hr[NH], lr[NH], hm[NH], lm[NH];
 #pragma unroll
-            for (int j = 0; j < NB; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int j = 0; j < NH; ++j) { hr[j] = 0.f; lr[j] = 0.f; hm[j] = 0.f; lm[j] = 0.f; }
             for (int g = 0; g < ngroups; ++g) {
                 if (!mbar_wait(&tfull_bar, eph, &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + half * NB;
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + cs * NH;
 #pragma unroll
-                for (int c0 = 0; c0 < NB; c0 += 8) {
-                    uint32_t a0[8], a1[8], a2[8], a3[8];
-                    tmem_ld8(tb + 0 * N + c0, a0);
-                    tmem_ld8(tb + 1 * N + c0, a1);
-                    tmem_ld8(tb + 2 * N + c0, a2);
-                    tmem_ld8(tb + 3 * N + c0, a3);
+                for (int c0 = 0; c0 < NH; c0 += 4) {
+                    uint32_t a0[4], a1[4], a2[4], a3[4], b0[4], b1[4], b2[4], b3[4];
+                    tmem_ld4(tb + 0 * N + c0, a0);
+                    tmem_ld4(tb + 1 * N + c0, a1);
+                    tmem_ld4(tb + 2 * N + c0, a2);
+                    tmem_ld4(tb + 3 * N + c0, a3);
+                    tmem_ld4(tb + 0 * N + NB + c0, b0);
+                    tmem_ld4(tb + 1 * N + NB + c0, b1);
+                    tmem_ld4(tb + 2 * N + NB + c0, b2);
+                    tmem_ld4(tb + 3 * N + NB + c0, b3);
                     tmem_wait_ld();
-                    if (c0 + 8 >= NB) {   // everything read: hand the accumulators back to the MMA warp
+                    if (c0 + 4 >= NH) {   // everything read: hand the accumulators back to the MMA warp
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&tempty_bar);
                     }
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
+                    for (int j = 0; j < 4; ++j) {
                         class_accumulate(__uint_as_float(a0[j]), __uint_as_float(a1[j]), __uint_as_float(a2[j]),
-                                         __uint_as_float(a3[j]), 1.0f, hi[c0 + j], lo[c0 + j]);
+                                         __uint_as_float(a3[j]), 1.0f, hr[c0 + j], lr[c0 + j]);
+                        class_accumulate(__uint_as_float(b0[j]), __uint_as_float(b1[j]), __uint_as_float(b2[j]),
+                                         __uint_as_float(b3[j]), 1.0f, hm[c0 + j], lm[c0 + j]);
+                    }
                 }
                 eph ^= 1;
             }
@@ -316,12 +346,15 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                         const int ea = p.aexp[r] - 16;
                         const int *eTk = p.eT + (size_t)tl.k * p.nbmax;
 #pragma unroll
-                        for (int j = 0; j < NB; ++j) {
-                            const int n = tl.nblk * NB + j;
+                        for (int jj = 0; jj < NH; ++jj) {
+                            const int n = tl.nblk * NB + cs * NH + jj;
                             if (n < pr.nb) {
-                                double v = scale2((double)hi[j] + (double)lo[j], ea + eTk[n]) * p.rs;
+                                const int ex = ea + eTk[n];
+                                double2 v;
+                                v.x = scale2((double)hr[jj] + (double)lr[jj], ex) * p.rs;
+                                v.y = scale2((double)hm[jj] + (double)lm[jj], ex) * p.rs;
                                 long long col = pr.col0 + (long long)m * pr.nb + n;
-                                reinterpret_cast<double *>(p.Z + col * p.RSc + p.nmt + g)[half] = v;
+                                p.Z[col * p.RSc + p.nmt + g] = v;
                             }
                         }
                     }
@@ -399,12 +432,17 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     int nsegp_max = 0;
     for (int ph = 0; ph < ZT_NPH; ++ph) nsegp_max = std::max(nsegp_max, (nseg[ph] + 7) / 8 * 8);
     const int Kh = nsegp_max * 8;
-    std::vector<int4> segtab((size_t)ZT_NPH * nsegp_max);
+    const int nzb = (in.tdim[2] + 7) / 8;
+    // cell offset of every segment in the sliced T box, relative to the tile
+    // shift (X, Y, zb) = (W_x - tlo_x, W_y - tlo_y, (W_z + ph - tlo_z) / 8)
+    std::vector<int> segtab((size_t)ZT_NPH * nsegp_max);
     int nchunk[ZT_NPH];
     for (int ph = 0; ph < ZT_NPH; ++ph) {
         nchunk[ph] = (nseg[ph] + 7) / 8;
-        for (int s2 = 0; s2 < nsegp_max; ++s2)
-            segtab[(size_t)ph * nsegp_max + s2] = s2 < nseg[ph] ? segs[ph][s2] : segs[ph][0];   // padding: any valid box
+        for (int s2 = 0; s2 < nsegp_max; ++s2) {
+            const int4 sg = s2 < nseg[ph] ? segs[ph][s2] : segs[ph][0];   // padding: any valid block
+            segtab[(size_t)ph * nsegp_max + s2] = (sg.x * in.tdim[1] + sg.y) * nzb + (sg.z - ph) / 8;
+        }
     }
     // ---- rows (k', m) of every k'
     std::vector<int> rowk, rowm, rowbase(nk, -1);
@@ -480,17 +518,35 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         }
     }
     if (tiles.empty()) return HFX_OK;
+    {
+        // every B segment of every tile must be one whole z block inside the sliced T box
+        int sx0 = 1 << 29, sx1 = -(1 << 29), sy0 = 1 << 29, sy1 = -(1 << 29), z00[ZT_NPH], z01[ZT_NPH];
+        for (int ph = 0; ph < ZT_NPH; ++ph) {
+            z00[ph] = 1 << 29;
+            z01[ph] = -(1 << 29);
+            for (const int4 &sg : segs[ph]) {
+                sx0 = std::min(sx0, sg.x); sx1 = std::max(sx1, sg.x);
+                sy0 = std::min(sy0, sg.y); sy1 = std::max(sy1, sg.y);
+                z00[ph] = std::min(z00[ph], sg.z); z01[ph] = std::max(z01[ph], sg.z);
+            }
+        }
+        for (const int4 &W : wxyz) {
+            const int Z0 = W.z + z00[W.w] - in.tlo[2], Z1 = W.z + z01[W.w] - in.tlo[2];
+            if (W.x + sx0 - in.tlo[0] < 0 || W.x + sx1 - in.tlo[0] >= in.tdim[0] || W.y + sy0 - in.tlo[1] < 0 ||
+                W.y + sy1 - in.tlo[1] >= in.tdim[1] || Z0 < 0 || (Z0 & 7) != 0 || (Z1 >> 3) >= nzb)
+                return set_err(ctx, HFX_EUNSUPPORTED, "interstitial segment outside the step-function box");
+        }
+    }
     // ---- device buffers (scratch s_zipw)
-    const int Zp = (in.tdim[2] + 7) / 8 * 8;
-    const size_t bandsz = (size_t)in.tdim[0] * in.tdim[1] * Zp;
-    const size_t tp_elems = (size_t)nslot * NPL * ZT_NPART * in.nb_max * bandsz;
+    const int nbpad = nblk * NBt;
+    const size_t tp_elems = (size_t)nslot * NPL * ZT_NPART * nbpad * in.tdim[0] * in.tdim[1] * nzb * 8;
     const size_t a_elems = (size_t)ZT_NPH * NPL * Rpad * 2 * Kh;
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
     const size_t o_tp = place(tp_elems * 2), o_a = place(a_elems * 2), o_aexp = place((size_t)Rpad * 4),
                  o_eT = place((size_t)nk * in.nb_max * 4), o_rowk = place((size_t)R * 4), o_rowm = place((size_t)R * 4),
                  o_line = place(line_of.size() * 4), o_sst = place(segstart.size() * 4), o_sz0 = place(segz0.size() * 4),
-                 o_seg = place(segtab.size() * sizeof(int4)), o_gtab = place(gtab.size() * 4),
+                 o_seg = place(segtab.size() * sizeof(int)), o_gtab = place(gtab.size() * 4),
                  o_pinfo = place(pinfo.size() * sizeof(ZPairInfo)), o_w = place(wxyz.size() * sizeof(int4)),
                  o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4);
     if ((rc = scratch_reserve(ctx, ctx->s_zipw, off))) return rc;
@@ -500,7 +556,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     };
     if ((rc = up(o_rowk, rowk.data(), R * 4)) || (rc = up(o_rowm, rowm.data(), R * 4)) ||
         (rc = up(o_line, line_of.data(), line_of.size() * 4)) || (rc = up(o_sst, segstart.data(), segstart.size() * 4)) ||
-        (rc = up(o_sz0, segz0.data(), segz0.size() * 4)) || (rc = up(o_seg, segtab.data(), segtab.size() * sizeof(int4))) ||
+        (rc = up(o_sz0, segz0.data(), segz0.size() * 4)) || (rc = up(o_seg, segtab.data(), segtab.size() * sizeof(int))) ||
         (rc = up(o_gtab, gtab.data(), gtab.size() * 4)) ||
         (rc = up(o_pinfo, pinfo.data(), pinfo.size() * sizeof(ZPairInfo))) ||
         (rc = up(o_w, wxyz.data(), wxyz.size() * sizeof(int4))) ||
@@ -514,18 +570,12 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                                        reinterpret_cast<int *>(b + o_rowm), reinterpret_cast<int *>(b + o_line), gmin[0], gmin[1],
                                        By, nL, reinterpret_cast<int *>(b + o_sst), reinterpret_cast<int *>(b + o_sz0), Kh, Rpad, A,
                                        aexp);
-    t_slices_kernel<<<dim3(in.nb_max, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], Zp, in.nb_max,
-                                                         reinterpret_cast<int *>(b + o_kslot), Tp, eT);
+    t_slices_kernel<<<dim3(nbpad, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], nzb, NBt, nblk,
+                                                     in.nb_max, reinterpret_cast<int *>(b + o_kslot), Tp, eT);
     if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw slices"))) return rc;
     // ---- tensor maps
-    CUtensorMap mA, mT;
+    CUtensorMap mA;
     if ((rc = make_map_2d(ctx, &mA, A, (long long)ZT_NPH * NPL * Rpad, 2LL * Kh, ZT_BM))) return rc;
-    unsigned long long dims[5] = {(unsigned long long)Zp, (unsigned long long)in.tdim[1], (unsigned long long)in.tdim[0],
-                                  (unsigned long long)in.nb_max, (unsigned long long)nslot * NPL * ZT_NPART};
-    unsigned long long strides[4] = {(unsigned long long)Zp * 2, (unsigned long long)Zp * in.tdim[1] * 2,
-                                     (unsigned long long)bandsz * 2, (unsigned long long)bandsz * in.nb_max * 2};
-    unsigned int box[5] = {8, 1, 1, (unsigned int)NBt, 2};
-    if ((rc = make_map_5d(ctx, &mT, Tp, dims, strides, box, 0))) return rc;
     ZParams p;
     p.tiles = reinterpret_cast<ZTile *>(b + o_tiles);
     p.ntiles = (int)tiles.size();
@@ -540,8 +590,13 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     p.aexp = aexp;
     p.eT = eT;
     p.kslot = reinterpret_cast<int *>(b + o_kslot);
-    p.segs = reinterpret_cast<int4 *>(b + o_seg);
+    p.segoff = reinterpret_cast<int *>(b + o_seg);
     p.nsegp_max = nsegp_max;
+    p.Tq = Tp;
+    p.td0 = in.tdim[0];
+    p.td1 = in.tdim[1];
+    p.nzb = nzb;
+    p.nblk = nblk;
     for (int ph = 0; ph < ZT_NPH; ++ph) p.nchunk[ph] = nchunk[ph];
     p.Z = in.d_Z;
     p.RSc = in.RSc;
@@ -567,7 +622,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                                        (size_t)smem_max - fa.sharedSizeBytes);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (in.ev_gemm0) cudaEventRecord(in.ev_gemm0, st);
-        kern<<<grid, 64 + 32 * ZT_EPI, smem, st>>>(mA, mT, p);
+        kern<<<grid, 64 + 32 * ZT_EPI, smem, st>>>(mA, p);
         if (in.ev_gemm1) cudaEventRecord(in.ev_gemm1, st);
     };
     switch (NBt) {
