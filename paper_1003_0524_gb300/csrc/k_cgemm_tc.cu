@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
                             im = re * f.y + im * f.x;
                             re = x;
                         }
-                        p.out[ro + co] = make_double2(re, im);
+                        __stcs(p.out + ro + co, make_double2(re, im));   // streaming: keep the operands in L2
                     }
                 }
             }

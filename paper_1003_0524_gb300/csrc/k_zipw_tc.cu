@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                                 v.x = scale2((double)hr[jj] + (double)lr[jj], ex) * p.rs;
                                 v.y = scale2((double)hm[jj] + (double)lm[jj], ex) * p.rs;
                                 long long col = pr.col0 + (long long)m * pr.nb + n;
-                                p.Z[col * p.RSc + p.nmt + g] = v;
+                                __stcs(p.Z + col * p.RSc + p.nmt + g, v);   // streaming: keep the operands in L2
                             }
                         }
                     }
@@ -518,6 +518,10 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         }
     }
     if (tiles.empty()) return HFX_OK;
+    // tiles of one z phase together: the C slices of a phase (8.4 MB for 512
+    // rows) and T of one k stay in L2 while the CTAs sweep that k's shifts
+    std::stable_sort(tiles.begin(), tiles.end(),
+                     [&](const ZTile &a, const ZTile &b) { return wxyz[a.w].w < wxyz[b.w].w; });
     {
         // every B segment of every tile must be one whole z block inside the sliced T box
         int sx0 = 1 << 29, sx1 = -(1 << 29), sy0 = 1 << 29, sy1 = -(1 << 29), z00[ZT_NPH], z01[ZT_NPH];

@@ -96,12 +96,12 @@ CONFIGS = {
             pos=[[0.0, 0.0, 0.0], [0.5, 0.5, 0.5], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5],
                  [0.0, 0.5, 0.5]],
             rmt=[2.4, 1.8, 1.5, 1.5, 1.5], mesh=(6, 6, 6), nb=120, no=20, lmax=4,
-            Lmax=4, P=3, gmax=3.0, aux=("count", 1100, 1100), sparse=True, a_scale=0.13,
-            scale=1.0),
+            Lmax=4, P=3, gmax=3.0, aux=("count", 1100, 1100), sparse=True, a_scale=0.17,
+            scale=0.223),
     4: dict(name="corundum_10atom_k4x4x4_n250",
             lattice=_rhombohedral(5.3 * ANGSTROM, 55.3), pos=_corundum_like_positions(),
             rmt=[1.7] * 4 + [1.35] * 6, mesh=(4, 4, 4), nb=250, no=48, lmax=4, Lmax=5,
-            P=2, gmax=3.0, aux=("count", 2300, 2300), sparse=True, a_scale=0.1, scale=1.0),
+            P=2, gmax=3.0, aux=("count", 2300, 2300), sparse=True, a_scale=0.15, scale=0.122),
 }
 
 

@@ -62,6 +62,12 @@ SMALL = {
     "cfg0": lambda: S.make_system(0),
     "cfg1_k2": lambda: S.make_system(1, mesh=(2, 2, 2)),
     "cfg2_k2": lambda: S.make_system(2, mesh=(2, 2, 2)),
+    # several band blocks in every tensor-core stage (72 bands)
+    "cfg1_nb72": lambda: S.make_system(1, mesh=(2, 1, 1), nb=72, no=6),
+    # the cells, atoms, aux sizes and MT channels of configs 3 and 4 on a 1x1x2
+    # mesh with narrow band windows, so that the oracle stays fast
+    "cfg3_shape": lambda: S.make_system(3, mesh=(1, 1, 2), nb=12, no=4),
+    "cfg4_shape": lambda: S.make_system(4, mesh=(1, 1, 2), nb=10, no=4),
 }
 
 
