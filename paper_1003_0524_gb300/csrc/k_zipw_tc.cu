@@ -95,8 +95,9 @@ __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int
 // ------------------------------------------------------------- T slices
 // Grid (n, k) over the padded band range: exponent of band n of T_k over the
 // box, then the four parts (Re T, Im T, -Im T, Re T) of every plane p into
-//   Tq[k][p][X][Y][zb][h][b][part & 1][j][z & 7],  part = 2 h + (part & 1),
+//   Tq[k][X][Y][zb][h][b][p][part & 1][j][z & 7],  part = 2 h + (part & 1),
 // n = b NB + j, z = 8 zb + (z & 7); bands past nb(k) and z past the box are 0.
+// One (k, X, Y, zb, h, b) block -- all planes of one segment -- is contiguous.
 __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int *__restrict__ nb_k, int td0, int td1,
                                 int td2, int nzb, int NB, int nblk, int nbmax, const int *__restrict__ kslot,
                                 __nv_bfloat16 *__restrict__ Tq, int *__restrict__ eT) {
@@ -130,13 +131,13 @@ __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int
         slice4(v.x, e, sr);
         slice4(v.y, e, si);
         const int zb = z >> 3, z8 = z & 7;
+        const long long cell = ((long long)slot * td0 * td1 + xy) * nzb + zb;   // (k, X, Y, zb)
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
             __nv_bfloat16 part[ZT_NPART] = {sr[p], si[p], __hneg(si[p]), sr[p]};
-            long long cell = (((long long)slot * NPL + p) * td0 * td1 + xy) * nzb + zb;   // (k, p, X, Y, zb)
 #pragma unroll
             for (int q = 0; q < ZT_NPART; ++q) {
-                long long o = ((cell * 2 + (q >> 1)) * nblk + b) * blk + ((long long)(q & 1) * NB + j) * 8 + z8;
+                long long o = ((cell * 2 + (q >> 1)) * nblk + b) * (NPL * blk) + ((long long)(p * 2 + (q & 1)) * NB + j) * 8 + z8;
                 Tq[o] = part[q];
             }
         }
@@ -176,9 +177,9 @@ template <int NB>
 __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                       ZParams p) {
     constexpr int N = 2 * NB;                            // real and imaginary output columns
-    constexpr int SEGB = N * 16;                         // one segment: N rows x 8 z
-    constexpr int B_PLANE = 8 * SEGB;                    // eight segments per 64-K chunk
-    constexpr int STAGE = NPL * (ZT_A_PLANE + B_PLANE);
+    constexpr int SEGB = N * 16;                         // one segment of one plane: N rows x 8 z
+    constexpr int SEG4 = NPL * SEGB;                     // one segment, all planes (one bulk copy)
+    constexpr int STAGE = NPL * ZT_A_PLANE + 8 * SEG4;   // eight segments per 64-K chunk
     extern __shared__ __align__(1024) unsigned char zt_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(zt_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
@@ -204,13 +205,13 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
 
     if (warp == 0) {
         // producer warp: lane 0 waits for the stage and arms its barrier, then
-        // lanes 0..3 load the four A planes and lane l the B segment l % 8 of plane l / 8
+        // lanes 0..3 load the four A planes and lanes 0..7 the eight B segments
         int s = 0;
         uint32_t ph = 0;
         int issued = 0;
-        const int bpl = lane >> 3, bj = lane & 7;
-        const long long plane_cells = (long long)p.td0 * p.td1 * p.nzb;
-        const long long cellb = 2LL * p.nblk * SEGB;
+        const int bj = lane & 7;
+        const long long slot_cells = (long long)p.td0 * p.td1 * p.nzb;
+        const long long cellb = 2LL * p.nblk * SEG4;
         const char *tq = reinterpret_cast<const char *>(p.Tq);
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
             const ZTile tl = p.tiles[t];
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             // T block cell of a segment = (k, p) plane + tile shift + segment offset;
             // X, Y inside the T box and z a whole block inside it by construction
             const long long tb = ((long long)(W.x - p.tlo0) * p.td1 + (W.y - p.tlo1)) * p.nzb + ((W.z + phz - p.tlo2) >> 3);
-            const long long pbase = ((long long)slot * NPL + bpl) * plane_cells + tb;
+            const long long kbase = (long long)slot * slot_cells + tb;
             bool stop = false;
             for (int c = 0; c < 2 * nch; ++c) {
                 int ok = 1;
@@ -236,9 +237,10 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                 if (lane < NPL)
                     tma_load_2d(saddr(st + lane * ZT_A_PLANE), &tmA, &full_bar[s], h * p.Kh + cl * 64,
                                 (phz * NPL + lane) * p.Rpad + tl.mrow);
-                const long long hb = ((long long)h * p.nblk + tl.nblk) * SEGB;
-                bulk_load(saddr(st + NPL * ZT_A_PLANE + bpl * B_PLANE + bj * SEGB), tq + (pbase + so[cl * 8 + bj]) * cellb + hb,
-                          SEGB, &full_bar[s]);
+                const long long hb = ((long long)h * p.nblk + tl.nblk) * SEG4;
+                if (lane < 8)
+                    bulk_load(saddr(st + NPL * ZT_A_PLANE + bj * SEG4), tq + (kbase + so[cl * 8 + bj]) * cellb + hb, SEG4,
+                              &full_bar[s]);
                 ++issued;
                 if (++s == ZT_STAGES) { s = 0; ph ^= 1; }
             }
@@ -271,8 +273,8 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                             const bool lead = tm == 0 || tm == 1 || tm == 3 || tm == 6;
 #pragma unroll
                             for (int ks = 0; ks < 4; ++ks) {
-                                // K step ks: segments 2 ks and 2 ks + 1
-                                const uint64_t db = desc_ns(b0 + term_b(tm) * B_PLANE + 2 * ks * SEGB, SEGB, 128);
+                                // K step ks: segments 2 ks and 2 ks + 1 (plane term_b of each)
+                                const uint64_t db = desc_ns(b0 + 2 * ks * SEG4 + term_b(tm) * SEGB, SEG4, 128);
                                 umma_bf16(tmem + term_w(tm) * N, da + 2 * ks, db, idesc, (first && lead && ks == 0) ? 0u : 1u);
                             }
                         }
@@ -622,7 +624,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     auto go = [&](auto kern, int nb) {
         cudaFuncAttributes fa;
         cudaFuncGetAttributes(&fa, kern);
-        size_t smem = std::max<size_t>((size_t)ZT_STAGES * NPL * (ZT_A_PLANE + 8 * 2 * nb * 16) + 1024,
+        size_t smem = std::max<size_t>((size_t)ZT_STAGES * (NPL * ZT_A_PLANE + 8 * NPL * 2 * nb * 16) + 1024,
                                        (size_t)smem_max - fa.sharedSizeBytes);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (in.ev_gemm0) cudaEventRecord(in.ev_gemm0, st);
