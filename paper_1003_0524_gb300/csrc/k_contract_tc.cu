@@ -115,15 +115,24 @@ __global__ void block_y_kernel(const QDesc *__restrict__ qd, const double2 *cons
     }
 }
 
+// d * 2^k by exponent arithmetic (d normal or zero, result normal)
+__device__ __forceinline__ double scale2(double d, int k) {
+    long long b = __double_as_longlong(d);
+    if ((b << 1) == 0) return d;
+    return __longlong_as_double(b + ((long long)k << 52));
+}
+
 // ------------------------------------------------------------- GEMM1
-// Tile: 128 rows of A' (one q) x 64 columns of Z; K chunks of 64 (one
-// 128-byte swizzled row per operand row), the four slices of both operands
-// per stage; four class accumulators, double-buffered in TMEM.
-struct G1Tile { int qslot, mrow, ncol0, klen; };
+// Tile: 128 rows of A' (one q) x 128 columns of Z; K chunks of 32 (one
+// 64-byte swizzled row per operand row), the four slices of both operands per
+// stage, three stages; the four class accumulators fill TMEM (single buffer:
+// the MMA warp waits for the epilogue to read a K group before the next).
+// CTAs of a cluster share the A rows of their tiles (A multicast).
+struct G1Tile { int qslot, mrow, ncol0, klen, out, pad; };
 
 struct G1Params {
-    const G1Tile *tiles;
-    int ntiles;
+    const G1Tile *tiles;          // ngroups x CS: the tiles of one group share their A rows
+    int ngroups;
     const QDesc *qd;
     const int *aexp;       // per A' row: [nk][MP]
     const int *zexp;       // per column of the batch
@@ -134,36 +143,45 @@ struct G1Params {
     int *err;
 };
 
-constexpr int G1_BM = 128, G1_BN = 64, G1_KC = 64;
-constexpr int G1_A_PLANE = G1_BM * G1_KC * 2;              // 16 KB
+constexpr int G1_BM = 128, G1_BN = 128, G1_KC = 32;
+constexpr int G1_A_PLANE = G1_BM * G1_KC * 2;              // 8 KB
 constexpr int G1_B_PLANE = G1_BN * G1_KC * 2;              // 8 KB
-constexpr int G1_STAGE = NPL * (G1_A_PLANE + G1_B_PLANE);   // 96 KB
-constexpr int G1_STAGES = 2;
-constexpr int G1_GROUP = 4;                                // chunks per exact K group (256)
-constexpr int G1_TMEM = 512;                               // 2 buffers x 4 classes x 64 columns
-constexpr int G1_EPI = 8;                                  // epilogue warps
+constexpr int G1_STAGE = NPL * (G1_A_PLANE + G1_B_PLANE);   // 64 KB
+constexpr int G1_STAGES = 3;
+constexpr int G1_GROUP = 8;                                // chunks per exact K group (256)
+constexpr int G1_TMEM = 512;                               // 4 classes x 128 columns
+constexpr int G1_THREADS = 384;                            // 3 warpgroups
+constexpr int G1_CS = 2;                                   // CTAs per cluster sharing A
+// register split (setmaxnreg): the control warpgroup gives its registers to
+// the two epilogue warpgroups; 4*32*64 + 8*32*216 <= 12*32*168
+constexpr int G1_REG_LAUNCH = 168, G1_REG_CTRL = 64, G1_REG_EPI = 216;
+static_assert(4 * G1_REG_CTRL + 8 * G1_REG_EPI <= 12 * G1_REG_LAUNCH, "register split exceeds the launch allocation");
 
-// warp 0: TMA producer; warp 1: MMA issuer; warps 2..9: epilogue
-// (lane quarter = w % 4, column half = (w - 2) / 4)
-__global__ void __launch_bounds__(64 + 32 * G1_EPI, 1) gemm1_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                                    const __grid_constant__ CUtensorMap tmB,
-                                                                    G1Params p) {
+// warpgroup 0: warp 0 TMA producer, warp 1 MMA issuer (warps 2, 3 idle);
+// warpgroups 1, 2: epilogue (TMEM lane quarter = w % 4, column half = (w - 4) / 4).
+// With CS > 1 the CS CTAs of a cluster take the CS tiles of one group (same A
+// rows, different columns); each loads 128/CS rows of every A chunk and
+// multicasts them to all, and every CTA's MMA releases a stage in all CTAs.
+template <int CS>
+__global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                              const __grid_constant__ CUtensorMap tmB, G1Params p) {
+    constexpr uint16_t kMask = (uint16_t)((1u << CS) - 1);
     extern __shared__ __align__(1024) unsigned char g1_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(g1_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
-    __shared__ uint64_t full_bar[G1_STAGES], empty_bar[G1_STAGES], tfull_bar[2], tempty_bar[2];
+    __shared__ uint64_t full_bar[G1_STAGES], empty_bar[G1_STAGES], tfull_bar, tempty_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int rank = CS > 1 ? (int)cluster_ctarank() : 0;
+    const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
     if (threadIdx.x == 0) {
         for (int s = 0; s < G1_STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], 1);
+            mbar_init(&empty_bar[s], CS);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&tfull_bar[b], 1);
-            mbar_init(&tempty_bar[b], G1_EPI);
-        }
+        mbar_init(&tfull_bar, 1);
+        mbar_init(&tempty_bar, 8);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -171,15 +189,17 @@ __global__ void __launch_bounds__(64 + 32 * G1_EPI, 1) gemm1_kernel(const __grid
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (CS > 1) cluster_sync();   // every peer's barriers exist before the first multicast
     uint32_t tmem = tmem_slot;
 
-    if (warp == 0) {
-        if (lane == 0) {
+    if (warp < 4) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(G1_REG_CTRL));
+        if (warp == 0 && lane == 0) {
             int s = 0;
             uint32_t ph = 0;
             int issued = 0;
-            for (int t = blockIdx.x; t < p.ntiles && !abort_flag; t += gridDim.x) {
-                G1Tile tl = p.tiles[t];
+            for (int g = cid; g < p.ngroups && !abort_flag; g += ncl) {
+                G1Tile tl = p.tiles[g * CS + rank];
                 int qi = p.qd[tl.qslot].iq;
                 int nk = tl.klen / G1_KC;
                 bool stop = false;
@@ -188,8 +208,13 @@ __global__ void __launch_bounds__(64 + 32 * G1_EPI, 1) gemm1_kernel(const __grid
                     int x = (kc < nk) ? kc * G1_KC : p.HS + (kc - nk) * G1_KC;
                     unsigned char *st = stages + (size_t)s * G1_STAGE;
                     mbar_expect_tx(&full_bar[s], G1_STAGE);
+#pragma unroll
                     for (int pl = 0; pl < NPL; ++pl) {
-                        tma_load_2d(saddr(st + pl * G1_A_PLANE), &tmA, &full_bar[s], x, (qi * NPL + pl) * p.MP + tl.mrow);
+                        if (CS == 1)
+                            tma_load_2d(saddr(st + pl * G1_A_PLANE), &tmA, &full_bar[s], x, (qi * NPL + pl) * p.MP + tl.mrow);
+                        else
+                            tma_load_2d_mc(saddr(st + pl * G1_A_PLANE + rank * (G1_A_PLANE / CS)), &tmA, &full_bar[s], x,
+                                           (qi * NPL + pl) * p.MP + tl.mrow + rank * (G1_BM / CS), kMask);
                         tma_load_2d(saddr(st + NPL * G1_A_PLANE + pl * G1_B_PLANE), &tmB, &full_bar[s], x,
                                     (int)(pl * p.NC + tl.ncol0));
                     }
@@ -201,105 +226,100 @@ __global__ void __launch_bounds__(64 + 32 * G1_EPI, 1) gemm1_kernel(const __grid
             if (abort_flag) {
                 for (int i = 0; i < G1_STAGES && i < issued; ++i) mbar_drain(&full_bar[i], 0), mbar_drain(&full_bar[i], 1);
             }
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
+        } else if (warp == 1 && lane == 0) {
             int s = 0;
-            uint32_t ph = 0;
-            int buf = 0;
-            uint32_t buf_ph[2] = {0, 0};
+            uint32_t ph = 0, eph = 0;
             constexpr uint32_t idesc = idesc_bf16(G1_BM, G1_BN);
             bool ok = true;
-            for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-                G1Tile tl = p.tiles[t];
+            for (int g = cid; g < p.ngroups && ok; g += ncl) {
+                G1Tile tl = p.tiles[g * CS + rank];
                 int nchunk = 2 * (tl.klen / G1_KC);
                 for (int g0 = 0; g0 < nchunk && ok; g0 += G1_GROUP) {
-                    if (!mbar_wait(&tempty_bar[buf], buf_ph[buf] ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
+                    if (!mbar_wait(&tempty_bar, eph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                     tc_fence_after();
-                    uint32_t dt = tmem + buf * (NPL * G1_BN);
-                    int started = 0;   // bit w: class w written in this group
                     for (int kc = g0; kc < min(nchunk, g0 + G1_GROUP); ++kc) {
                         if (!mbar_wait(&full_bar[s], ph, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                         tc_fence_after();
                         unsigned char *st = stages + (size_t)s * G1_STAGE;
-                        uint32_t a0 = saddr(st), b0 = saddr(st + NPL * G1_A_PLANE);
-                        for (int tm = 0; tm < NTERM; ++tm) {
-                            int w = kSW[tm];
-                            uint64_t da = desc_sw128(a0 + kSA[tm] * G1_A_PLANE);
-                            uint64_t db = desc_sw128(b0 + kSB[tm] * G1_B_PLANE);
+                        const uint32_t a0 = saddr(st), b0 = saddr(st + NPL * G1_A_PLANE);
+                        const bool first = kc == g0;
 #pragma unroll
-                            for (int ks = 0; ks < G1_KC / 16; ++ks) {
-                                umma_bf16(dt + w * G1_BN, da + 2 * ks, db + 2 * ks, idesc, ((started >> w) & 1) ? 1u : 0u);
-                                started |= 1 << w;
-                            }
+                        for (int tm = 0; tm < NTERM; ++tm) {
+                            const uint64_t da = desc_sw64(a0 + slice_term_a(tm) * G1_A_PLANE);
+                            const uint64_t db = desc_sw64(b0 + slice_term_b(tm) * G1_B_PLANE);
+                            const bool lead = tm == 0 || tm == 1 || tm == 3 || tm == 6;
+#pragma unroll
+                            for (int ks = 0; ks < G1_KC / 16; ++ks)
+                                umma_bf16(tmem + slice_term_w(tm) * G1_BN, da + 2 * ks, db + 2 * ks, idesc,
+                                          (first && lead && ks == 0) ? 0u : 1u);
                         }
-                        umma_commit(&empty_bar[s]);
+                        if (CS == 1) umma_commit(&empty_bar[s]);
+                        else umma_commit_mc(&empty_bar[s], kMask);
                         if (++s == G1_STAGES) { s = 0; ph ^= 1; }
                     }
                     if (!ok) break;
-                    umma_commit(&tfull_bar[buf]);
-                    buf_ph[buf] ^= 1;
-                    buf ^= 1;
+                    umma_commit(&tfull_bar);
+                    eph ^= 1;
                 }
             }
         }
     } else {
-        int e = warp - 2;
-        int quarter = warp % 4, half = e / 4;
-        int buf = 0;
-        uint32_t buf_ph[2] = {0, 0};
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(G1_REG_EPI));
+        const int quarter = warp % 4, half = (warp - 4) / 4;
+        uint32_t eph = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-            G1Tile tl = p.tiles[t];
+        for (int g = cid; g < p.ngroups && ok; g += ncl) {
+            G1Tile tl = p.tiles[g * CS + rank];
             const QDesc q = p.qd[tl.qslot];
             int nchunk = 2 * (tl.klen / G1_KC);
             int ngroups = (nchunk + G1_GROUP - 1) / G1_GROUP;
-            float hi[32], lo[32];
+            float hi[64], lo[64];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
-            for (int g = 0; g < ngroups; ++g) {
-                if (!mbar_wait(&tfull_bar[buf], buf_ph[buf], &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
+            for (int j = 0; j < 64; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int gg = 0; gg < ngroups; ++gg) {
+                if (!mbar_wait(&tfull_bar, eph, &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
                 tc_fence_after();
-                uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (NPL * G1_BN) + half * 32;
+                uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + half * 64;
 #pragma unroll
-                for (int c0 = 0; c0 < 32; c0 += 16) {
-                    uint32_t a0[16], a1[16], a2[16], a3[16];
-                    tmem_ld16(tb + 0 * G1_BN + c0, a0);
-                    tmem_ld16(tb + 1 * G1_BN + c0, a1);
-                    tmem_ld16(tb + 2 * G1_BN + c0, a2);
-                    tmem_ld16(tb + 3 * G1_BN + c0, a3);
+                for (int c0 = 0; c0 < 64; c0 += 8) {
+                    uint32_t a0[8], a1[8], a2[8], a3[8];
+                    tmem_ld8(tb + 0 * G1_BN + c0, a0);
+                    tmem_ld8(tb + 1 * G1_BN + c0, a1);
+                    tmem_ld8(tb + 2 * G1_BN + c0, a2);
+                    tmem_ld8(tb + 3 * G1_BN + c0, a3);
                     tmem_wait_ld();
+                    if (c0 + 8 == 64) {   // everything read: hand the accumulators back to the MMA warp
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tempty_bar);
+                    }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
+                    for (int j = 0; j < 8; ++j)
                         class_accumulate(__uint_as_float(a0[j]), __uint_as_float(a1[j]), __uint_as_float(a2[j]),
                                          __uint_as_float(a3[j]), 1.0f, hi[c0 + j], lo[c0 + j]);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty_bar[buf]);
-                buf_ph[buf] ^= 1;
-                buf ^= 1;
+                eph ^= 1;
             }
             if (!ok) break;
             int r = tl.mrow + quarter * 32 + lane;           // row of A' in this q
             bool im = r >= p.Dpad;
             int rr = im ? r - p.Dpad : r;
-            if (rr < q.D) {
-                int ea = p.aexp[(size_t)q.iq * p.MP + r];
+            if (rr < q.D && tl.out) {
+                const int ea = p.aexp[(size_t)q.iq * p.MP + r] - 16;
+                const long long c0 = tl.ncol0 + half * 64, cend = q.colbase + q.ncols;
+                double *dst = reinterpret_cast<double *>(p.Y + c0 * p.RSc + p.N0 + rr) + (im ? 1 : 0);
+                const long long cstride = 2 * p.RSc;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    long long col = tl.ncol0 + half * 32 + j;
-                    if (col < q.colbase + q.ncols) {
-                        double v = ldexp((double)hi[j] + (double)lo[j], ea + p.zexp[col] - 16);
-                        double *dst = reinterpret_cast<double *>(p.Y + col * p.RSc + p.N0 + rr);
-                        dst[im ? 1 : 0] = v;
-                    }
+                for (int j = 0; j < 64; ++j) {
+                    if (c0 + j < cend) dst[j * cstride] = scale2((double)hi[j] + (double)lo[j], ea + p.zexp[c0 + j]);
                 }
             }
         }
     }
     tc_fence_before();
     __syncthreads();
+    // no CTA leaves while a peer may still multicast into it or release its stages
+    if (CS > 1) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, G1_TMEM);
@@ -556,6 +576,24 @@ int make_map_2d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, l
     return HFX_OK;
 }
 
+// 2-D BF16 tensor [rows][cols], box {box_cols, box_rows}, swizzle of box_cols*2 bytes (32, 64 or 128)
+int make_map_2d_sw(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows,
+                   int box_cols, int swizzle_bytes) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_err(ctx, HFX_EDEVICE, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                            : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                            : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_err(ctx, HFX_EDEVICE, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return HFX_OK;
+}
+
 int num_sms() {
     static int n = 0;
     if (!n) {
@@ -619,14 +657,21 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
                     const QDesc *d_q, int nq, const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc,
                     long long NC, int N0, int N0pad, int Dpad, int RS, void *d_tiles_buf, size_t tiles_cap) {
     int HS = N0pad + Dpad, MP = 2 * Dpad;
+    // clusters of G1_CS CTAs share the A rows of their tiles (multicast A)
+    constexpr int CS = G1_CS;
     std::vector<G1Tile> tiles;
     for (int s = 0; s < nq; ++s) {
         const QDesc &q = h_q[s];
         int klen = ((N0pad + q.D + G1_KC - 1) / G1_KC) * G1_KC;
         int mt = (q.D + G1_BM - 1) / G1_BM;   // tiles per half that touch real rows
-        for (long long n0 = 0; n0 < q.ncols; n0 += G1_BN)
-            for (int half = 0; half < 2; ++half)
-                for (int i = 0; i < mt; ++i) tiles.push_back(G1Tile{s, half * Dpad + i * G1_BM, (int)(q.colbase + n0), klen});
+        for (int half = 0; half < 2; ++half)
+            for (int i = 0; i < mt; ++i)
+                for (long long n0 = 0; n0 < q.ncols; n0 += (long long)G1_BN * CS)
+                    for (int j = 0; j < CS; ++j) {
+                        long long c0 = n0 + (long long)j * G1_BN;
+                        bool real = c0 < q.ncols;   // padding tiles repeat the group's first tile and write nothing
+                        tiles.push_back(G1Tile{s, half * Dpad + i * G1_BM, (int)(q.colbase + (real ? c0 : n0)), klen, real ? 1 : 0, 0});
+                    }
     }
     if (tiles.empty()) return HFX_OK;
     if (tiles.size() * sizeof(G1Tile) > tiles_cap) return set_err(ctx, HFX_ENOMEM, "gemm1 tile table too large");
@@ -635,11 +680,11 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
                                              cudaMemcpyHostToDevice, ctx->stream), "gemm1 tiles");
     if (rc) return rc;
     CUtensorMap mA, mB;
-    if ((rc = make_map_2d(ctx, &mA, d_Ap_all, ap_rows, RS, G1_BM))) return rc;
-    if ((rc = make_map_2d(ctx, &mB, d_ZS, (long long)NPL * NC, RS, G1_BN))) return rc;
+    if ((rc = make_map_2d_sw(ctx, &mA, d_Ap_all, ap_rows, RS, G1_BM / CS, G1_KC, 64))) return rc;
+    if ((rc = make_map_2d_sw(ctx, &mB, d_ZS, (long long)NPL * NC, RS, G1_BN, G1_KC, 64))) return rc;
     G1Params p;
     p.tiles = reinterpret_cast<const G1Tile *>(d_tiles_buf);
-    p.ntiles = (int)tiles.size();
+    p.ngroups = (int)(tiles.size() / CS);
     p.qd = d_q;
     p.aexp = d_aexp;
     p.zexp = d_zexp;
@@ -654,9 +699,32 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
     p.Dpad = Dpad;
     p.err = ctx->d_err;
     size_t smem = (size_t)G1_STAGES * G1_STAGE + 1024;
-    cudaFuncSetAttribute(gemm1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int grid = std::min<int>(num_sms(), p.ntiles);
-    gemm1_kernel<<<grid, 64 + 32 * G1_EPI, smem, ctx->stream>>>(mA, mB, p);
+    auto kern = gemm1_kernel<CS>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        // the register split of the kernel assumes this launch allocation
+        cudaFuncAttributes fa;
+        if ((rc = cuda_check(ctx, cudaFuncGetAttributes(&fa, kern), "gemm1 attributes"))) return rc;
+        if (fa.numRegs < G1_REG_LAUNCH)
+            return set_err(ctx, HFX_EUNSUPPORTED, "gemm1 compiled with fewer registers than its warpgroup split needs");
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(G1_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(num_sms() / CS * CS);
+    int ncl = 0;
+    if ((rc = cuda_check(ctx, cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg), "gemm1 cluster occupancy"))) return rc;
+    if (ncl < 1) return set_err(ctx, HFX_EUNSUPPORTED, "gemm1: no cluster fits on the device");
+    cfg.gridDim = dim3(std::min(ncl, p.ngroups) * CS);
+    if ((rc = cuda_check(ctx, cudaLaunchKernelEx(&cfg, kern, mA, mB, p), "gemm1 launch"))) return rc;
     return cuda_check(ctx, cudaGetLastError(), "gemm1 launch");
 }
 

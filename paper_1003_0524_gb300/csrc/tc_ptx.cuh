@@ -72,6 +72,36 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// ------------------------------------------------------------- clusters
+// TMA multicast and tcgen05.commit multicast reach the CTAs of this CTA's
+// cluster only (the GPU's own memory; nothing leaves the device).
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// 2-D tile load written to the same shared-memory offset of every CTA in mask,
+// completing bytes on the mbarrier at the same offset in each of them
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%3, "
+        "%4}], [%2], %5;" ::"r"(dst),
+        "l"((uint64_t)map), "r"(saddr(bar)), "r"(x), "r"(y), "h"(mask)
+        : "memory");
+}
+// arrive once on the mbarrier at this offset in every CTA of mask when the
+// tcgen05 operations issued so far have completed
+__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     saddr(bar)),
+                 "h"(mask)
+                 : "memory");
+}
+
 // 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16)
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -144,6 +174,22 @@ __device__ __forceinline__ uint64_t desc_ns(uint32_t addr, uint32_t lbo, uint32_
     d |= (uint64_t)1 << 46;
     return d;
 }
+
+// K-major operand, 64-byte swizzle (rows of 32 BF16): 8-row atoms of 512 bytes.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+// slice-product term t of the ten kept (i + j <= 3): weight class, slice of A, slice of B
+__device__ __forceinline__ constexpr int slice_term_w(int t) { return t < 1 ? 0 : t < 3 ? 1 : t < 6 ? 2 : 3; }
+__device__ __forceinline__ constexpr int slice_term_a(int t) { return t - slice_term_w(t) * (slice_term_w(t) + 1) / 2; }
+__device__ __forceinline__ constexpr int slice_term_b(int t) { return slice_term_w(t) - slice_term_a(t); }
 
 // Instruction descriptor: BF16 x BF16 -> FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -239,6 +285,8 @@ __device__ __forceinline__ void class_accumulate(float a0, float a1, float a2, f
 }
 
 int make_map_2d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows);
+int make_map_2d_sw(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows,
+                   int box_cols, int swizzle_bytes);
 int make_map_5d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, const unsigned long long dims[5],
                 const unsigned long long strides_bytes[4], const unsigned int box[5], int swizzle_bytes);
 int num_sms();
