@@ -29,6 +29,23 @@ UNIT = "s/SCF step"
 WORKLOAD = "zincblende 2-atom cell a=10.3 bohr, 4x4x4 k (4096 k,q pairs), 40 bands, 8 occupied, N_aux~635, sparse v(q)"
 
 
+def _profiled_traffic(kernel_file: str, profile: str):
+    """DRAM bytes per launch recorded by an ncu capture under profiles/, or None
+    when the kernel source changed since the capture."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        src = open(os.path.join(ROOT, "paper_1003_0524_gb300", "csrc", kernel_file), "rb").read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    h = re.search(r"source_sha256_prefix: ([0-9a-f]+)", text)
+    if not m or not h or hashlib.sha256(src).hexdigest()[:len(h.group(1))] != h.group(1):
+        return None
+    return int(m.group(1))
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -260,8 +277,9 @@ def run_ours(args):
             # every real multiply-add of the method expands into 10 BF16 slice products
             achieved = 10.0 * kernels[dom][1] / (kernels[dom][0] * 1e-3) / 1e12
             peak = peaks.get("bf16_tflops_sustained", 1700.0)
+            traffic = _profiled_traffic("k_zipw_tc.cu", "zipw_tc_kernel_config1.md") if dom == "zipw" else None
             roof = {"bound": "tensor", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic,
                     "peak_source": f"bf16_tflops_sustained ({peak_kind})",
                     "useful_tflops": kernels[dom][1] / (kernels[dom][0] * 1e-3) / 1e12,
                     "per_kernel_ms": {names[k]: kernels[k][0] for k in kernels}}

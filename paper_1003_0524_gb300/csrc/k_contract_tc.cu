@@ -664,9 +664,11 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
         const QDesc &q = h_q[s];
         int klen = ((N0pad + q.D + G1_KC - 1) / G1_KC) * G1_KC;
         int mt = (q.D + G1_BM - 1) / G1_BM;   // tiles per half that touch real rows
-        for (int half = 0; half < 2; ++half)
-            for (int i = 0; i < mt; ++i)
-                for (long long n0 = 0; n0 < q.ncols; n0 += (long long)G1_BN * CS)
+        // all row tiles of one column group back to back: the Z columns are read
+        // from HBM once and the Re and Im rows of Y meet in L2
+        for (long long n0 = 0; n0 < q.ncols; n0 += (long long)G1_BN * CS)
+            for (int half = 0; half < 2; ++half)
+                for (int i = 0; i < mt; ++i)
                     for (int j = 0; j < CS; ++j) {
                         long long c0 = n0 + (long long)j * G1_BN;
                         bool real = c0 < q.ncols;   // padding tiles repeat the group's first tile and write nothing
