@@ -46,19 +46,25 @@ __device__ __constant__ int kSW[NTERM] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 // For every column of the batch: exponent over its rows (real and imaginary
 // parts of rows [0, N0) and [N0, N0 + D_q) of Zc), then slices into
 // XS[p][col][u]: u in [0, HS) real parts, [HS, 2 HS) imaginary parts (mu=0
-// rows padded to N0pad, dense rows padded to Dpad).  One warp per column.
+// rows padded to N0pad, dense rows padded to Dpad).  One warp per column; in
+// the slicing pass each lane takes four consecutive rows, so every plane is
+// written with 8-byte stores (N0pad and HS are multiples of 64).
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
 template <typename V>
 __global__ void slice_cols_kernel(const V *__restrict__ Z, long long RSc, const QDesc *__restrict__ qd, int N0,
                                   int N0pad, int Dpad, int RS, long long NC, __nv_bfloat16 *__restrict__ XS,
                                   int *__restrict__ xexp) {
     const QDesc q = qd[blockIdx.y];
-    int HS = N0pad + Dpad;
-    int wpb = blockDim.x / 32, lane = threadIdx.x % 32;
-    long long plane = NC * RS;
+    const int HS = N0pad + Dpad;
+    const int wpb = blockDim.x / 32, lane = threadIdx.x % 32;
+    const long long plane = NC * RS;
     for (long long c = (long long)blockIdx.x * wpb + threadIdx.x / 32; c < q.ncols; c += (long long)gridDim.x * wpb) {
-        long long col = q.colbase + c;
+        const long long col = q.colbase + c;
         const V *z = Z + col * RSc;
-        int nrow = N0 + q.D;
+        const int nrow = N0 + q.D;
         unsigned long long mx = 0;
         for (int r = lane; r < nrow; r += 32) {
             V v = z[r];
@@ -66,26 +72,32 @@ __global__ void slice_cols_kernel(const V *__restrict__ Z, long long RSc, const 
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        int e = line_exp_bits(mx);
+        const int e = line_exp_bits(mx);
         if (lane == 0) xexp[col] = e;
-        size_t base = (size_t)col * RS;
-        for (int u = lane; u < HS; u += 32) {
-            int row = -1;
-            if (u < N0pad) row = (u < N0) ? u : -1;
-            else if (u - N0pad < q.D) row = N0 + (u - N0pad);
-            double xr = 0.0, xi = 0.0;
-            if (row >= 0) {
-                V v = z[row];
-                xr = (double)v.x;
-                xi = (double)v.y;
+        const long long base = col * RS;
+        for (int u0 = 4 * lane; u0 < HS; u0 += 128) {
+            // the four rows u0..u0+3 lie in one region (N0pad is a multiple of 64)
+            int row0, nvalid;
+            if (u0 < N0pad) { row0 = u0; nvalid = N0 - u0; }
+            else { row0 = N0 + (u0 - N0pad); nvalid = q.D - (u0 - N0pad); }
+            __nv_bfloat16 sr[4][NPL], si[4][NPL];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                double xr = 0.0, xi = 0.0;
+                if (t < nvalid) {
+                    V v = z[row0 + t];
+                    xr = (double)v.x;
+                    xi = (double)v.y;
+                }
+                slice4(xr, e, sr[t]);
+                slice4(xi, e, si[t]);
             }
-            __nv_bfloat16 sr[NPL], si[NPL];
-            slice4(xr, e, sr);
-            slice4(xi, e, si);
 #pragma unroll
             for (int p = 0; p < NPL; ++p) {
-                XS[p * plane + base + u] = sr[p];
-                XS[p * plane + base + HS + u] = si[p];
+                uint2 wr = make_uint2(pack_bf16x2(sr[0][p], sr[1][p]), pack_bf16x2(sr[2][p], sr[3][p]));
+                uint2 wi = make_uint2(pack_bf16x2(si[0][p], si[1][p]), pack_bf16x2(si[2][p], si[3][p]));
+                *reinterpret_cast<uint2 *>(XS + p * plane + base + u0) = wr;
+                *reinterpret_cast<uint2 *>(XS + p * plane + base + HS + u0) = wi;
             }
         }
     }
