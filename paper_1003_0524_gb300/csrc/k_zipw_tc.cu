@@ -12,11 +12,12 @@
 // product with the real and imaginary outputs side by side in N):
 //   A row (k', m) = [ Re C | Im C ]                       (128-byte swizzle, 2-D TMA)
 //   B columns     = [ T_r ; -T_i ] (real out), [ T_i ; T_r ] (imag out)
-// The sliced T box is stored in blocks of 8 z with both parts of an output
-// block and all bands of a band block contiguous, so the B operand of one
-// segment is a single 1-D bulk copy (no swizzle).  The segments of the lines
-// are aligned to those z blocks per z phase of W: the C slices come in eight
-// phase variants, T in one copy.
+// The sliced T box is stored in blocks of 8 z with all planes, both parts of
+// an output block and all bands of a band block contiguous, so the B operand
+// of one segment is a single 1-D bulk copy (no swizzle).  A copy must start on
+// a 16-byte boundary, i.e. at a multiple of 8 in z: T is kept in four copies
+// shifted by 0, 2, 4, 6 in z, and the segments of every line start on the
+// z parity of W (two phase variants of the C slices).
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -34,7 +35,8 @@ constexpr int ZT_A_PLANE = 128 * 64 * 2;   // 16 KB: 128 rows x 64 K
 constexpr int ZT_GROUP = 4;                // 64-K chunks per exact group (256)
 constexpr int ZT_STAGES = 2;
 constexpr int ZT_EPI = 8;
-constexpr int ZT_NPH = 8;                  // z phases of the segment grid
+constexpr int ZT_NPH = 2;                  // z phases of the segment grid (segment starts mod 2)
+constexpr int ZT_NCOPY = 8 / ZT_NPH;       // z-shifted copies of the sliced T box
 constexpr int ZT_NPART = 4;                // T parts: Re, Im, -Im, Re
 
 // slice-product term t: weight class w, slice of A, slice of B (a + b = w)
@@ -94,12 +96,14 @@ __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int
 
 // ------------------------------------------------------------- T slices
 // Grid (n, k) over the padded band range: exponent of band n of T_k over the
-// box, then the four parts (Re T, Im T, -Im T, Re T) of every plane p into
-//   Tq[k][X][Y][zb][h][b][p][part & 1][j][z & 7],  part = 2 h + (part & 1),
-// n = b NB + j, z = 8 zb + (z & 7); bands past nb(k) and z past the box are 0.
-// One (k, X, Y, zb, h, b) block -- all planes of one segment -- is contiguous.
+// box, then the four parts (Re T, Im T, -Im T, Re T) of every plane p of copy
+// c (T shifted by c * ZT_NPH in z) into
+//   Tq[c][k][X][Y][zb][h][b][p][part & 1][j][z & 7] = part(T_k[n](X, Y, z + c ZT_NPH)),
+// part = 2 h + (part & 1), n = b NB + j, z = 8 zb + (z & 7); bands past nb(k)
+// and z past the box are 0.  One (c, k, X, Y, zb, h, b) block -- all planes of
+// one segment -- is contiguous.
 __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int *__restrict__ nb_k, int td0, int td1,
-                                int td2, int nzb, int NB, int nblk, int nbmax, const int *__restrict__ kslot,
+                                int td2, int nzb, int NB, int nblk, int nbmax, int nslot, const int *__restrict__ kslot,
                                 __nv_bfloat16 *__restrict__ Tq, int *__restrict__ eT) {
     int n = blockIdx.x, k = blockIdx.y;
     int slot = kslot[k];
@@ -123,15 +127,18 @@ __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int
     const long long zspan = (long long)nzb * 8;
     const long long npts = (long long)td0 * td1 * zspan;
     const long long blk = 2LL * NB * 8;                       // one (h, b) block: 2 parts x NB bands x 8 z
-    for (long long i = threadIdx.x; i < npts; i += blockDim.x) {
-        int z = (int)(i % zspan);
-        long long xy = i / zspan;
-        double2 v = (live && z < td2) ? T[xy * td2 + z] : make_double2(0.0, 0.0);
+    for (long long i = threadIdx.x; i < npts * ZT_NCOPY; i += blockDim.x) {
+        const int c = (int)(i / npts);
+        const long long ip = i % npts;
+        int z = (int)(ip % zspan);
+        long long xy = ip / zspan;
+        const int zz = z + c * ZT_NPH;
+        double2 v = (live && zz < td2) ? T[xy * td2 + zz] : make_double2(0.0, 0.0);
         __nv_bfloat16 sr[NPL], si[NPL];
         slice4(v.x, e, sr);
         slice4(v.y, e, si);
         const int zb = z >> 3, z8 = z & 7;
-        const long long cell = ((long long)slot * td0 * td1 + xy) * nzb + zb;   // (k, X, Y, zb)
+        const long long cell = (((long long)c * nslot + slot) * td0 * td1 + xy) * nzb + zb;   // (c, k, X, Y, zb)
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
             __nv_bfloat16 part[ZT_NPART] = {sr[p], si[p], __hneg(si[p]), sr[p]};
@@ -160,10 +167,10 @@ struct ZParams {
     const int *rowk, *rowm;       // rows of A (k', m)
     const int *aexp, *eT;         // row exponents, [k][n] band exponents
     const int *kslot;             // k -> slot of its T slices
-    const int *segoff;            // [phase][segment] cell offset of the segment's T block
+    const int2 *segoff;           // [phase][segment] (x td1 + y of its line, z0 - phase)
     int nsegp_max;
     const __nv_bfloat16 *Tq;      // sliced T blocks (t_slices_kernel layout)
-    int td0, td1, nzb, nblk;
+    int td0, td1, nzb, nblk, nslot;
     int nchunk[ZT_NPH];           // 64-K chunks per K half, per phase
     double2 *Z;
     long long RSc;
@@ -210,7 +217,6 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
         uint32_t ph = 0;
         int issued = 0;
         const int bj = lane & 7;
-        const long long slot_cells = (long long)p.td0 * p.td1 * p.nzb;
         const long long cellb = 2LL * p.nblk * SEG4;
         const char *tq = reinterpret_cast<const char *>(p.Tq);
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
@@ -218,11 +224,12 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             const int4 W = p.wxyz[tl.w];
             const int phz = W.w, nch = p.nchunk[phz];
             const int slot = p.kslot[tl.k];
-            const int *so = p.segoff + (size_t)phz * p.nsegp_max;
-            // T block cell of a segment = (k, p) plane + tile shift + segment offset;
-            // X, Y inside the T box and z a whole block inside it by construction
-            const long long tb = ((long long)(W.x - p.tlo0) * p.td1 + (W.y - p.tlo1)) * p.nzb + ((W.z + phz - p.tlo2) >> 3);
-            const long long kbase = (long long)slot * slot_cells + tb;
+            const int2 *so = p.segoff + (size_t)phz * p.nsegp_max;
+            // a segment starts at X = W_x + x - tlo_x, Y likewise, and T z index
+            // Zs = (W_z + ph - tlo_z) + (z0 - ph), a multiple of ZT_NPH: copy
+            // c = (Zs mod 8) / ZT_NPH, z block Zs / 8 -- inside the box by construction
+            const int bxy = (W.x - p.tlo0) * p.td1 + (W.y - p.tlo1);
+            const int bz = W.z + phz - p.tlo2;
             bool stop = false;
             for (int c = 0; c < 2 * nch; ++c) {
                 int ok = 1;
@@ -238,9 +245,14 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                     tma_load_2d(saddr(st + lane * ZT_A_PLANE), &tmA, &full_bar[s], h * p.Kh + cl * 64,
                                 (phz * NPL + lane) * p.Rpad + tl.mrow);
                 const long long hb = ((long long)h * p.nblk + tl.nblk) * SEG4;
-                if (lane < 8)
-                    bulk_load(saddr(st + NPL * ZT_A_PLANE + bj * SEG4), tq + (kbase + so[cl * 8 + bj]) * cellb + hb, SEG4,
-                              &full_bar[s]);
+                if (lane < 8) {
+                    const int2 sg = so[cl * 8 + bj];
+                    const int Zs = bz + sg.y;
+                    const int cp = (Zs & 7) / ZT_NPH;
+                    const long long cell =
+                        (((long long)cp * p.nslot + slot) * ((long long)p.td0 * p.td1) + bxy + sg.x) * p.nzb + (Zs >> 3);
+                    bulk_load(saddr(st + NPL * ZT_A_PLANE + bj * SEG4), tq + cell * cellb + hb, SEG4, &full_bar[s]);
+                }
                 ++issued;
                 if (++s == ZT_STAGES) { s = 0; ph ^= 1; }
             }
@@ -419,12 +431,12 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
             lzhi.push_back(zhi[b]);
         }
     const int nL = (int)lx.size();
-    // segment grid per z phase: segments of a line start at z0 = ph (mod 8)
+    // segment grid per z phase: segments of a line start at z0 = ph (mod ZT_NPH)
     std::vector<int> segstart((size_t)ZT_NPH * nL), segz0((size_t)ZT_NPH * nL), nseg(ZT_NPH);
     std::vector<std::vector<int4>> segs(ZT_NPH);
     for (int ph = 0; ph < ZT_NPH; ++ph) {
         for (int l = 0; l < nL; ++l) {
-            int z0 = lzlo[l] - (((lzlo[l] - ph) % 8) + 8) % 8;
+            int z0 = lzlo[l] - (((lzlo[l] - ph) % ZT_NPH) + ZT_NPH) % ZT_NPH;
             segstart[(size_t)ph * nL + l] = (int)segs[ph].size();
             segz0[(size_t)ph * nL + l] = z0;
             for (int z = z0; z <= lzhi[l]; z += 8) segs[ph].push_back(make_int4(lx[l], ly[l], z, 0));
@@ -435,15 +447,15 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     for (int ph = 0; ph < ZT_NPH; ++ph) nsegp_max = std::max(nsegp_max, (nseg[ph] + 7) / 8 * 8);
     const int Kh = nsegp_max * 8;
     const int nzb = (in.tdim[2] + 7) / 8;
-    // cell offset of every segment in the sliced T box, relative to the tile
-    // shift (X, Y, zb) = (W_x - tlo_x, W_y - tlo_y, (W_z + ph - tlo_z) / 8)
-    std::vector<int> segtab((size_t)ZT_NPH * nsegp_max);
+    // every segment: (x td1 + y) of its line and z0 - ph, offsets from the tile
+    // shift (W_x - tlo_x) td1 + (W_y - tlo_y) and W_z + ph - tlo_z
+    std::vector<int2> segtab((size_t)ZT_NPH * nsegp_max);
     int nchunk[ZT_NPH];
     for (int ph = 0; ph < ZT_NPH; ++ph) {
         nchunk[ph] = (nseg[ph] + 7) / 8;
         for (int s2 = 0; s2 < nsegp_max; ++s2) {
             const int4 sg = s2 < nseg[ph] ? segs[ph][s2] : segs[ph][0];   // padding: any valid block
-            segtab[(size_t)ph * nsegp_max + s2] = (sg.x * in.tdim[1] + sg.y) * nzb + (sg.z - ph) / 8;
+            segtab[(size_t)ph * nsegp_max + s2] = make_int2(sg.x * in.tdim[1] + sg.y, sg.z - ph);
         }
     }
     // ---- rows (k', m) of every k'
@@ -512,8 +524,8 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
             const int widx = (int)wxyz.size();
             const int w2 = (int)(wi % wd[2]), w1 = (int)((wi / wd[2]) % wd[1]), w0 = (int)(wi / ((size_t)wd[1] * wd[2]));
             const int Wz = w2 + amin[2];
-            // z phase: the T z index of every segment start is a multiple of 8
-            wxyz.push_back(make_int4(w0 + amin[0], w1 + amin[1], Wz, (((in.tlo[2] - Wz) % 8) + 8) % 8));
+            // z phase: the T z index of every segment start is a multiple of ZT_NPH
+            wxyz.push_back(make_int4(w0 + amin[0], w1 + amin[1], Wz, (((in.tlo[2] - Wz) % ZT_NPH) + ZT_NPH) % ZT_NPH));
             for (int t = 0; t < nmtile; ++t)
                 if (need[wi * nmtile + t])
                     for (int b = 0; b < nblk; ++b) tiles.push_back(ZTile{ik, widx, t * ZT_BM, b});
@@ -539,20 +551,20 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         for (const int4 &W : wxyz) {
             const int Z0 = W.z + z00[W.w] - in.tlo[2], Z1 = W.z + z01[W.w] - in.tlo[2];
             if (W.x + sx0 - in.tlo[0] < 0 || W.x + sx1 - in.tlo[0] >= in.tdim[0] || W.y + sy0 - in.tlo[1] < 0 ||
-                W.y + sy1 - in.tlo[1] >= in.tdim[1] || Z0 < 0 || (Z0 & 7) != 0 || (Z1 >> 3) >= nzb)
+                W.y + sy1 - in.tlo[1] >= in.tdim[1] || Z0 < 0 || (Z0 % ZT_NPH) != 0 || (Z1 >> 3) >= nzb)
                 return set_err(ctx, HFX_EUNSUPPORTED, "interstitial segment outside the step-function box");
         }
     }
     // ---- device buffers (scratch s_zipw)
     const int nbpad = nblk * NBt;
-    const size_t tp_elems = (size_t)nslot * NPL * ZT_NPART * nbpad * in.tdim[0] * in.tdim[1] * nzb * 8;
+    const size_t tp_elems = (size_t)ZT_NCOPY * nslot * NPL * ZT_NPART * nbpad * in.tdim[0] * in.tdim[1] * nzb * 8;
     const size_t a_elems = (size_t)ZT_NPH * NPL * Rpad * 2 * Kh;
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
     const size_t o_tp = place(tp_elems * 2), o_a = place(a_elems * 2), o_aexp = place((size_t)Rpad * 4),
                  o_eT = place((size_t)nk * in.nb_max * 4), o_rowk = place((size_t)R * 4), o_rowm = place((size_t)R * 4),
                  o_line = place(line_of.size() * 4), o_sst = place(segstart.size() * 4), o_sz0 = place(segz0.size() * 4),
-                 o_seg = place(segtab.size() * sizeof(int)), o_gtab = place(gtab.size() * 4),
+                 o_seg = place(segtab.size() * sizeof(int2)), o_gtab = place(gtab.size() * 4),
                  o_pinfo = place(pinfo.size() * sizeof(ZPairInfo)), o_w = place(wxyz.size() * sizeof(int4)),
                  o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4);
     if ((rc = scratch_reserve(ctx, ctx->s_zipw, off))) return rc;
@@ -562,7 +574,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     };
     if ((rc = up(o_rowk, rowk.data(), R * 4)) || (rc = up(o_rowm, rowm.data(), R * 4)) ||
         (rc = up(o_line, line_of.data(), line_of.size() * 4)) || (rc = up(o_sst, segstart.data(), segstart.size() * 4)) ||
-        (rc = up(o_sz0, segz0.data(), segz0.size() * 4)) || (rc = up(o_seg, segtab.data(), segtab.size() * sizeof(int))) ||
+        (rc = up(o_sz0, segz0.data(), segz0.size() * 4)) || (rc = up(o_seg, segtab.data(), segtab.size() * sizeof(int2))) ||
         (rc = up(o_gtab, gtab.data(), gtab.size() * 4)) ||
         (rc = up(o_pinfo, pinfo.data(), pinfo.size() * sizeof(ZPairInfo))) ||
         (rc = up(o_w, wxyz.data(), wxyz.size() * sizeof(int4))) ||
@@ -577,7 +589,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                                        By, nL, reinterpret_cast<int *>(b + o_sst), reinterpret_cast<int *>(b + o_sz0), Kh, Rpad, A,
                                        aexp);
     t_slices_kernel<<<dim3(nbpad, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], nzb, NBt, nblk,
-                                                     in.nb_max, reinterpret_cast<int *>(b + o_kslot), Tp, eT);
+                                                     in.nb_max, nslot, reinterpret_cast<int *>(b + o_kslot), Tp, eT);
     if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw slices"))) return rc;
     // ---- tensor maps
     CUtensorMap mA;
@@ -596,13 +608,14 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     p.aexp = aexp;
     p.eT = eT;
     p.kslot = reinterpret_cast<int *>(b + o_kslot);
-    p.segoff = reinterpret_cast<int *>(b + o_seg);
+    p.segoff = reinterpret_cast<int2 *>(b + o_seg);
     p.nsegp_max = nsegp_max;
     p.Tq = Tp;
     p.td0 = in.tdim[0];
     p.td1 = in.tdim[1];
     p.nzb = nzb;
     p.nblk = nblk;
+    p.nslot = nslot;
     for (int ph = 0; ph < ZT_NPH; ++ph) p.nchunk[ph] = nchunk[ph];
     p.Z = in.d_Z;
     p.RSc = in.RSc;
