@@ -285,9 +285,9 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
             const QDesc q = p.qd[tl.qslot];
             int nchunk = 2 * (tl.klen / G1_KC);
             int ngroups = (nchunk + G1_GROUP - 1) / G1_GROUP;
-            float hi[64], lo[64];
+            uint64_t hi[32], lo[32];   // packed pairs of columns
 #pragma unroll
-            for (int j = 0; j < 64; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
             for (int gg = 0; gg < ngroups; ++gg) {
                 if (!mbar_wait(&tfull_bar, eph, &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
                 tc_fence_after();
@@ -306,9 +306,9 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                         if (lane == 0) mbar_arrive(&tempty_bar);
                     }
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        class_accumulate(__uint_as_float(a0[j]), __uint_as_float(a1[j]), __uint_as_float(a2[j]),
-                                         __uint_as_float(a3[j]), 1.0f, hi[c0 + j], lo[c0 + j]);
+                    for (int j = 0; j < 8; j += 2)
+                        class_accumulate2(f2_pack(a0[j], a0[j + 1]), f2_pack(a1[j], a1[j + 1]), f2_pack(a2[j], a2[j + 1]),
+                                          f2_pack(a3[j], a3[j + 1]), hi[(c0 + j) / 2], lo[(c0 + j) / 2]);
                 }
                 eph ^= 1;
             }
@@ -322,8 +322,10 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                 double *dst = reinterpret_cast<double *>(p.Y + c0 * p.RSc + p.N0 + rr) + (im ? 1 : 0);
                 const long long cstride = 2 * p.RSc;
 #pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    if (c0 + j < cend) dst[j * cstride] = scale2((double)hi[j] + (double)lo[j], ea + p.zexp[c0 + j]);
+                for (int j = 0; j < 64; j += 2) {
+                    const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
+                    if (c0 + j < cend) dst[j * cstride] = scale2((double)h.x + (double)l.x, ea + p.zexp[c0 + j]);
+                    if (c0 + j + 1 < cend) dst[(j + 1) * cstride] = scale2((double)h.y + (double)l.y, ea + p.zexp[c0 + j + 1]);
                 }
             }
         }

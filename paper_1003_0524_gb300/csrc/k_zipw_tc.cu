@@ -311,9 +311,9 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             const ZTile tl = p.tiles[t];
             const int4 W = p.wxyz[tl.w];
             const int ngroups = (2 * p.nchunk[W.w] + ZT_GROUP - 1) / ZT_GROUP;
-            float hr[NH], lr[NH], hm[NH], lm[NH];
+            uint64_t hr[NH / 2], lr[NH / 2], hm[NH / 2], lm[NH / 2];   // packed pairs of columns
 #pragma unroll
-            for (int j = 0; j < NH; ++j) { hr[j] = 0.f; lr[j] = 0.f; hm[j] = 0.f; lm[j] = 0.f; }
+            for (int j = 0; j < NH / 2; ++j) { hr[j] = 0; lr[j] = 0; hm[j] = 0; lm[j] = 0; }
             for (int g = 0; g < ngroups; ++g) {
                 if (!mbar_wait(&tfull_bar, eph, &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
                 tc_fence_after();
@@ -336,11 +336,11 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                         if (lane == 0) mbar_arrive(&tempty_bar);
                     }
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        class_accumulate(__uint_as_float(a0[j]), __uint_as_float(a1[j]), __uint_as_float(a2[j]),
-                                         __uint_as_float(a3[j]), 1.0f, hr[c0 + j], lr[c0 + j]);
-                        class_accumulate(__uint_as_float(b0[j]), __uint_as_float(b1[j]), __uint_as_float(b2[j]),
-                                         __uint_as_float(b3[j]), 1.0f, hm[c0 + j], lm[c0 + j]);
+                    for (int j = 0; j < 4; j += 2) {
+                        class_accumulate2(f2_pack(a0[j], a0[j + 1]), f2_pack(a1[j], a1[j + 1]), f2_pack(a2[j], a2[j + 1]),
+                                          f2_pack(a3[j], a3[j + 1]), hr[(c0 + j) / 2], lr[(c0 + j) / 2]);
+                        class_accumulate2(f2_pack(b0[j], b0[j + 1]), f2_pack(b1[j], b1[j + 1]), f2_pack(b2[j], b2[j + 1]),
+                                          f2_pack(b3[j], b3[j + 1]), hm[(c0 + j) / 2], lm[(c0 + j) / 2]);
                     }
                 }
                 eph ^= 1;
@@ -364,9 +364,12 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                             const int n = tl.nblk * NB + cs * NH + jj;
                             if (n < pr.nb) {
                                 const int ex = ea + eTk[n];
+                                const float2 h1 = f2_unpack(hr[jj / 2]), l1 = f2_unpack(lr[jj / 2]);
+                                const float2 h2 = f2_unpack(hm[jj / 2]), l2 = f2_unpack(lm[jj / 2]);
+                                const bool odd = jj & 1;
                                 double2 v;
-                                v.x = scale2((double)hr[jj] + (double)lr[jj], ex) * p.rs;
-                                v.y = scale2((double)hm[jj] + (double)lm[jj], ex) * p.rs;
+                                v.x = scale2((double)(odd ? h1.y : h1.x) + (double)(odd ? l1.y : l1.x), ex) * p.rs;
+                                v.y = scale2((double)(odd ? h2.y : h2.x) + (double)(odd ? l2.y : l2.x), ex) * p.rs;
                                 long long col = pr.col0 + (long long)m * pr.nb + n;
                                 __stcs(p.Z + col * p.RSc + p.nmt + g, v);   // streaming: keep the operands in L2
                             }

@@ -284,6 +284,48 @@ __device__ __forceinline__ void class_accumulate(float a0, float a1, float a2, f
     lo += er + c * (0x1p-8f * sc);
 }
 
+// Packed FP32 pairs (two columns per instruction; each lane rounds to nearest
+// exactly as the scalar operation does).
+__device__ __forceinline__ uint64_t f2_pack(uint32_t x, uint32_t y) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(x), "r"(y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t v) {
+    uint32_t x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(x), "=r"(y) : "l"(v));
+    return make_float2(__uint_as_float(x), __uint_as_float(y));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// class_accumulate (sc = 1) for two columns at once; a_w hold the class sums
+// of the two columns as packed pairs.
+__device__ __forceinline__ void class_accumulate2(uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, uint64_t &hi,
+                                                  uint64_t &lo) {
+    const uint64_t s8 = f2_pack(0x3b800000u, 0x3b800000u);   // 2^-8, 2^-8
+    uint64_t c = f2_fma(a3, s8, a2);
+    c = f2_fma(c, s8, a1);
+    const uint64_t s = f2_add(hi, a0);
+    const uint64_t bb = f2_sub(s, hi);
+    const uint64_t er = f2_add(f2_sub(hi, f2_sub(s, bb)), f2_sub(a0, bb));
+    hi = s;
+    lo = f2_add(lo, f2_fma(c, s8, er));
+}
+
 int make_map_2d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows);
 int make_map_2d_sw(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows,
                    int box_cols, int swizzle_bytes);
