@@ -172,9 +172,9 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             const CgTile tl = p.tiles[t];
             int ngroups = (tl.nchunk + CG_GROUP - 1) / CG_GROUP;
-            float hi[32], lo[32];
+            uint64_t hi[16], lo[16];   // packed pairs of columns
 #pragma unroll
-            for (int j = 0; j < 32; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
             for (int g = 0; g < ngroups; ++g) {
                 if (!mbar_wait(&tfull_bar[buf], buf_ph[buf], &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
                 tc_fence_after();
@@ -188,9 +188,9 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
                     tmem_ld16(tb + 3 * CG_BN + c0, a3);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        class_accumulate(__uint_as_float(a0[j]), __uint_as_float(a1[j]), __uint_as_float(a2[j]),
-                                         __uint_as_float(a3[j]), 1.0f, hi[c0 + j], lo[c0 + j]);
+                    for (int j = 0; j < 16; j += 2)
+                        class_accumulate2(f2_pack(a0[j], a0[j + 1]), f2_pack(a1[j], a1[j + 1]), f2_pack(a2[j], a2[j + 1]),
+                                          f2_pack(a3[j], a3[j + 1]), hi[(c0 + j) / 2], lo[(c0 + j) / 2]);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -209,8 +209,9 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
                     const int c = tl.brow + half * 32 + j;
                     const long long co = co_tab[c >> 1];
                     if (co >= 0) {
-                        double re = scale2((double)hi[j] + (double)lo[j], ea + p.bexp[c]);
-                        double im = scale2((double)hi[j + 1] + (double)lo[j + 1], ea + p.bexp[c + 1]);
+                        const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
+                        double re = scale2((double)h.x + (double)l.x, ea + p.bexp[c]);
+                        double im = scale2((double)h.y + (double)l.y, ea + p.bexp[c + 1]);
                         if (p.phase) {
                             const double2 f = p.phase[tl.phb + p.pkey[c >> 1]];
                             const double x = re * f.x - im * f.y;

@@ -494,9 +494,9 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
             const PairDesc pr = p.pairs[tl.pair];
             const QDesc q = p.qd[pr.qslot];
             int nc = g2_chunks(q, p.N0pad);
-            float hi[CW], lo[CW];
+            uint64_t hi[CW / 2], lo[CW / 2];   // packed pairs of columns
 #pragma unroll
-            for (int j = 0; j < CW; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int j = 0; j < CW / 2; ++j) { hi[j] = 0; lo[j] = 0; }
             for (int m = 0; m < pr.no && ok; ++m) {
                 long long cola = pr.col0 + (long long)m * pr.nb + tl.bi * NB + (row % NB);
                 long long colb0 = pr.col0 + (long long)m * pr.nb + tl.bj * NB;
@@ -507,28 +507,21 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                     uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + cg * CW;
 #pragma unroll
                     for (int c0 = 0; c0 < CW; c0 += 8) {
-                        uint32_t x[8], y[8];
-                        float c[8];
-                        // classes 3 and 2, then 1, then the exact class 0
-                        tmem_ld8(tb + 3 * W + c0, x);
-                        tmem_ld8(tb + 2 * W + c0, y);
+                        uint32_t a0[8], a1[8], a2[8], a3[8];
+                        tmem_ld8(tb + 0 * W + c0, a0);
+                        tmem_ld8(tb + 1 * W + c0, a1);
+                        tmem_ld8(tb + 2 * W + c0, a2);
+                        tmem_ld8(tb + 3 * W + c0, a3);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) c[j] = fmaf(__uint_as_float(x[j]), 0x1p-8f, __uint_as_float(y[j]));
-                        tmem_ld8(tb + 1 * W + c0, x);
-                        tmem_ld8(tb + 0 * W + c0, y);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                        for (int j = 0; j < 8; j += 2) {
                             int b = cg * CW + c0 + j;
-                            float sc = ldexpf(1.0f, ea + p.yexp[min(colb0 + (b % NB), p.NC - 1)]);
-                            float cc = fmaf(c[j], 0x1p-8f, __uint_as_float(x[j]));
-                            float xv = __uint_as_float(y[j]) * sc;
-                            float s2 = hi[c0 + j] + xv;
-                            float bb = s2 - hi[c0 + j];
-                            float er = (hi[c0 + j] - (s2 - bb)) + (xv - bb);
-                            hi[c0 + j] = s2;
-                            lo[c0 + j] += er + cc * (0x1p-8f * sc);
+                            float s0 = ldexpf(1.0f, ea + p.yexp[min(colb0 + (b % NB), p.NC - 1)]);
+                            float s1 = ldexpf(1.0f, ea + p.yexp[min(colb0 + ((b + 1) % NB), p.NC - 1)]);
+                            class_accumulate2_sc(f2_pack(a0[j], a0[j + 1]), f2_pack(a1[j], a1[j + 1]),
+                                                 f2_pack(a2[j], a2[j + 1]), f2_pack(a3[j], a3[j + 1]),
+                                                 f2_pack(__float_as_uint(s0), __float_as_uint(s1)), hi[(c0 + j) / 2],
+                                                 lo[(c0 + j) / 2]);
                         }
                     }
                     tc_fence_before();
@@ -543,7 +536,11 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                 double *out = p.praw + p.praw_off[tl.pair] + ((size_t)tl.bi * nblk + tl.bj) * W * W + (size_t)row * W +
                               cg * CW;
 #pragma unroll
-                for (int j = 0; j < CW; ++j) out[j] = (double)hi[j] + (double)lo[j];
+                for (int j = 0; j < CW; j += 2) {
+                    const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
+                    out[j] = (double)h.x + (double)l.x;
+                    out[j + 1] = (double)h.y + (double)l.y;
+                }
             }
         }
     }

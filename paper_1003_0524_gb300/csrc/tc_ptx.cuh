@@ -306,6 +306,11 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
     uint64_t r;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
@@ -324,6 +329,20 @@ __device__ __forceinline__ void class_accumulate2(uint64_t a0, uint64_t a1, uint
     const uint64_t er = f2_add(f2_sub(hi, f2_sub(s, bb)), f2_sub(a0, bb));
     hi = s;
     lo = f2_add(lo, f2_fma(c, s8, er));
+}
+
+// class_accumulate for two columns with per-column scales sc (packed pair)
+__device__ __forceinline__ void class_accumulate2_sc(uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, uint64_t sc,
+                                                     uint64_t &hi, uint64_t &lo) {
+    const uint64_t s8 = f2_pack(0x3b800000u, 0x3b800000u);   // 2^-8, 2^-8
+    uint64_t c = f2_fma(a3, s8, a2);
+    c = f2_fma(c, s8, a1);
+    const uint64_t x = f2_mul(a0, sc);
+    const uint64_t s = f2_add(hi, x);
+    const uint64_t bb = f2_sub(s, hi);
+    const uint64_t er = f2_add(f2_sub(hi, f2_sub(s, bb)), f2_sub(x, bb));
+    hi = s;
+    lo = f2_add(lo, f2_fma(c, f2_mul(s8, sc), er));
 }
 
 int make_map_2d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows);
