@@ -670,7 +670,9 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> s1ev, ctev;
     double flops = 0.0, fl_apply = 0.0, fl_zhy = 0.0, fl_zipw = 0.0;
     int npairs_total = 0;
-    int nlaunch = 1 + 2 * (int)kset.size();  // theta + per-k B and Theta-psi
+    // theta + per-k B (+ per-k Theta-psi in FP64; in the sliced build the Toeplitz
+    // and band slices, the T product, and the two Z^MT operand slicings)
+    int nlaunch = 1 + (tc ? (int)kset.size() + 5 : 2 * (int)kset.size());
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_zipw, ev_apply, ev_zhy, ev_zipw_gemm;
 
     for (Batch &bt : batches) {
@@ -822,7 +824,7 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
             if (rc) return set_err(ctx, rc, "interstitial kernel does not fit this size");
         }
         ev_zipw.push_back({ez0, evs.make(ctx)});
-        nlaunch += 2;
+        nlaunch += tc ? 4 : 2;   // Z^MT; Z^IPW (sliced: C slices, T slices, GEMM)
         for (int i = 0; i < npairs; ++i) {
             auto it = ctx->zover.find(std::make_pair(bt.pairs[i].ik, bt.pairs[i].iq));
             if (it == ctx->zover.end()) continue;
