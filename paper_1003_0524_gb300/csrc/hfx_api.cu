@@ -824,7 +824,7 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
             if (rc) return set_err(ctx, rc, "interstitial kernel does not fit this size");
         }
         ev_zipw.push_back({ez0, evs.make(ctx)});
-        nlaunch += tc ? 4 : 2;   // Z^MT; Z^IPW (sliced: C slices, T slices, GEMM)
+        nlaunch += tc ? 5 : 2;   // Z^MT; Z^IPW (sliced: C slices, T exponents, T slices, GEMM)
         for (int i = 0; i < npairs; ++i) {
             auto it = ctx->zover.find(std::make_pair(bt.pairs[i].ik, bt.pairs[i].iq));
             if (it == ctx->zover.end()) continue;

@@ -44,6 +44,10 @@ __device__ __forceinline__ constexpr int term_w(int t) { return t < 1 ? 0 : t < 
 __device__ __forceinline__ constexpr int term_a(int t) { return t - term_w(t) * (term_w(t) + 1) / 2; }
 __device__ __forceinline__ constexpr int term_b(int t) { return term_w(t) - term_a(t); }
 
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
 __device__ __forceinline__ double scale2(double d, int k) {
     long long b = __double_as_longlong(d);
     if ((b << 1) == 0) return d;
@@ -95,58 +99,83 @@ __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int
 }
 
 // ------------------------------------------------------------- T slices
-// Grid (n, k) over the padded band range: exponent of band n of T_k over the
-// box, then the four parts (Re T, Im T, -Im T, Re T) of every plane p of copy
-// c (T shifted by c * ZT_NPH in z) into
-//   Tq[c][k][X][Y][zb][h][b][p][part & 1][j][z & 7] = part(T_k[n](X, Y, z + c ZT_NPH)),
-// part = 2 h + (part & 1), n = b NB + j, z = 8 zb + (z & 7); bands past nb(k)
-// and z past the box are 0.  One (c, k, X, Y, zb, h, b) block -- all planes of
-// one segment -- is contiguous.
-__global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int *__restrict__ nb_k, int td0, int td1,
-                                int td2, int nzb, int NB, int nblk, int nbmax, int nslot, const int *__restrict__ kslot,
-                                __nv_bfloat16 *__restrict__ Tq, int *__restrict__ eT) {
+// Band exponents: grid (n, k) over the bands, max over the box of T_k[n].
+__global__ void t_exp_kernel(const double2 *const *__restrict__ Tk, const int *__restrict__ nb_k, int td0, int td1,
+                             int td2, int nbmax, const int *__restrict__ kslot, int *__restrict__ eT) {
     int n = blockIdx.x, k = blockIdx.y;
-    int slot = kslot[k];
-    if (slot < 0) return;
-    const bool live = n < nb_k[k];
+    if (kslot[k] < 0 || n >= nb_k[k]) return;
     long long box = (long long)td0 * td1 * td2;
-    const double2 *T = live ? Tk[k] + (size_t)n * box : nullptr;
+    const double2 *T = Tk[k] + (size_t)n * box;
     __shared__ unsigned long long red[256];
     unsigned long long mx = 0;
-    if (live)
-        for (long long i = threadIdx.x; i < box; i += blockDim.x) mx = max(mx, max(abs_bits(T[i].x), abs_bits(T[i].y)));
+    for (long long i = threadIdx.x; i < box; i += blockDim.x) mx = max(mx, max(abs_bits(T[i].x), abs_bits(T[i].y)));
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
         if (threadIdx.x < st) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + st]);
         __syncthreads();
     }
-    int e = line_exp_bits(red[0]);
-    if (threadIdx.x == 0 && n < nbmax) eT[(size_t)k * nbmax + n] = e;
+    if (threadIdx.x == 0) eT[(size_t)k * nbmax + n] = line_exp_bits(red[0]);
+}
+
+// Slices of T: one thread per (k, cell (X, Y, zb), band n) slices the 14 values
+// T_k[n](X, Y, 8 zb .. 8 zb + 13) once and writes, for every copy c (T shifted
+// by c * ZT_NPH in z), plane p and part (Re T, Im T, -Im T, Re T), the 8 z
+// values of its row into
+//   Tq[c][k][X][Y][zb][h][b][p][part & 1][j][0..7],  part = 2 h + (part & 1),
+// n = b NB + j; bands past nb(k) and z past the box are 0.  Consecutive threads
+// take consecutive bands, so each 16-byte row store is coalesced.  One
+// (c, k, X, Y, zb, h, b) block -- all planes of one segment -- is contiguous.
+__global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int *__restrict__ nb_k, int td0, int td1,
+                                int td2, int nzb, int NB, int nblk, int nbmax, int nslot, const int *__restrict__ kslot,
+                                const int *__restrict__ eT, __nv_bfloat16 *__restrict__ Tq) {
+    constexpr int NZ = 8 + (ZT_NCOPY - 1) * ZT_NPH;           // z values a thread needs
+    const int k = blockIdx.y;
+    const int slot = kslot[k];
+    if (slot < 0) return;
+    const int nbpad = NB * nblk;
+    const long long ncell = (long long)td0 * td1 * nzb;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ncell * nbpad) return;
+    const int n = (int)(idx % nbpad);
+    const long long cellk = idx / nbpad;                      // (X, Y, zb) of this k
+    const int zb = (int)(cellk % nzb);
+    const long long xy = cellk / nzb;
+    const bool live = n < nb_k[k];
+    const long long box = (long long)td0 * td1 * td2;
+    const double2 *T = live ? Tk[k] + (size_t)n * box + xy * td2 : nullptr;
+    const int e = live ? eT[(size_t)k * nbmax + n] : 0;
+    __nv_bfloat16 sr[NZ][NPL], si[NZ][NPL];
+#pragma unroll
+    for (int t = 0; t < NZ; ++t) {
+        const int z = zb * 8 + t;
+        const double2 v = (live && z < td2) ? T[z] : make_double2(0.0, 0.0);
+        slice4(v.x, e, sr[t]);
+        slice4(v.y, e, si[t]);
+    }
     const int b = n / NB, j = n % NB;
-    const long long zspan = (long long)nzb * 8;
-    const long long npts = (long long)td0 * td1 * zspan;
-    const long long blk = 2LL * NB * 8;                       // one (h, b) block: 2 parts x NB bands x 8 z
-    for (long long i = threadIdx.x; i < npts * ZT_NCOPY; i += blockDim.x) {
-        const int c = (int)(i / npts);
-        const long long ip = i % npts;
-        int z = (int)(ip % zspan);
-        long long xy = ip / zspan;
-        const int zz = z + c * ZT_NPH;
-        double2 v = (live && zz < td2) ? T[xy * td2 + zz] : make_double2(0.0, 0.0);
-        __nv_bfloat16 sr[NPL], si[NPL];
-        slice4(v.x, e, sr);
-        slice4(v.y, e, si);
-        const int zb = z >> 3, z8 = z & 7;
-        const long long cell = (((long long)c * nslot + slot) * td0 * td1 + xy) * nzb + zb;   // (c, k, X, Y, zb)
+    const long long blk = 2LL * NB * 8;                       // one plane of a block: 2 parts x NB bands x 8 z
+#pragma unroll
+    for (int c = 0; c < ZT_NCOPY; ++c) {
+        const long long cell = ((long long)c * nslot + slot) * ncell + cellk;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
-            __nv_bfloat16 part[ZT_NPART] = {sr[p], si[p], __hneg(si[p]), sr[p]};
+            uint4 re, im, nim;
+            uint32_t *pr = &re.x, *pi = &im.x, *pn = &nim.x;
 #pragma unroll
-            for (int q = 0; q < ZT_NPART; ++q) {
-                long long o = ((cell * 2 + (q >> 1)) * nblk + b) * (NPL * blk) + ((long long)(p * 2 + (q & 1)) * NB + j) * 8 + z8;
-                Tq[o] = part[q];
+            for (int t = 0; t < 8; t += 2) {
+                const int z0 = c * ZT_NPH + t;
+                pr[t / 2] = pack_bf16x2(sr[z0][p], sr[z0 + 1][p]);
+                pi[t / 2] = pack_bf16x2(si[z0][p], si[z0 + 1][p]);
+                pn[t / 2] = pack_bf16x2(__hneg(si[z0][p]), __hneg(si[z0 + 1][p]));
             }
+            // parts: h = 0 holds (Re T, Im T), h = 1 holds (-Im T, Re T)
+            __nv_bfloat16 *b0 = Tq + ((cell * 2 + 0) * nblk + b) * (NPL * blk) + ((long long)(p * 2) * NB + j) * 8;
+            __nv_bfloat16 *b1 = Tq + ((cell * 2 + 1) * nblk + b) * (NPL * blk) + ((long long)(p * 2) * NB + j) * 8;
+            *reinterpret_cast<uint4 *>(b0) = re;
+            *reinterpret_cast<uint4 *>(b0 + NB * 8) = im;
+            *reinterpret_cast<uint4 *>(b1) = nim;
+            *reinterpret_cast<uint4 *>(b1 + NB * 8) = re;
         }
     }
 }
@@ -591,8 +620,14 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                                        reinterpret_cast<int *>(b + o_rowm), reinterpret_cast<int *>(b + o_line), gmin[0], gmin[1],
                                        By, nL, reinterpret_cast<int *>(b + o_sst), reinterpret_cast<int *>(b + o_sz0), Kh, Rpad, A,
                                        aexp);
-    t_slices_kernel<<<dim3(nbpad, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], nzb, NBt, nblk,
-                                                     in.nb_max, nslot, reinterpret_cast<int *>(b + o_kslot), Tp, eT);
+    t_exp_kernel<<<dim3(in.nb_max, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], in.nb_max,
+                                                      reinterpret_cast<int *>(b + o_kslot), eT);
+    {
+        const long long nthreads = (long long)in.tdim[0] * in.tdim[1] * nzb * nbpad;
+        t_slices_kernel<<<dim3((unsigned)((nthreads + 255) / 256), nk), 256, 0, st>>>(
+            in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], nzb, NBt, nblk, in.nb_max, nslot,
+            reinterpret_cast<int *>(b + o_kslot), eT, Tp);
+    }
     if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw slices"))) return rc;
     // ---- tensor maps
     CUtensorMap mA;
