@@ -274,6 +274,7 @@ int hfx_set_kpoint(hfx_ctx *ctx, int ik, int n_bands, int n_occ, int npw, const 
         (rc = h2d(ctx, k.d_A, reinterpret_cast<const double2 *>(A), nA / 2)))
         return rc;
     bool gchanged = !k.set || k.G.size() != (size_t)3 * npw || std::memcmp(k.G.data(), G, sizeof(int) * 3 * npw) != 0;
+    if (gchanged || k.nb != n_bands || k.no != n_occ || k.npw != npw) ++ctx->struct_epoch;
     if (gchanged) k.G.assign(G, G + 3 * npw);
     k.nb = n_bands;
     k.no = n_occ;
@@ -311,6 +312,9 @@ int hfx_set_coulomb(hfx_ctx *ctx, int iq, int n_ipw, const int *G_aux, const dou
     if ((rc = h2d(ctx, q.d_G, G_aux, (size_t)3 * n_ipw)) || (rc = h2d(ctx, q.d_v, reinterpret_cast<const double2 *>(v), nv / 2)) ||
         (rc = sync(ctx)))
         return rc;
+    if (!q.set || q.nipw != n_ipw || q.G.size() != (size_t)3 * n_ipw ||
+        (n_ipw > 0 && std::memcmp(q.G.data(), G_aux, sizeof(int) * 3 * n_ipw) != 0))
+        ++ctx->struct_epoch;
     q.G.assign(G_aux, G_aux + 3 * n_ipw);
     q.nipw = n_ipw;
     q.set = true;

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <memory>
 #include <string>
 #include <utility>
 #include <vector>
@@ -141,6 +142,11 @@ struct hfx_ctx {
     // scratch
     hfx::Scratch s_theta, s_thpsi, s_B, s_zc, s_zs, s_ys, s_y64, s_praw, s_vacc, s_pairs, s_qd,
         s_misc, s_ap, s_aexp, s_xexp, s_zipw, s_cgT, s_cgZ;
+
+    // bumped whenever a plane-wave list, an aux list or a band window changes;
+    // host tables built from the structure are reused while it stays the same
+    uint64_t struct_epoch = 0;
+    std::shared_ptr<void> zipw_plan;
 };
 
 namespace hfx {

@@ -19,6 +19,7 @@
 // shifted by 0, 2, 4, 6 in z, and the segments of every line start on the
 // z parity of W (two phase variants of the C slices).
 #include <algorithm>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -429,243 +430,303 @@ int pick_nb(int nb_max) {
 
 }  // namespace
 
+// Host tables of one batch of the interstitial GEMM (see zipw_tc_prepare_and_launch).
+struct ZipwPlan {
+    bool valid = false;
+    uint64_t sig = 0;
+    void *base = nullptr;                 // scratch the tables were uploaded to
+    ZParams p;
+    size_t o_rowk = 0, o_rowm = 0, o_line = 0, o_sst = 0, o_sz0 = 0, o_tp = 0, o_a = 0, o_aexp = 0, o_eT = 0, o_kslot = 0;
+    size_t a_elems = 0;
+    int R = 0, Rpad = 0, nzb = 0, NBt = 0, nblk = 0, nbpad = 0, nslot = 0, Kh = 0, nL = 0, gx0 = 0, gy0 = 0, By = 0;
+};
+
+// FNV-1a over everything the tables depend on
+uint64_t zipw_signature(hfx_ctx *ctx, const ZipwTcInput &in) {
+    uint64_t h = 1469598103934665603ULL;
+    auto mix = [&](const void *d, size_t n) {
+        const unsigned char *c = static_cast<const unsigned char *>(d);
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ULL;
+    };
+    auto mixv = [&](const auto &v) { mix(v.data(), v.size() * sizeof(v[0])); };
+    mix(&ctx->struct_epoch, sizeof(ctx->struct_epoch));
+    mix(&ctx->nk, sizeof(int));
+    mix(&ctx->nmt, sizeof(int));
+    mix(&ctx->omega, sizeof(double));
+    mixv(in.kset);
+    mixv(in.qs);
+    mixv(in.pairs);
+    mix(&in.nb_max, sizeof(int));
+    mix(in.tlo, sizeof(in.tlo));
+    mix(in.tdim, sizeof(in.tdim));
+    return h;
+}
+
 // Host side: segment grid, slices, shift lists, tiles and launch for one batch.
 int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     cudaStream_t st = ctx->stream;
     int rc;
     const int nk = ctx->nk;
-    // ---- G1 lines (x, y) with their z ranges over every k' plane-wave list
-    int gmin[3] = {1 << 29, 1 << 29, 1 << 29}, gmax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
-    for (auto &k : ctx->kp)
-        for (size_t i = 0; i < k.G.size(); ++i) {
-            int x = i % 3;
-            gmin[x] = std::min(gmin[x], k.G[i]);
-            gmax[x] = std::max(gmax[x], k.G[i]);
-        }
-    if (gmin[0] > gmax[0]) return HFX_OK;
-    const int Bx = gmax[0] - gmin[0] + 1, By = gmax[1] - gmin[1] + 1;
-    std::vector<int> zlo((size_t)Bx * By, 1 << 29), zhi((size_t)Bx * By, -(1 << 29));
-    for (auto &k : ctx->kp)
-        for (size_t i = 0; i + 2 < k.G.size(); i += 3) {
-            size_t b = (size_t)(k.G[i] - gmin[0]) * By + (k.G[i + 1] - gmin[1]);
-            zlo[b] = std::min(zlo[b], k.G[i + 2]);
-            zhi[b] = std::max(zhi[b], k.G[i + 2]);
-        }
-    std::vector<int> line_of((size_t)Bx * By, -1), lx, ly, lzlo, lzhi;
-    for (int x = 0; x < Bx; ++x)
-        for (int y = 0; y < By; ++y) {
-            size_t b = (size_t)x * By + y;
-            if (zlo[b] > zhi[b]) continue;
-            line_of[b] = (int)lx.size();
-            lx.push_back(gmin[0] + x);
-            ly.push_back(gmin[1] + y);
-            lzlo.push_back(zlo[b]);
-            lzhi.push_back(zhi[b]);
-        }
-    const int nL = (int)lx.size();
-    // segment grid per z phase: segments of a line start at z0 = ph (mod ZT_NPH)
-    std::vector<int> segstart((size_t)ZT_NPH * nL), segz0((size_t)ZT_NPH * nL), nseg(ZT_NPH);
-    std::vector<std::vector<int4>> segs(ZT_NPH);
-    for (int ph = 0; ph < ZT_NPH; ++ph) {
-        for (int l = 0; l < nL; ++l) {
-            int z0 = lzlo[l] - (((lzlo[l] - ph) % ZT_NPH) + ZT_NPH) % ZT_NPH;
-            segstart[(size_t)ph * nL + l] = (int)segs[ph].size();
-            segz0[(size_t)ph * nL + l] = z0;
-            for (int z = z0; z <= lzhi[l]; z += 8) segs[ph].push_back(make_int4(lx[l], ly[l], z, 0));
-        }
-        nseg[ph] = (int)segs[ph].size();
+    // every table below depends only on the structure of the inputs (plane-wave
+    // and aux lists, band windows, the batch's pairs): build and upload them
+    // once and reuse them while that structure and the scratch buffer stay
+    std::shared_ptr<ZipwPlan> plan = std::static_pointer_cast<ZipwPlan>(ctx->zipw_plan);
+    if (!plan) {
+        plan = std::make_shared<ZipwPlan>();
+        ctx->zipw_plan = plan;
     }
-    int nsegp_max = 0;
-    for (int ph = 0; ph < ZT_NPH; ++ph) nsegp_max = std::max(nsegp_max, (nseg[ph] + 7) / 8 * 8);
-    const int Kh = nsegp_max * 8;
-    const int nzb = (in.tdim[2] + 7) / 8;
-    // every segment: (x td1 + y) of its line and z0 - ph, offsets from the tile
-    // shift (W_x - tlo_x) td1 + (W_y - tlo_y) and W_z + ph - tlo_z
-    std::vector<int2> segtab((size_t)ZT_NPH * nsegp_max);
-    int nchunk[ZT_NPH];
-    for (int ph = 0; ph < ZT_NPH; ++ph) {
-        nchunk[ph] = (nseg[ph] + 7) / 8;
-        for (int s2 = 0; s2 < nsegp_max; ++s2) {
-            const int4 sg = s2 < nseg[ph] ? segs[ph][s2] : segs[ph][0];   // padding: any valid block
-            segtab[(size_t)ph * nsegp_max + s2] = make_int2(sg.x * in.tdim[1] + sg.y, sg.z - ph);
-        }
-    }
-    // ---- rows (k', m) of every k'
-    std::vector<int> rowk, rowm, rowbase(nk, -1);
-    for (int kp = 0; kp < nk; ++kp) {
-        rowbase[kp] = (int)rowk.size();
-        for (int m = 0; m < ctx->kp[kp].no; ++m) { rowk.push_back(kp); rowm.push_back(m); }
-    }
-    const int R = (int)rowk.size();
-    if (R == 0) return HFX_OK;
-    const int Rpad = (R + ZT_BM - 1) / ZT_BM * ZT_BM;
-    const int NBt = pick_nb(in.nb_max);
-    const int nblk = (in.nb_max + NBt - 1) / NBt;
-    // ---- aux lookup tables over the batch's q
-    int amin[3] = {1 << 29, 1 << 29, 1 << 29}, amax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
-    for (int iq : in.qs)
-        for (size_t i = 0; i < ctx->qp[iq].G.size(); ++i) {
-            int x = i % 3;
-            amin[x] = std::min(amin[x], ctx->qp[iq].G[i]);
-            amax[x] = std::max(amax[x], ctx->qp[iq].G[i]);
-        }
-    int ad[3];
-    for (int x = 0; x < 3; ++x) {
-        if (amin[x] > amax[x]) amin[x] = amax[x] = 0;
-        ad[x] = amax[x] - amin[x] + 1;
-    }
-    const int nq = (int)in.qs.size();
-    std::vector<int> gtab((size_t)nq * ad[0] * ad[1] * ad[2], -1);
-    for (int s = 0; s < nq; ++s) {
-        const std::vector<int> &G = ctx->qp[in.qs[s]].G;
-        for (size_t g = 0; g < G.size() / 3; ++g)
-            gtab[(((size_t)s * ad[0] + (G[3 * g] - amin[0])) * ad[1] + (G[3 * g + 1] - amin[1])) * ad[2] + (G[3 * g + 2] - amin[2])] = (int)g;
-    }
-    // ---- pair info (k, k') and the shift lists / tiles per k
-    std::vector<ZPairInfo> pinfo((size_t)nk * nk, ZPairInfo{-1, 0, 0, 0});
-    for (int i = 0; i < (int)in.pairs.size(); ++i) {
-        const PairDesc &pr = in.pairs[i];
-        pinfo[(size_t)pr.ik * nk + pr.ikp] = ZPairInfo{i, pr.g0[0], pr.g0[1], pr.g0[2]};
-    }
-    // W = G - G0 lies in [amin, amax + 1]
-    const int wd[3] = {ad[0] + 1, ad[1] + 1, ad[2] + 1};
-    const size_t wvol = (size_t)wd[0] * wd[1] * wd[2];
-    const int nmtile = Rpad / ZT_BM;
-    std::vector<int4> wxyz;
-    std::vector<ZTile> tiles;
-    std::vector<unsigned char> need;
-    std::vector<int> kslot(nk, -1);
-    int nslot = 0;
-    for (int ik : in.kset) {
-        kslot[ik] = nslot++;
-        need.assign(wvol * nmtile, 0);
-        for (const PairDesc &pr : in.pairs) {
-            if (pr.ik != ik || pr.no == 0) continue;
-            const std::vector<int> &G = ctx->qp[pr.iq].G;
-            const int t0 = rowbase[pr.ikp] / ZT_BM, t1 = (rowbase[pr.ikp] + pr.no - 1) / ZT_BM;
-            for (size_t g = 0; g < G.size() / 3; ++g) {
-                int w0 = G[3 * g] - pr.g0[0] - amin[0], w1 = G[3 * g + 1] - pr.g0[1] - amin[1], w2 = G[3 * g + 2] - pr.g0[2] - amin[2];
-                size_t wi = ((size_t)w0 * wd[1] + w1) * wd[2] + w2;
-                for (int t = t0; t <= t1; ++t) need[wi * nmtile + t] = 1;
+    const uint64_t sig = zipw_signature(ctx, in);
+    if (!(plan->valid && plan->sig == sig && plan->base == ctx->s_zipw.p)) {
+        plan->valid = false;
+        // ---- G1 lines (x, y) with their z ranges over every k' plane-wave list
+        int gmin[3] = {1 << 29, 1 << 29, 1 << 29}, gmax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
+        for (auto &k : ctx->kp)
+            for (size_t i = 0; i < k.G.size(); ++i) {
+                int x = i % 3;
+                gmin[x] = std::min(gmin[x], k.G[i]);
+                gmax[x] = std::max(gmax[x], k.G[i]);
             }
-        }
-        for (size_t wi = 0; wi < wvol; ++wi) {
-            bool any = false;
-            for (int t = 0; t < nmtile; ++t) any |= need[wi * nmtile + t] != 0;
-            if (!any) continue;
-            const int widx = (int)wxyz.size();
-            const int w2 = (int)(wi % wd[2]), w1 = (int)((wi / wd[2]) % wd[1]), w0 = (int)(wi / ((size_t)wd[1] * wd[2]));
-            const int Wz = w2 + amin[2];
-            // z phase: the T z index of every segment start is a multiple of ZT_NPH
-            wxyz.push_back(make_int4(w0 + amin[0], w1 + amin[1], Wz, (((in.tlo[2] - Wz) % ZT_NPH) + ZT_NPH) % ZT_NPH));
-            for (int t = 0; t < nmtile; ++t)
-                if (need[wi * nmtile + t])
-                    for (int b = 0; b < nblk; ++b) tiles.push_back(ZTile{ik, widx, t * ZT_BM, b});
-        }
-    }
-    if (tiles.empty()) return HFX_OK;
-    // tiles of one z phase together: the C slices of a phase (8.4 MB for 512
-    // rows) and T of one k stay in L2 while the CTAs sweep that k's shifts
-    std::stable_sort(tiles.begin(), tiles.end(),
-                     [&](const ZTile &a, const ZTile &b) { return wxyz[a.w].w < wxyz[b.w].w; });
-    {
-        // every B segment of every tile must be one whole z block inside the sliced T box
-        int sx0 = 1 << 29, sx1 = -(1 << 29), sy0 = 1 << 29, sy1 = -(1 << 29), z00[ZT_NPH], z01[ZT_NPH];
+        if (gmin[0] > gmax[0]) return HFX_OK;
+        const int Bx = gmax[0] - gmin[0] + 1, By = gmax[1] - gmin[1] + 1;
+        std::vector<int> zlo((size_t)Bx * By, 1 << 29), zhi((size_t)Bx * By, -(1 << 29));
+        for (auto &k : ctx->kp)
+            for (size_t i = 0; i + 2 < k.G.size(); i += 3) {
+                size_t b = (size_t)(k.G[i] - gmin[0]) * By + (k.G[i + 1] - gmin[1]);
+                zlo[b] = std::min(zlo[b], k.G[i + 2]);
+                zhi[b] = std::max(zhi[b], k.G[i + 2]);
+            }
+        std::vector<int> line_of((size_t)Bx * By, -1), lx, ly, lzlo, lzhi;
+        for (int x = 0; x < Bx; ++x)
+            for (int y = 0; y < By; ++y) {
+                size_t b = (size_t)x * By + y;
+                if (zlo[b] > zhi[b]) continue;
+                line_of[b] = (int)lx.size();
+                lx.push_back(gmin[0] + x);
+                ly.push_back(gmin[1] + y);
+                lzlo.push_back(zlo[b]);
+                lzhi.push_back(zhi[b]);
+            }
+        const int nL = (int)lx.size();
+        // segment grid per z phase: segments of a line start at z0 = ph (mod ZT_NPH)
+        std::vector<int> segstart((size_t)ZT_NPH * nL), segz0((size_t)ZT_NPH * nL), nseg(ZT_NPH);
+        std::vector<std::vector<int4>> segs(ZT_NPH);
         for (int ph = 0; ph < ZT_NPH; ++ph) {
-            z00[ph] = 1 << 29;
-            z01[ph] = -(1 << 29);
-            for (const int4 &sg : segs[ph]) {
-                sx0 = std::min(sx0, sg.x); sx1 = std::max(sx1, sg.x);
-                sy0 = std::min(sy0, sg.y); sy1 = std::max(sy1, sg.y);
-                z00[ph] = std::min(z00[ph], sg.z); z01[ph] = std::max(z01[ph], sg.z);
+            for (int l = 0; l < nL; ++l) {
+                int z0 = lzlo[l] - (((lzlo[l] - ph) % ZT_NPH) + ZT_NPH) % ZT_NPH;
+                segstart[(size_t)ph * nL + l] = (int)segs[ph].size();
+                segz0[(size_t)ph * nL + l] = z0;
+                for (int z = z0; z <= lzhi[l]; z += 8) segs[ph].push_back(make_int4(lx[l], ly[l], z, 0));
+            }
+            nseg[ph] = (int)segs[ph].size();
+        }
+        int nsegp_max = 0;
+        for (int ph = 0; ph < ZT_NPH; ++ph) nsegp_max = std::max(nsegp_max, (nseg[ph] + 7) / 8 * 8);
+        const int Kh = nsegp_max * 8;
+        const int nzb = (in.tdim[2] + 7) / 8;
+        // every segment: (x td1 + y) of its line and z0 - ph, offsets from the tile
+        // shift (W_x - tlo_x) td1 + (W_y - tlo_y) and W_z + ph - tlo_z
+        std::vector<int2> segtab((size_t)ZT_NPH * nsegp_max);
+        int nchunk[ZT_NPH];
+        for (int ph = 0; ph < ZT_NPH; ++ph) {
+            nchunk[ph] = (nseg[ph] + 7) / 8;
+            for (int s2 = 0; s2 < nsegp_max; ++s2) {
+                const int4 sg = s2 < nseg[ph] ? segs[ph][s2] : segs[ph][0];   // padding: any valid block
+                segtab[(size_t)ph * nsegp_max + s2] = make_int2(sg.x * in.tdim[1] + sg.y, sg.z - ph);
             }
         }
-        for (const int4 &W : wxyz) {
-            const int Z0 = W.z + z00[W.w] - in.tlo[2], Z1 = W.z + z01[W.w] - in.tlo[2];
-            if (W.x + sx0 - in.tlo[0] < 0 || W.x + sx1 - in.tlo[0] >= in.tdim[0] || W.y + sy0 - in.tlo[1] < 0 ||
-                W.y + sy1 - in.tlo[1] >= in.tdim[1] || Z0 < 0 || (Z0 % ZT_NPH) != 0 || (Z1 >> 3) >= nzb)
-                return set_err(ctx, HFX_EUNSUPPORTED, "interstitial segment outside the step-function box");
+        // ---- rows (k', m) of every k'
+        std::vector<int> rowk, rowm, rowbase(nk, -1);
+        for (int kp = 0; kp < nk; ++kp) {
+            rowbase[kp] = (int)rowk.size();
+            for (int m = 0; m < ctx->kp[kp].no; ++m) { rowk.push_back(kp); rowm.push_back(m); }
         }
+        const int R = (int)rowk.size();
+        if (R == 0) return HFX_OK;
+        const int Rpad = (R + ZT_BM - 1) / ZT_BM * ZT_BM;
+        const int NBt = pick_nb(in.nb_max);
+        const int nblk = (in.nb_max + NBt - 1) / NBt;
+        // ---- aux lookup tables over the batch's q
+        int amin[3] = {1 << 29, 1 << 29, 1 << 29}, amax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
+        for (int iq : in.qs)
+            for (size_t i = 0; i < ctx->qp[iq].G.size(); ++i) {
+                int x = i % 3;
+                amin[x] = std::min(amin[x], ctx->qp[iq].G[i]);
+                amax[x] = std::max(amax[x], ctx->qp[iq].G[i]);
+            }
+        int ad[3];
+        for (int x = 0; x < 3; ++x) {
+            if (amin[x] > amax[x]) amin[x] = amax[x] = 0;
+            ad[x] = amax[x] - amin[x] + 1;
+        }
+        const int nq = (int)in.qs.size();
+        std::vector<int> gtab((size_t)nq * ad[0] * ad[1] * ad[2], -1);
+        for (int s = 0; s < nq; ++s) {
+            const std::vector<int> &G = ctx->qp[in.qs[s]].G;
+            for (size_t g = 0; g < G.size() / 3; ++g)
+                gtab[(((size_t)s * ad[0] + (G[3 * g] - amin[0])) * ad[1] + (G[3 * g + 1] - amin[1])) * ad[2] + (G[3 * g + 2] - amin[2])] = (int)g;
+        }
+        // ---- pair info (k, k') and the shift lists / tiles per k
+        std::vector<ZPairInfo> pinfo((size_t)nk * nk, ZPairInfo{-1, 0, 0, 0});
+        for (int i = 0; i < (int)in.pairs.size(); ++i) {
+            const PairDesc &pr = in.pairs[i];
+            pinfo[(size_t)pr.ik * nk + pr.ikp] = ZPairInfo{i, pr.g0[0], pr.g0[1], pr.g0[2]};
+        }
+        // W = G - G0 lies in [amin, amax + 1]
+        const int wd[3] = {ad[0] + 1, ad[1] + 1, ad[2] + 1};
+        const size_t wvol = (size_t)wd[0] * wd[1] * wd[2];
+        const int nmtile = Rpad / ZT_BM;
+        std::vector<int4> wxyz;
+        std::vector<ZTile> tiles;
+        std::vector<unsigned char> need;
+        std::vector<int> kslot(nk, -1);
+        int nslot = 0;
+        for (int ik : in.kset) {
+            kslot[ik] = nslot++;
+            need.assign(wvol * nmtile, 0);
+            for (const PairDesc &pr : in.pairs) {
+                if (pr.ik != ik || pr.no == 0) continue;
+                const std::vector<int> &G = ctx->qp[pr.iq].G;
+                const int t0 = rowbase[pr.ikp] / ZT_BM, t1 = (rowbase[pr.ikp] + pr.no - 1) / ZT_BM;
+                for (size_t g = 0; g < G.size() / 3; ++g) {
+                    int w0 = G[3 * g] - pr.g0[0] - amin[0], w1 = G[3 * g + 1] - pr.g0[1] - amin[1], w2 = G[3 * g + 2] - pr.g0[2] - amin[2];
+                    size_t wi = ((size_t)w0 * wd[1] + w1) * wd[2] + w2;
+                    for (int t = t0; t <= t1; ++t) need[wi * nmtile + t] = 1;
+                }
+            }
+            for (size_t wi = 0; wi < wvol; ++wi) {
+                bool any = false;
+                for (int t = 0; t < nmtile; ++t) any |= need[wi * nmtile + t] != 0;
+                if (!any) continue;
+                const int widx = (int)wxyz.size();
+                const int w2 = (int)(wi % wd[2]), w1 = (int)((wi / wd[2]) % wd[1]), w0 = (int)(wi / ((size_t)wd[1] * wd[2]));
+                const int Wz = w2 + amin[2];
+                // z phase: the T z index of every segment start is a multiple of ZT_NPH
+                wxyz.push_back(make_int4(w0 + amin[0], w1 + amin[1], Wz, (((in.tlo[2] - Wz) % ZT_NPH) + ZT_NPH) % ZT_NPH));
+                for (int t = 0; t < nmtile; ++t)
+                    if (need[wi * nmtile + t])
+                        for (int b = 0; b < nblk; ++b) tiles.push_back(ZTile{ik, widx, t * ZT_BM, b});
+            }
+        }
+        if (tiles.empty()) return HFX_OK;
+        // tiles of one z phase together: the C slices of a phase (8.4 MB for 512
+        // rows) and T of one k stay in L2 while the CTAs sweep that k's shifts
+        std::stable_sort(tiles.begin(), tiles.end(),
+                         [&](const ZTile &a, const ZTile &b) { return wxyz[a.w].w < wxyz[b.w].w; });
+        {
+            // every B segment of every tile must be one whole z block inside the sliced T box
+            int sx0 = 1 << 29, sx1 = -(1 << 29), sy0 = 1 << 29, sy1 = -(1 << 29), z00[ZT_NPH], z01[ZT_NPH];
+            for (int ph = 0; ph < ZT_NPH; ++ph) {
+                z00[ph] = 1 << 29;
+                z01[ph] = -(1 << 29);
+                for (const int4 &sg : segs[ph]) {
+                    sx0 = std::min(sx0, sg.x); sx1 = std::max(sx1, sg.x);
+                    sy0 = std::min(sy0, sg.y); sy1 = std::max(sy1, sg.y);
+                    z00[ph] = std::min(z00[ph], sg.z); z01[ph] = std::max(z01[ph], sg.z);
+                }
+            }
+            for (const int4 &W : wxyz) {
+                const int Z0 = W.z + z00[W.w] - in.tlo[2], Z1 = W.z + z01[W.w] - in.tlo[2];
+                if (W.x + sx0 - in.tlo[0] < 0 || W.x + sx1 - in.tlo[0] >= in.tdim[0] || W.y + sy0 - in.tlo[1] < 0 ||
+                    W.y + sy1 - in.tlo[1] >= in.tdim[1] || Z0 < 0 || (Z0 % ZT_NPH) != 0 || (Z1 >> 3) >= nzb)
+                    return set_err(ctx, HFX_EUNSUPPORTED, "interstitial segment outside the step-function box");
+            }
+        }
+        // ---- device buffers (scratch s_zipw)
+        const int nbpad = nblk * NBt;
+        const size_t tp_elems = (size_t)ZT_NCOPY * nslot * NPL * ZT_NPART * nbpad * in.tdim[0] * in.tdim[1] * nzb * 8;
+        const size_t a_elems = (size_t)ZT_NPH * NPL * Rpad * 2 * Kh;
+        size_t off = 0;
+        auto place = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
+        const size_t o_tp = place(tp_elems * 2), o_a = place(a_elems * 2), o_aexp = place((size_t)Rpad * 4),
+                     o_eT = place((size_t)nk * in.nb_max * 4), o_rowk = place((size_t)R * 4), o_rowm = place((size_t)R * 4),
+                     o_line = place(line_of.size() * 4), o_sst = place(segstart.size() * 4), o_sz0 = place(segz0.size() * 4),
+                     o_seg = place(segtab.size() * sizeof(int2)), o_gtab = place(gtab.size() * 4),
+                     o_pinfo = place(pinfo.size() * sizeof(ZPairInfo)), o_w = place(wxyz.size() * sizeof(int4)),
+                     o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4);
+        if ((rc = scratch_reserve(ctx, ctx->s_zipw, off))) return rc;
+        char *b = reinterpret_cast<char *>(ctx->s_zipw.p);
+        auto up = [&](size_t o, const void *src, size_t bytes) {
+            return cuda_check(ctx, cudaMemcpyAsync(b + o, src, bytes, cudaMemcpyHostToDevice, st), "zipw tables");
+        };
+        if ((rc = up(o_rowk, rowk.data(), R * 4)) || (rc = up(o_rowm, rowm.data(), R * 4)) ||
+            (rc = up(o_line, line_of.data(), line_of.size() * 4)) || (rc = up(o_sst, segstart.data(), segstart.size() * 4)) ||
+            (rc = up(o_sz0, segz0.data(), segz0.size() * 4)) || (rc = up(o_seg, segtab.data(), segtab.size() * sizeof(int2))) ||
+            (rc = up(o_gtab, gtab.data(), gtab.size() * 4)) ||
+            (rc = up(o_pinfo, pinfo.data(), pinfo.size() * sizeof(ZPairInfo))) ||
+            (rc = up(o_w, wxyz.data(), wxyz.size() * sizeof(int4))) ||
+            (rc = up(o_tiles, tiles.data(), tiles.size() * sizeof(ZTile))) || (rc = up(o_kslot, kslot.data(), nk * 4)))
+            return rc;
+        ZParams &p = plan->p;
+        p.tiles = reinterpret_cast<ZTile *>(b + o_tiles);
+        p.ntiles = (int)tiles.size();
+        p.wxyz = reinterpret_cast<int4 *>(b + o_w);
+        p.pinfo = reinterpret_cast<ZPairInfo *>(b + o_pinfo);
+        p.pairs = in.d_pairs;
+        p.gtab = reinterpret_cast<int *>(b + o_gtab);
+        p.ax0 = amin[0]; p.ay0 = amin[1]; p.az0 = amin[2];
+        p.ad0 = ad[0]; p.ad1 = ad[1]; p.ad2 = ad[2];
+        p.rowk = reinterpret_cast<int *>(b + o_rowk);
+        p.rowm = reinterpret_cast<int *>(b + o_rowm);
+        p.aexp = reinterpret_cast<int *>(b + o_aexp);
+        p.eT = reinterpret_cast<int *>(b + o_eT);
+        p.kslot = reinterpret_cast<int *>(b + o_kslot);
+        p.segoff = reinterpret_cast<int2 *>(b + o_seg);
+        p.nsegp_max = nsegp_max;
+        p.Tq = reinterpret_cast<__nv_bfloat16 *>(b + o_tp);
+        p.td0 = in.tdim[0];
+        p.td1 = in.tdim[1];
+        p.nzb = nzb;
+        p.nblk = nblk;
+        p.nslot = nslot;
+        for (int ph = 0; ph < ZT_NPH; ++ph) p.nchunk[ph] = nchunk[ph];
+        p.Z = in.d_Z;
+        p.RSc = in.RSc;
+        p.nmt = ctx->nmt;
+        p.nk = nk;
+        p.R = R;
+        p.Rpad = Rpad;
+        p.Kh = Kh;
+        p.nbmax = in.nb_max;
+        p.tlo0 = in.tlo[0]; p.tlo1 = in.tlo[1]; p.tlo2 = in.tlo[2];
+        p.rs = 1.0 / sqrt(ctx->omega);
+        p.err = ctx->d_err;
+            plan->o_rowk = o_rowk; plan->o_rowm = o_rowm; plan->o_line = o_line; plan->o_sst = o_sst; plan->o_sz0 = o_sz0;
+            plan->o_tp = o_tp; plan->o_a = o_a; plan->o_aexp = o_aexp; plan->o_eT = o_eT; plan->o_kslot = o_kslot;
+            plan->a_elems = a_elems;
+            plan->R = R; plan->Rpad = Rpad; plan->nzb = nzb; plan->NBt = NBt; plan->nblk = nblk; plan->nbpad = nbpad;
+            plan->nslot = nslot; plan->Kh = Kh; plan->nL = nL; plan->gx0 = gmin[0]; plan->gy0 = gmin[1]; plan->By = By;
+            plan->sig = sig;
+            plan->base = ctx->s_zipw.p;
+            plan->valid = true;
     }
-    // ---- device buffers (scratch s_zipw)
-    const int nbpad = nblk * NBt;
-    const size_t tp_elems = (size_t)ZT_NCOPY * nslot * NPL * ZT_NPART * nbpad * in.tdim[0] * in.tdim[1] * nzb * 8;
-    const size_t a_elems = (size_t)ZT_NPH * NPL * Rpad * 2 * Kh;
-    size_t off = 0;
-    auto place = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
-    const size_t o_tp = place(tp_elems * 2), o_a = place(a_elems * 2), o_aexp = place((size_t)Rpad * 4),
-                 o_eT = place((size_t)nk * in.nb_max * 4), o_rowk = place((size_t)R * 4), o_rowm = place((size_t)R * 4),
-                 o_line = place(line_of.size() * 4), o_sst = place(segstart.size() * 4), o_sz0 = place(segz0.size() * 4),
-                 o_seg = place(segtab.size() * sizeof(int2)), o_gtab = place(gtab.size() * 4),
-                 o_pinfo = place(pinfo.size() * sizeof(ZPairInfo)), o_w = place(wxyz.size() * sizeof(int4)),
-                 o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4);
-    if ((rc = scratch_reserve(ctx, ctx->s_zipw, off))) return rc;
+    const ZipwPlan &P = *plan;
     char *b = reinterpret_cast<char *>(ctx->s_zipw.p);
-    auto up = [&](size_t o, const void *src, size_t bytes) {
-        return cuda_check(ctx, cudaMemcpyAsync(b + o, src, bytes, cudaMemcpyHostToDevice, st), "zipw tables");
-    };
-    if ((rc = up(o_rowk, rowk.data(), R * 4)) || (rc = up(o_rowm, rowm.data(), R * 4)) ||
-        (rc = up(o_line, line_of.data(), line_of.size() * 4)) || (rc = up(o_sst, segstart.data(), segstart.size() * 4)) ||
-        (rc = up(o_sz0, segz0.data(), segz0.size() * 4)) || (rc = up(o_seg, segtab.data(), segtab.size() * sizeof(int2))) ||
-        (rc = up(o_gtab, gtab.data(), gtab.size() * 4)) ||
-        (rc = up(o_pinfo, pinfo.data(), pinfo.size() * sizeof(ZPairInfo))) ||
-        (rc = up(o_w, wxyz.data(), wxyz.size() * sizeof(int4))) ||
-        (rc = up(o_tiles, tiles.data(), tiles.size() * sizeof(ZTile))) || (rc = up(o_kslot, kslot.data(), nk * 4)))
-        return rc;
-    __nv_bfloat16 *Tp = reinterpret_cast<__nv_bfloat16 *>(b + o_tp), *A = reinterpret_cast<__nv_bfloat16 *>(b + o_a);
-    int *aexp = reinterpret_cast<int *>(b + o_aexp), *eT = reinterpret_cast<int *>(b + o_eT);
-    cudaMemsetAsync(aexp, 0, (size_t)Rpad * 4, st);
-    cudaMemsetAsync(A, 0, a_elems * 2, st);
-    c_slices_kernel<<<R, 256, 0, st>>>(in.d_ck, in.d_Gk, in.d_npw, reinterpret_cast<int *>(b + o_rowk),
-                                       reinterpret_cast<int *>(b + o_rowm), reinterpret_cast<int *>(b + o_line), gmin[0], gmin[1],
-                                       By, nL, reinterpret_cast<int *>(b + o_sst), reinterpret_cast<int *>(b + o_sz0), Kh, Rpad, A,
-                                       aexp);
+    __nv_bfloat16 *Tp = reinterpret_cast<__nv_bfloat16 *>(b + P.o_tp), *A = reinterpret_cast<__nv_bfloat16 *>(b + P.o_a);
+    int *aexp = reinterpret_cast<int *>(b + P.o_aexp), *eT = reinterpret_cast<int *>(b + P.o_eT);
+    cudaMemsetAsync(aexp, 0, (size_t)P.Rpad * 4, st);
+    cudaMemsetAsync(A, 0, P.a_elems * 2, st);
+    c_slices_kernel<<<P.R, 256, 0, st>>>(in.d_ck, in.d_Gk, in.d_npw, reinterpret_cast<int *>(b + P.o_rowk),
+                                         reinterpret_cast<int *>(b + P.o_rowm), reinterpret_cast<int *>(b + P.o_line), P.gx0,
+                                         P.gy0, P.By, P.nL, reinterpret_cast<int *>(b + P.o_sst), reinterpret_cast<int *>(b + P.o_sz0),
+                                         P.Kh, P.Rpad, A, aexp);
     t_exp_kernel<<<dim3(in.nb_max, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], in.nb_max,
-                                                      reinterpret_cast<int *>(b + o_kslot), eT);
+                                                      reinterpret_cast<int *>(b + P.o_kslot), eT);
     {
-        const long long nthreads = (long long)in.tdim[0] * in.tdim[1] * nzb * nbpad;
+        const long long nthreads = (long long)in.tdim[0] * in.tdim[1] * P.nzb * P.nbpad;
         t_slices_kernel<<<dim3((unsigned)((nthreads + 255) / 256), nk), 256, 0, st>>>(
-            in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], nzb, NBt, nblk, in.nb_max, nslot,
-            reinterpret_cast<int *>(b + o_kslot), eT, Tp);
+            in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], P.nzb, P.NBt, P.nblk, in.nb_max, P.nslot,
+            reinterpret_cast<int *>(b + P.o_kslot), eT, Tp);
     }
     if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw slices"))) return rc;
-    // ---- tensor maps
+    // ---- tensor maps and launch
     CUtensorMap mA;
-    if ((rc = make_map_2d(ctx, &mA, A, (long long)ZT_NPH * NPL * Rpad, 2LL * Kh, ZT_BM))) return rc;
-    ZParams p;
-    p.tiles = reinterpret_cast<ZTile *>(b + o_tiles);
-    p.ntiles = (int)tiles.size();
-    p.wxyz = reinterpret_cast<int4 *>(b + o_w);
-    p.pinfo = reinterpret_cast<ZPairInfo *>(b + o_pinfo);
+    if ((rc = make_map_2d(ctx, &mA, A, (long long)ZT_NPH * NPL * P.Rpad, 2LL * P.Kh, ZT_BM))) return rc;
+    ZParams p = P.p;   // per-call pointers: the batch's pairs and projections, the error word
     p.pairs = in.d_pairs;
-    p.gtab = reinterpret_cast<int *>(b + o_gtab);
-    p.ax0 = amin[0]; p.ay0 = amin[1]; p.az0 = amin[2];
-    p.ad0 = ad[0]; p.ad1 = ad[1]; p.ad2 = ad[2];
-    p.rowk = reinterpret_cast<int *>(b + o_rowk);
-    p.rowm = reinterpret_cast<int *>(b + o_rowm);
-    p.aexp = aexp;
-    p.eT = eT;
-    p.kslot = reinterpret_cast<int *>(b + o_kslot);
-    p.segoff = reinterpret_cast<int2 *>(b + o_seg);
-    p.nsegp_max = nsegp_max;
-    p.Tq = Tp;
-    p.td0 = in.tdim[0];
-    p.td1 = in.tdim[1];
-    p.nzb = nzb;
-    p.nblk = nblk;
-    p.nslot = nslot;
-    for (int ph = 0; ph < ZT_NPH; ++ph) p.nchunk[ph] = nchunk[ph];
     p.Z = in.d_Z;
     p.RSc = in.RSc;
-    p.nmt = ctx->nmt;
-    p.nk = nk;
-    p.R = R;
-    p.Rpad = Rpad;
-    p.Kh = Kh;
-    p.nbmax = in.nb_max;
-    p.tlo0 = in.tlo[0]; p.tlo1 = in.tlo[1]; p.tlo2 = in.tlo[2];
-    p.rs = 1.0 / sqrt(ctx->omega);
     p.err = ctx->d_err;
+    const int NBt = P.NBt;
     const int grid = std::min<int>(num_sms(), p.ntiles);
     // the whole opt-in shared memory: the pipeline stages plus a guard region
     // past the last stage that no descriptor of the B operand can reach beyond
