@@ -57,10 +57,11 @@ __device__ __forceinline__ double scale2(double d, int k) {
 
 // ------------------------------------------------------------- C slices
 // One block per row r = (k', m): exponent over |Re c|, |Im c| of the row, then
-// [Re C | Im C] = [c_r | -c_i] at K = segment * 8 + (z - z0) in every phase.
+// [Re C | Im C] = [c_r | -c_i] at K = segment * 8 + (z - z0) of the segment grid
+// of the row's tile, in every phase.
 __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int *const *__restrict__ Gk,
                                 const int *__restrict__ npw_k, const int *__restrict__ rowk, const int *__restrict__ rowm,
-                                const int *__restrict__ line_of, int gx0, int gy0, int By, int nL,
+                                const int *__restrict__ line_of, int gx0, int gy0, int By, int nL, int nmtile,
                                 const int *__restrict__ segstart, const int *__restrict__ segz0, int Kh, int Rpad,
                                 __nv_bfloat16 *__restrict__ A, int *__restrict__ aexp) {
     int r = blockIdx.x;
@@ -88,7 +89,8 @@ __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int
         slice4(c[i].x, e, sr);
         slice4(-c[i].y, e, si);
         for (int ph = 0; ph < ZT_NPH; ++ph) {
-            long long K = (long long)segstart[ph * nL + li] * 8 + (z - segz0[ph * nL + li]);
+            const size_t sl = ((size_t)ph * nmtile + r / ZT_BM) * nL + li;   // segment grid of the row's tile
+            long long K = (long long)segstart[sl] * 8 + (z - segz0[sl]);
 #pragma unroll
             for (int p = 0; p < NPL; ++p) {
                 __nv_bfloat16 *row = A + ((long long)(ph * NPL + p) * Rpad + r) * W2;
@@ -197,11 +199,11 @@ struct ZParams {
     const int *rowk, *rowm;       // rows of A (k', m)
     const int *aexp, *eT;         // row exponents, [k][n] band exponents
     const int *kslot;             // k -> slot of its T slices
-    const int2 *segoff;           // [phase][segment] (x td1 + y of its line, z0 - phase)
-    int nsegp_max;
+    const int2 *segoff;           // [phase][row tile][segment] (x td1 + y of its line, z0 - phase)
+    int nsegp_max, nmtile;
+    const int *nchunk;            // [phase][row tile] 64-K chunks per K half
     const __nv_bfloat16 *Tq;      // sliced T blocks (t_slices_kernel layout)
     int td0, td1, nzb, nblk, nslot;
-    int nchunk[ZT_NPH];           // 64-K chunks per K half, per phase
     double2 *Z;
     long long RSc;
     int nmt, nk, R, Rpad, Kh, nbmax, tlo0, tlo1, tlo2;
@@ -252,9 +254,9 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
             const ZTile tl = p.tiles[t];
             const int4 W = p.wxyz[tl.w];
-            const int phz = W.w, nch = p.nchunk[phz];
+            const int phz = W.w, gt = phz * p.nmtile + tl.mrow / ZT_BM, nch = p.nchunk[gt];
             const int slot = p.kslot[tl.k];
-            const int2 *so = p.segoff + (size_t)phz * p.nsegp_max;
+            const int2 *so = p.segoff + (size_t)gt * p.nsegp_max;
             // a segment starts at X = W_x + x - tlo_x, Y likewise, and T z index
             // Zs = (W_z + ph - tlo_z) + (z0 - ph), a multiple of ZT_NPH: copy
             // c = (Zs mod 8) / ZT_NPH, z block Zs / 8 -- inside the box by construction
@@ -299,7 +301,8 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             constexpr uint32_t idesc = idesc_bf16(ZT_BM, N);
             bool ok = true;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-                const int nchunk = 2 * p.nchunk[p.wxyz[p.tiles[t].w].w];
+                const ZTile tm0 = p.tiles[t];
+                const int nchunk = 2 * p.nchunk[p.wxyz[tm0.w].w * p.nmtile + tm0.mrow / ZT_BM];
                 for (int g0 = 0; g0 < nchunk && ok; g0 += ZT_GROUP) {
                     if (!mbar_wait(&tempty_bar, eph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                     tc_fence_after();
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             const ZTile tl = p.tiles[t];
             const int4 W = p.wxyz[tl.w];
-            const int ngroups = (2 * p.nchunk[W.w] + ZT_GROUP - 1) / ZT_GROUP;
+            const int ngroups = (2 * p.nchunk[W.w * p.nmtile + tl.mrow / ZT_BM] + ZT_GROUP - 1) / ZT_GROUP;
             uint64_t hr[NH / 2], lr[NH / 2], hm[NH / 2], lm[NH / 2];   // packed pairs of columns
 #pragma unroll
             for (int j = 0; j < NH / 2; ++j) { hr[j] = 0; lr[j] = 0; hm[j] = 0; lm[j] = 0; }
@@ -438,7 +441,7 @@ struct ZipwPlan {
     ZParams p;
     size_t o_rowk = 0, o_rowm = 0, o_line = 0, o_sst = 0, o_sz0 = 0, o_tp = 0, o_a = 0, o_aexp = 0, o_eT = 0, o_kslot = 0;
     size_t a_elems = 0;
-    int R = 0, Rpad = 0, nzb = 0, NBt = 0, nblk = 0, nbpad = 0, nslot = 0, Kh = 0, nL = 0, gx0 = 0, gy0 = 0, By = 0;
+    int R = 0, Rpad = 0, nzb = 0, NBt = 0, nblk = 0, nbpad = 0, nslot = 0, Kh = 0, nL = 0, gx0 = 0, gy0 = 0, By = 0, nmtile = 0;
 };
 
 // FNV-1a over everything the tables depend on
@@ -507,42 +510,77 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                 lzhi.push_back(zhi[b]);
             }
         const int nL = (int)lx.size();
-        // segment grid per z phase: segments of a line start at z0 = ph (mod ZT_NPH)
-        std::vector<int> segstart((size_t)ZT_NPH * nL), segz0((size_t)ZT_NPH * nL), nseg(ZT_NPH);
-        std::vector<std::vector<int4>> segs(ZT_NPH);
-        for (int ph = 0; ph < ZT_NPH; ++ph) {
-            for (int l = 0; l < nL; ++l) {
-                int z0 = lzlo[l] - (((lzlo[l] - ph) % ZT_NPH) + ZT_NPH) % ZT_NPH;
-                segstart[(size_t)ph * nL + l] = (int)segs[ph].size();
-                segz0[(size_t)ph * nL + l] = z0;
-                for (int z = z0; z <= lzhi[l]; z += 8) segs[ph].push_back(make_int4(lx[l], ly[l], z, 0));
-            }
-            nseg[ph] = (int)segs[ph].size();
-        }
-        int nsegp_max = 0;
-        for (int ph = 0; ph < ZT_NPH; ++ph) nsegp_max = std::max(nsegp_max, (nseg[ph] + 7) / 8 * 8);
-        const int Kh = nsegp_max * 8;
-        const int nzb = (in.tdim[2] + 7) / 8;
-        // every segment: (x td1 + y) of its line and z0 - ph, offsets from the tile
-        // shift (W_x - tlo_x) td1 + (W_y - tlo_y) and W_z + ph - tlo_z
-        std::vector<int2> segtab((size_t)ZT_NPH * nsegp_max);
-        int nchunk[ZT_NPH];
-        for (int ph = 0; ph < ZT_NPH; ++ph) {
-            nchunk[ph] = (nseg[ph] + 7) / 8;
-            for (int s2 = 0; s2 < nsegp_max; ++s2) {
-                const int4 sg = s2 < nseg[ph] ? segs[ph][s2] : segs[ph][0];   // padding: any valid block
-                segtab[(size_t)ph * nsegp_max + s2] = make_int2(sg.x * in.tdim[1] + sg.y, sg.z - ph);
-            }
-        }
-        // ---- rows (k', m) of every k'
+        // ---- rows (k', m): k' in Morton order of their mesh indices, so that a
+        // 128-row tile holds a compact block of the mesh (overlapping spheres)
+        const int *Mh = ctx->sys.mesh;
+        auto morton = [&](int ik) {
+            const int j[3] = {ik / (Mh[1] * Mh[2]), (ik / Mh[2]) % Mh[1], ik % Mh[2]};
+            unsigned long long code = 0;
+            for (int bit = 0; bit < 20; ++bit)
+                for (int x = 0; x < 3; ++x) code |= (unsigned long long)((j[x] >> bit) & 1) << (3 * bit + 2 - x);
+            return code;
+        };
+        std::vector<int> korder(nk);
+        for (int i = 0; i < nk; ++i) korder[i] = i;
+        std::stable_sort(korder.begin(), korder.end(), [&](int a, int b2) { return morton(a) < morton(b2); });
         std::vector<int> rowk, rowm, rowbase(nk, -1);
-        for (int kp = 0; kp < nk; ++kp) {
+        for (int kp : korder) {
             rowbase[kp] = (int)rowk.size();
             for (int m = 0; m < ctx->kp[kp].no; ++m) { rowk.push_back(kp); rowm.push_back(m); }
         }
         const int R = (int)rowk.size();
         if (R == 0) return HFX_OK;
         const int Rpad = (R + ZT_BM - 1) / ZT_BM * ZT_BM;
+        const int nmtile = Rpad / ZT_BM;
+        std::vector<std::vector<int>> tile_k(nmtile);
+        for (int r = 0; r < R; ++r)
+            if (tile_k[r / ZT_BM].empty() || tile_k[r / ZT_BM].back() != rowk[r]) tile_k[r / ZT_BM].push_back(rowk[r]);
+        // segment grid per (z phase, row tile): the lines of the tile's spheres;
+        // segments of a line start at z0 = ph (mod ZT_NPH)
+        const int ngt = ZT_NPH * nmtile;
+        std::vector<int> segstart((size_t)ngt * nL, 0), segz0((size_t)ngt * nL, 0), nseg(ngt);
+        std::vector<std::vector<int4>> segs(ngt);
+        std::vector<int> tzlo(nL), tzhi(nL);
+        for (int t = 0; t < nmtile; ++t) {
+            std::fill(tzlo.begin(), tzlo.end(), 1 << 29);
+            std::fill(tzhi.begin(), tzhi.end(), -(1 << 29));
+            for (int kp : tile_k[t]) {
+                const std::vector<int> &G = ctx->kp[kp].G;
+                for (size_t i = 0; i + 2 < G.size(); i += 3) {
+                    int l = line_of[(size_t)(G[i] - gmin[0]) * By + (G[i + 1] - gmin[1])];
+                    tzlo[l] = std::min(tzlo[l], G[i + 2]);
+                    tzhi[l] = std::max(tzhi[l], G[i + 2]);
+                }
+            }
+            for (int ph = 0; ph < ZT_NPH; ++ph) {
+                const int g = ph * nmtile + t;
+                for (int l = 0; l < nL; ++l) {
+                    if (tzlo[l] > tzhi[l]) continue;
+                    int z0 = tzlo[l] - (((tzlo[l] - ph) % ZT_NPH) + ZT_NPH) % ZT_NPH;
+                    segstart[(size_t)g * nL + l] = (int)segs[g].size();
+                    segz0[(size_t)g * nL + l] = z0;
+                    for (int z = z0; z <= tzhi[l]; z += 8) segs[g].push_back(make_int4(lx[l], ly[l], z, 0));
+                }
+                if (segs[g].empty()) segs[g].push_back(make_int4(lx[0], ly[0], lzlo[0] - (((lzlo[0] - ph) % ZT_NPH) + ZT_NPH) % ZT_NPH, 0));
+                nseg[g] = (int)segs[g].size();
+            }
+        }
+        int nsegp_max = 0;
+        for (int g = 0; g < ngt; ++g) nsegp_max = std::max(nsegp_max, (nseg[g] + 7) / 8 * 8);
+        const int Kh = nsegp_max * 8;
+        const int nzb = (in.tdim[2] + 7) / 8;
+        // every segment: (x td1 + y) of its line and z0 - ph, offsets from the tile
+        // shift (W_x - tlo_x) td1 + (W_y - tlo_y) and W_z + ph - tlo_z
+        std::vector<int2> segtab((size_t)ngt * nsegp_max);
+        std::vector<int> nchunk(ngt);
+        for (int g = 0; g < ngt; ++g) {
+            const int ph = g / nmtile;
+            nchunk[g] = (nseg[g] + 7) / 8;
+            for (int s2 = 0; s2 < nsegp_max; ++s2) {
+                const int4 sg = s2 < nseg[g] ? segs[g][s2] : segs[g][0];   // padding: any valid block
+                segtab[(size_t)g * nsegp_max + s2] = make_int2(sg.x * in.tdim[1] + sg.y, sg.z - ph);
+            }
+        }
         const int NBt = pick_nb(in.nb_max);
         const int nblk = (in.nb_max + NBt - 1) / NBt;
         // ---- aux lookup tables over the batch's q
@@ -574,7 +612,6 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         // W = G - G0 lies in [amin, amax + 1]
         const int wd[3] = {ad[0] + 1, ad[1] + 1, ad[2] + 1};
         const size_t wvol = (size_t)wd[0] * wd[1] * wd[2];
-        const int nmtile = Rpad / ZT_BM;
         std::vector<int4> wxyz;
         std::vector<ZTile> tiles;
         std::vector<unsigned char> need;
@@ -618,7 +655,10 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
             for (int ph = 0; ph < ZT_NPH; ++ph) {
                 z00[ph] = 1 << 29;
                 z01[ph] = -(1 << 29);
-                for (const int4 &sg : segs[ph]) {
+            }
+            for (int g = 0; g < ngt; ++g) {
+                const int ph = g / nmtile;
+                for (const int4 &sg : segs[g]) {
                     sx0 = std::min(sx0, sg.x); sx1 = std::max(sx1, sg.x);
                     sy0 = std::min(sy0, sg.y); sy1 = std::max(sy1, sg.y);
                     z00[ph] = std::min(z00[ph], sg.z); z01[ph] = std::max(z01[ph], sg.z);
@@ -642,7 +682,8 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                      o_line = place(line_of.size() * 4), o_sst = place(segstart.size() * 4), o_sz0 = place(segz0.size() * 4),
                      o_seg = place(segtab.size() * sizeof(int2)), o_gtab = place(gtab.size() * 4),
                      o_pinfo = place(pinfo.size() * sizeof(ZPairInfo)), o_w = place(wxyz.size() * sizeof(int4)),
-                     o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4);
+                     o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4),
+                     o_nch = place(nchunk.size() * 4);
         if ((rc = scratch_reserve(ctx, ctx->s_zipw, off))) return rc;
         char *b = reinterpret_cast<char *>(ctx->s_zipw.p);
         auto up = [&](size_t o, const void *src, size_t bytes) {
@@ -654,7 +695,8 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
             (rc = up(o_gtab, gtab.data(), gtab.size() * 4)) ||
             (rc = up(o_pinfo, pinfo.data(), pinfo.size() * sizeof(ZPairInfo))) ||
             (rc = up(o_w, wxyz.data(), wxyz.size() * sizeof(int4))) ||
-            (rc = up(o_tiles, tiles.data(), tiles.size() * sizeof(ZTile))) || (rc = up(o_kslot, kslot.data(), nk * 4)))
+            (rc = up(o_tiles, tiles.data(), tiles.size() * sizeof(ZTile))) || (rc = up(o_kslot, kslot.data(), nk * 4)) ||
+            (rc = up(o_nch, nchunk.data(), nchunk.size() * 4)))
             return rc;
         ZParams &p = plan->p;
         p.tiles = reinterpret_cast<ZTile *>(b + o_tiles);
@@ -678,7 +720,8 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         p.nzb = nzb;
         p.nblk = nblk;
         p.nslot = nslot;
-        for (int ph = 0; ph < ZT_NPH; ++ph) p.nchunk[ph] = nchunk[ph];
+        p.nchunk = reinterpret_cast<int *>(b + o_nch);
+        p.nmtile = nmtile;
         p.Z = in.d_Z;
         p.RSc = in.RSc;
         p.nmt = ctx->nmt;
@@ -695,6 +738,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
             plan->a_elems = a_elems;
             plan->R = R; plan->Rpad = Rpad; plan->nzb = nzb; plan->NBt = NBt; plan->nblk = nblk; plan->nbpad = nbpad;
             plan->nslot = nslot; plan->Kh = Kh; plan->nL = nL; plan->gx0 = gmin[0]; plan->gy0 = gmin[1]; plan->By = By;
+        plan->nmtile = nmtile;
             plan->sig = sig;
             plan->base = ctx->s_zipw.p;
             plan->valid = true;
@@ -707,7 +751,8 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     cudaMemsetAsync(A, 0, P.a_elems * 2, st);
     c_slices_kernel<<<P.R, 256, 0, st>>>(in.d_ck, in.d_Gk, in.d_npw, reinterpret_cast<int *>(b + P.o_rowk),
                                          reinterpret_cast<int *>(b + P.o_rowm), reinterpret_cast<int *>(b + P.o_line), P.gx0,
-                                         P.gy0, P.By, P.nL, reinterpret_cast<int *>(b + P.o_sst), reinterpret_cast<int *>(b + P.o_sz0),
+                                         P.gy0, P.By, P.nL, P.nmtile, reinterpret_cast<int *>(b + P.o_sst),
+                                         reinterpret_cast<int *>(b + P.o_sz0),
                                          P.Kh, P.Rpad, A, aexp);
     t_exp_kernel<<<dim3(in.nb_max, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], in.nb_max,
                                                       reinterpret_cast<int *>(b + P.o_kslot), eT);
