@@ -313,9 +313,9 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                 eph ^= 1;
             }
             if (!ok) break;
-            int r = tl.mrow + quarter * 32 + lane;           // row of A' in this q
-            bool im = r >= p.Dpad;
-            int rr = im ? r - p.Dpad : r;
+            int r = tl.mrow + quarter * 32 + lane;           // row of A' in this q: [0, D) real, [D, 2D) imaginary
+            bool im = r >= q.D;
+            int rr = im ? r - q.D : r;
             if (rr < q.D && tl.out) {
                 const int ea = p.aexp[(size_t)q.iq * p.MP + r] - 16;
                 const long long c0 = tl.ncol0 + half * 64, cend = q.colbase + q.ncols;
@@ -674,17 +674,16 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
     for (int s = 0; s < nq; ++s) {
         const QDesc &q = h_q[s];
         int klen = ((N0pad + q.D + G1_KC - 1) / G1_KC) * G1_KC;
-        int mt = (q.D + G1_BM - 1) / G1_BM;   // tiles per half that touch real rows
+        int mt = (2 * q.D + G1_BM - 1) / G1_BM;   // row tiles over the D real and D imaginary rows
         // all row tiles of one column group back to back: the Z columns are read
         // from HBM once and the Re and Im rows of Y meet in L2
         for (long long n0 = 0; n0 < q.ncols; n0 += (long long)G1_BN * CS)
-            for (int half = 0; half < 2; ++half)
-                for (int i = 0; i < mt; ++i)
-                    for (int j = 0; j < CS; ++j) {
-                        long long c0 = n0 + (long long)j * G1_BN;
-                        bool real = c0 < q.ncols;   // padding tiles repeat the group's first tile and write nothing
-                        tiles.push_back(G1Tile{s, half * Dpad + i * G1_BM, (int)(q.colbase + (real ? c0 : n0)), klen, real ? 1 : 0, 0});
-                    }
+            for (int i = 0; i < mt; ++i)
+                for (int j = 0; j < CS; ++j) {
+                    long long c0 = n0 + (long long)j * G1_BN;
+                    bool real = c0 < q.ncols;   // padding tiles repeat the group's first tile and write nothing
+                    tiles.push_back(G1Tile{s, i * G1_BM, (int)(q.colbase + (real ? c0 : n0)), klen, real ? 1 : 0, 0});
+                }
     }
     if (tiles.empty()) return HFX_OK;
     if (tiles.size() * sizeof(G1Tile) > tiles_cap) return set_err(ctx, HFX_ENOMEM, "gemm1 tile table too large");

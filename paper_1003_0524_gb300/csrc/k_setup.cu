@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include "hfx_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace hfx {
 
@@ -260,7 +261,7 @@ __global__ void transform_v_kernel(const double2 *v, double2 *VD, double2 *VB, c
 __device__ __forceinline__ double ap_elem(const double2 *VD, int r, int c, int D, int naux, int N0, int N0pad,
                                          int Dpad) {
     int HS = N0pad + Dpad;
-    int rim = r >= Dpad, rr = rim ? r - Dpad : r;
+    int rim = r >= D, rr = rim ? r - D : r;   // real rows [0, D), imaginary rows [D, 2D)
     int cim = c >= HS, u = cim ? c - HS : c;
     int j = -1;
     if (u < N0pad) j = (u < N0) ? u : -1;
@@ -273,33 +274,29 @@ __device__ __forceinline__ double ap_elem(const double2 *VD, int r, int c, int D
     return val.x;
 }
 
-// Fixed-point slices of A' (one block per row): exponent e_r with
-// max_c |A'_rc| < 2^e_r, then four 8-bit integer slices per element stored
+// Fixed-point slices of A' (one block per row; rows [0, D) real, [D, 2D)
+// imaginary, the rest of the 2 Dpad rows zero): exponent e_r with
+// max_c |A'_rc| < 2^e_r, then the four slices of tc_ptx.cuh per element, stored
 // as BF16 planes [4][2 Dpad][RS] (the slice format of k_contract_tc.cu).
 __global__ void build_ap_kernel(const double2 *VD, __nv_bfloat16 *Ap, int *aexp, int D, int naux, int N0, int N0pad,
                                 int Dpad, int RS) {
     int r = blockIdx.x;
     long long plane = 2LL * Dpad * RS;
-    __shared__ double red[256];
-    double mx = 0.0;
-    for (int c = threadIdx.x; c < RS; c += blockDim.x) mx = fmax(mx, fabs(ap_elem(VD, r, c, D, naux, N0, N0pad, Dpad)));
+    __shared__ unsigned long long red[256];
+    unsigned long long mx = 0;
+    for (int c = threadIdx.x; c < RS; c += blockDim.x) mx = max(mx, tc::abs_bits(ap_elem(VD, r, c, D, naux, N0, N0pad, Dpad)));
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + st]);
+        if (threadIdx.x < st) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + st]);
         __syncthreads();
     }
-    int e = 0;
-    if (red[0] > 0.0) frexp(red[0], &e);
+    const int e = tc::line_exp_bits(red[0]);
     if (threadIdx.x == 0) aexp[r] = e;
     for (int c = threadIdx.x; c < RS; c += blockDim.x) {
-        double u = ldexp(ap_elem(VD, r, c, D, naux, N0, N0pad, Dpad), -e);
-        for (int i = 0; i < 4; ++i) {
-            u *= 256.0;
-            double sg = rint(u);
-            u -= sg;
-            Ap[i * plane + (long long)r * RS + c] = __double2bfloat16(sg);
-        }
+        __nv_bfloat16 sl[tc::NPL];
+        tc::slice4(ap_elem(VD, r, c, D, naux, N0, N0pad, Dpad), e, sl);
+        for (int i = 0; i < tc::NPL; ++i) Ap[i * plane + (long long)r * RS + c] = sl[i];
     }
 }
 
