@@ -630,6 +630,16 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
         cudaMemGetInfo(&fr, &totm);
         budget = (size_t)(0.55 * (double)fr);
     }
+    // band block of the Z^H Y tiles: a multiple of 8 up to 64. A tile's MMA work and operand bytes grow
+    // with NB (its 128-row A operand is padded), so pick the NB with the least nblk^2 * NB.
+    int NB = 8;
+    {
+        long long best = 1LL << 60;
+        for (int nbc = 8; nbc <= 64; nbc += 8) {
+            long long nblk = (nb_max + nbc - 1) / nbc, cost = nblk * nblk * nbc;
+            if (cost < best || (cost == best && nbc > NB)) { best = cost; NB = nbc; }
+        }
+    }
     auto qbytes = [&](int iq, long long *ncols_out, int *npairs_out) {
         long long nc = 0;
         int np = 0;
@@ -640,8 +650,8 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
             nc += (long long)hno[ikp] * hnb[ik];
             ++np;
             if (tc) {
-                int nblk = (hnb[ik] + 63) / 64;
-                praw += (size_t)nblk * nblk * 128 * 128 * sizeof(double);
+                int nblk = (hnb[ik] + NB - 1) / NB;
+                praw += (size_t)nblk * nblk * (2 * NB) * (2 * NB) * sizeof(double);
             } else {
                 praw += (size_t)hnb[ik] * hnb[ik] * sizeof(double2);
             }
@@ -666,8 +676,6 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
         }
         if (!cur.qs.empty()) batches.push_back(cur);
     }
-    // NB for the tensor-core Z^H Y tile: 16-row multiple covering the band windows, at most 64
-    int NB = (int)std::min<long long>(64, rup(std::max(nb_max, 16), 16));
 
     cudaEvent_t e_pre = evs.make(ctx);
     float ms_s1 = 0.f, ms_ct = 0.f;

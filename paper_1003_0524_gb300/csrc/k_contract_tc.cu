@@ -744,7 +744,7 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
                     const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *h_pairs,
                     const PairDesc *d_pairs, int npairs, const QDesc *d_q, int NB, const long long *d_praw_off,
                     double *d_praw, void *d_tiles_buf, size_t tiles_cap) {
-    if (NB % 16 != 0 || NB < 16 || NB > 64) return set_err(ctx, HFX_EINVAL, "gemm2: band tile must be 16, 32, 48 or 64");
+    if (NB % 8 != 0 || NB < 8 || NB > 64) return set_err(ctx, HFX_EINVAL, "gemm2: band tile must be a multiple of 8 up to 64");
     std::vector<G2Tile> tiles;
     for (int i = 0; i < npairs; ++i) {
         int nblk = (h_pairs[i].nb + NB - 1) / NB;
@@ -784,9 +784,13 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
         kern<<<grid, 64 + 32 * G2_EPI_WARPS, smem, ctx->stream>>>(mZ, mY, p);
     };
     switch (NB) {
+    case 8: go(gemm2_kernel<8>); break;
     case 16: go(gemm2_kernel<16>); break;
+    case 24: go(gemm2_kernel<24>); break;
     case 32: go(gemm2_kernel<32>); break;
+    case 40: go(gemm2_kernel<40>); break;
     case 48: go(gemm2_kernel<48>); break;
+    case 56: go(gemm2_kernel<56>); break;
     default: go(gemm2_kernel<64>); break;
     }
     return cuda_check(ctx, cudaGetLastError(), "gemm2 launch");
