@@ -6,18 +6,18 @@
 // (k, q) that needs this W is one row of a GEMM
 //   Z[(k', m), n] = sum_{G1} C[(k', m), G1] T_k[n](W + G1),   C = conj(c),
 // whose reduction index G1 runs over the plane waves of all k' in segments of
-// 8 consecutive z values along the (x, y) lines of the plane-wave spheres.
+// 4 consecutive z values along the (x, y) lines of the plane-wave spheres.
 //
 // Operands (fixed-point slices of tc_ptx.cuh, real embedding of the complex
-// product with the real and imaginary outputs side by side in N):
-//   A row (k', m) = [ Re C | Im C ]                       (128-byte swizzle, 2-D TMA)
-//   B columns     = [ T_r ; -T_i ] (real out), [ T_i ; T_r ] (imag out)
-// The sliced T box is stored in blocks of 8 z with all planes, both parts of
-// an output block and all bands of a band block contiguous, so the B operand
-// of one segment is a single 1-D bulk copy (no swizzle).  A copy must start on
-// a 16-byte boundary, i.e. at a multiple of 8 in z: T is kept in four copies
-// shifted by 0, 2, 4, 6 in z, and the segments of every line start on the
-// z parity of W (two phase variants of the C slices).
+// product with the real and imaginary outputs side by side in N); one segment
+// is 8 K values, the real and imaginary parts of its 4 z values:
+//   A row (k', m) = [ Re C(4 z) | Im C(4 z) ] per segment   (128-byte swizzle, 2-D TMA)
+//   B rows        = [ T_r(4 z) | -T_i(4 z) ] (real out), [ T_i(4 z) | T_r(4 z) ] (imag out)
+// The sliced T box is stored in blocks of 4 z with all planes and both output
+// rows of all bands of a band block contiguous, so the B operand of one
+// segment is a single 1-D bulk copy (no swizzle).  A copy must start on a
+// 16-byte boundary, i.e. at a multiple of 4 in z: T is kept in four copies
+// shifted by 0, 1, 2, 3 in z, so a segment may start at any z.
 #include <algorithm>
 #include <memory>
 #include <string>
@@ -36,9 +36,8 @@ constexpr int ZT_A_PLANE = 128 * 64 * 2;   // 16 KB: 128 rows x 64 K
 constexpr int ZT_GROUP = 4;                // 64-K chunks per exact group (256)
 constexpr int ZT_STAGES = 2;
 constexpr int ZT_EPI = 8;
-constexpr int ZT_NPH = 2;                  // z phases of the segment grid (segment starts mod 2)
-constexpr int ZT_NCOPY = 8 / ZT_NPH;       // z-shifted copies of the sliced T box
-constexpr int ZT_NPART = 4;                // T parts: Re, Im, -Im, Re
+constexpr int ZT_SEGZ = 4;                 // z values per segment (8 K values: real and imaginary parts)
+constexpr int ZT_NCOPY = ZT_SEGZ;          // z-shifted copies of the sliced T box
 
 // slice-product term t: weight class w, slice of A, slice of B (a + b = w)
 __device__ __forceinline__ constexpr int term_w(int t) { return t < 1 ? 0 : t < 3 ? 1 : t < 6 ? 2 : 3; }
@@ -57,19 +56,19 @@ __device__ __forceinline__ double scale2(double d, int k) {
 
 // ------------------------------------------------------------- C slices
 // One block per row r = (k', m): exponent over |Re c|, |Im c| of the row, then
-// [Re C | Im C] = [c_r | -c_i] at K = segment * 8 + (z - z0) of the segment grid
-// of the row's tile, in every phase.
+// Re C = c_r at K = 8 s + j and Im C = -c_i at K = 8 s + 4 + j, where segment
+// s = segstart + (z - z0) / 4 and j = (z - z0) mod 4 on the segment grid of the
+// row's tile.
 __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int *const *__restrict__ Gk,
                                 const int *__restrict__ npw_k, const int *__restrict__ rowk, const int *__restrict__ rowm,
-                                const int *__restrict__ line_of, int gx0, int gy0, int By, int nL, int nmtile,
-                                const int *__restrict__ segstart, const int *__restrict__ segz0, int Kh, int Rpad,
+                                const int *__restrict__ line_of, int gx0, int gy0, int By, int nL,
+                                const int *__restrict__ segstart, const int *__restrict__ segz0, int Kp, int Rpad,
                                 __nv_bfloat16 *__restrict__ A, int *__restrict__ aexp) {
     int r = blockIdx.x;
     int kp = rowk[r], m = rowm[r];
     int npw = npw_k[kp];
     const double2 *c = ck[kp] + (size_t)m * npw;
     const int *G = Gk[kp];
-    const long long W2 = 2LL * Kh;
     __shared__ unsigned long long red[256];
     unsigned long long mx = 0;
     for (int i = threadIdx.x; i < npw; i += blockDim.x) mx = max(mx, max(abs_bits(c[i].x), abs_bits(c[i].y)));
@@ -88,15 +87,14 @@ __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int
         __nv_bfloat16 sr[NPL], si[NPL];
         slice4(c[i].x, e, sr);
         slice4(-c[i].y, e, si);
-        for (int ph = 0; ph < ZT_NPH; ++ph) {
-            const size_t sl = ((size_t)ph * nmtile + r / ZT_BM) * nL + li;   // segment grid of the row's tile
-            long long K = (long long)segstart[sl] * 8 + (z - segz0[sl]);
+        const size_t sl = (size_t)(r / ZT_BM) * nL + li;   // segment grid of the row's tile
+        const int dz = z - segz0[sl];
+        const long long K = (long long)(segstart[sl] + dz / ZT_SEGZ) * 8 + dz % ZT_SEGZ;
 #pragma unroll
-            for (int p = 0; p < NPL; ++p) {
-                __nv_bfloat16 *row = A + ((long long)(ph * NPL + p) * Rpad + r) * W2;
-                row[K] = sr[p];
-                row[Kh + K] = si[p];
-            }
+        for (int p = 0; p < NPL; ++p) {
+            __nv_bfloat16 *row = A + ((long long)p * Rpad + r) * Kp;
+            row[K] = sr[p];
+            row[K + ZT_SEGZ] = si[p];
         }
     }
 }
@@ -121,18 +119,19 @@ __global__ void t_exp_kernel(const double2 *const *__restrict__ Tk, const int *_
     if (threadIdx.x == 0) eT[(size_t)k * nbmax + n] = line_exp_bits(red[0]);
 }
 
-// Slices of T: one thread per (k, cell (X, Y, zb), band n) slices the 14 values
-// T_k[n](X, Y, 8 zb .. 8 zb + 13) once and writes, for every copy c (T shifted
-// by c * ZT_NPH in z), plane p and part (Re T, Im T, -Im T, Re T), the 8 z
-// values of its row into
-//   Tq[c][k][X][Y][zb][h][b][p][part & 1][j][0..7],  part = 2 h + (part & 1),
-// n = b NB + j; bands past nb(k) and z past the box are 0.  Consecutive threads
-// take consecutive bands, so each 16-byte row store is coalesced.  One
-// (c, k, X, Y, zb, h, b) block -- all planes of one segment -- is contiguous.
+// Slices of T: one thread per (k, cell (X, Y, zb), band n) slices the 7 values
+// T_k[n](X, Y, 4 zb .. 4 zb + 6) once and writes, for every copy c (T shifted
+// by c in z) and plane p, the two B rows of band n = b NB + j over the 4 z
+// values 4 zb + c .. 4 zb + c + 3:
+//   Tq[c][k][X][Y][zb][b][p][j]      = [ Re T (4 z) | -Im T (4 z) ]   (real output)
+//   Tq[c][k][X][Y][zb][b][p][NB + j] = [ Im T (4 z) |  Re T (4 z) ]   (imaginary output)
+// (16 bytes each); bands past nb(k) and z past the box are 0.  Consecutive
+// threads take consecutive bands, so the row stores are coalesced.  One
+// (c, k, X, Y, zb, b) block -- all planes of one segment -- is contiguous.
 __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int *__restrict__ nb_k, int td0, int td1,
                                 int td2, int nzb, int NB, int nblk, int nbmax, int nslot, const int *__restrict__ kslot,
                                 const int *__restrict__ eT, __nv_bfloat16 *__restrict__ Tq) {
-    constexpr int NZ = 8 + (ZT_NCOPY - 1) * ZT_NPH;           // z values a thread needs
+    constexpr int NZ = ZT_SEGZ + ZT_NCOPY - 1;                // z values a thread needs
     const int k = blockIdx.y;
     const int slot = kslot[k];
     if (slot < 0) return;
@@ -151,34 +150,30 @@ __global__ void t_slices_kernel(const double2 *const *__restrict__ Tk, const int
     __nv_bfloat16 sr[NZ][NPL], si[NZ][NPL];
 #pragma unroll
     for (int t = 0; t < NZ; ++t) {
-        const int z = zb * 8 + t;
+        const int z = zb * ZT_SEGZ + t;
         const double2 v = (live && z < td2) ? T[z] : make_double2(0.0, 0.0);
         slice4(v.x, e, sr[t]);
         slice4(v.y, e, si[t]);
     }
     const int b = n / NB, j = n % NB;
-    const long long blk = 2LL * NB * 8;                       // one plane of a block: 2 parts x NB bands x 8 z
+    const long long blk = 2LL * NB * 8;                       // one plane of a block: 2 NB rows of 8 values
 #pragma unroll
     for (int c = 0; c < ZT_NCOPY; ++c) {
         const long long cell = ((long long)c * nslot + slot) * ncell + cellk;
+        __nv_bfloat16 *dst = Tq + (cell * nblk + b) * (NPL * blk) + (long long)j * 8;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
-            uint4 re, im, nim;
-            uint32_t *pr = &re.x, *pi = &im.x, *pn = &nim.x;
-#pragma unroll
-            for (int t = 0; t < 8; t += 2) {
-                const int z0 = c * ZT_NPH + t;
-                pr[t / 2] = pack_bf16x2(sr[z0][p], sr[z0 + 1][p]);
-                pi[t / 2] = pack_bf16x2(si[z0][p], si[z0 + 1][p]);
-                pn[t / 2] = pack_bf16x2(__hneg(si[z0][p]), __hneg(si[z0 + 1][p]));
-            }
-            // parts: h = 0 holds (Re T, Im T), h = 1 holds (-Im T, Re T)
-            __nv_bfloat16 *b0 = Tq + ((cell * 2 + 0) * nblk + b) * (NPL * blk) + ((long long)(p * 2) * NB + j) * 8;
-            __nv_bfloat16 *b1 = Tq + ((cell * 2 + 1) * nblk + b) * (NPL * blk) + ((long long)(p * 2) * NB + j) * 8;
-            *reinterpret_cast<uint4 *>(b0) = re;
-            *reinterpret_cast<uint4 *>(b0 + NB * 8) = im;
-            *reinterpret_cast<uint4 *>(b1) = nim;
-            *reinterpret_cast<uint4 *>(b1 + NB * 8) = re;
+            uint4 ro, io;   // real-output row, imaginary-output row
+            ro.x = pack_bf16x2(sr[c][p], sr[c + 1][p]);
+            ro.y = pack_bf16x2(sr[c + 2][p], sr[c + 3][p]);
+            ro.z = pack_bf16x2(__hneg(si[c][p]), __hneg(si[c + 1][p]));
+            ro.w = pack_bf16x2(__hneg(si[c + 2][p]), __hneg(si[c + 3][p]));
+            io.x = pack_bf16x2(si[c][p], si[c + 1][p]);
+            io.y = pack_bf16x2(si[c + 2][p], si[c + 3][p]);
+            io.z = ro.x;
+            io.w = ro.y;
+            *reinterpret_cast<uint4 *>(dst + p * blk) = ro;
+            *reinterpret_cast<uint4 *>(dst + p * blk + NB * 8) = io;
         }
     }
 }
@@ -191,7 +186,7 @@ struct ZPairInfo { int pair; int g0x, g0y, g0z; };
 struct ZParams {
     const ZTile *tiles;
     int ntiles;
-    const int4 *wxyz;             // [nw] shift W (x, y, z) and its z phase (w)
+    const int4 *wxyz;             // [nw] shift W (x, y, z)
     const ZPairInfo *pinfo;       // [nk][nk] by (k, k')
     const PairDesc *pairs;
     const int *gtab;              // [nq][ax][ay][az] aux index or -1
@@ -199,14 +194,14 @@ struct ZParams {
     const int *rowk, *rowm;       // rows of A (k', m)
     const int *aexp, *eT;         // row exponents, [k][n] band exponents
     const int *kslot;             // k -> slot of its T slices
-    const int2 *segoff;           // [phase][row tile][segment] (x td1 + y of its line, z0 - phase)
-    int nsegp_max, nmtile;
-    const int *nchunk;            // [phase][row tile] 64-K chunks per K half
+    const int2 *segoff;           // [row tile][segment] (x td1 + y of its line, z0)
+    int nsegp_max;
+    const int *nchunk;            // [row tile] 64-K chunks
     const __nv_bfloat16 *Tq;      // sliced T blocks (t_slices_kernel layout)
     int td0, td1, nzb, nblk, nslot;
     double2 *Z;
     long long RSc;
-    int nmt, nk, R, Rpad, Kh, nbmax, tlo0, tlo1, tlo2;
+    int nmt, nk, R, Rpad, nbmax, tlo0, tlo1, tlo2;
     double rs;                    // Omega^{-1/2}
     int *err;
 };
@@ -216,7 +211,7 @@ template <int NB>
 __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                       ZParams p) {
     constexpr int N = 2 * NB;                            // real and imaginary output columns
-    constexpr int SEGB = N * 16;                         // one segment of one plane: N rows x 8 z
+    constexpr int SEGB = N * 16;                         // one segment of one plane: N rows x 8 K
     constexpr int SEG4 = NPL * SEGB;                     // one segment, all planes (one bulk copy)
     constexpr int STAGE = NPL * ZT_A_PLANE + 8 * SEG4;   // eight segments per 64-K chunk
     extern __shared__ __align__(1024) unsigned char zt_smem[];
@@ -249,21 +244,20 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
         uint32_t ph = 0;
         int issued = 0;
         const int bj = lane & 7;
-        const long long cellb = 2LL * p.nblk * SEG4;
         const char *tq = reinterpret_cast<const char *>(p.Tq);
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
             const ZTile tl = p.tiles[t];
             const int4 W = p.wxyz[tl.w];
-            const int phz = W.w, gt = phz * p.nmtile + tl.mrow / ZT_BM, nch = p.nchunk[gt];
+            const int gt = tl.mrow / ZT_BM, nch = p.nchunk[gt];
             const int slot = p.kslot[tl.k];
             const int2 *so = p.segoff + (size_t)gt * p.nsegp_max;
             // a segment starts at X = W_x + x - tlo_x, Y likewise, and T z index
-            // Zs = (W_z + ph - tlo_z) + (z0 - ph), a multiple of ZT_NPH: copy
-            // c = (Zs mod 8) / ZT_NPH, z block Zs / 8 -- inside the box by construction
+            // Zs = W_z - tlo_z + z0: copy Zs mod 4, z block Zs / 4 -- inside the
+            // box by construction
             const int bxy = (W.x - p.tlo0) * p.td1 + (W.y - p.tlo1);
-            const int bz = W.z + phz - p.tlo2;
+            const int bz = W.z - p.tlo2;
             bool stop = false;
-            for (int c = 0; c < 2 * nch; ++c) {
+            for (int c = 0; c < nch; ++c) {
                 int ok = 1;
                 if (lane == 0) {
                     ok = mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma) ? 1 : 0;
@@ -271,19 +265,17 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                 }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { stop = true; break; }
-                const int h = c >= nch, cl = h ? c - nch : c;
                 unsigned char *st = stages + (size_t)s * STAGE;
                 if (lane < NPL)
-                    tma_load_2d(saddr(st + lane * ZT_A_PLANE), &tmA, &full_bar[s], h * p.Kh + cl * 64,
-                                (phz * NPL + lane) * p.Rpad + tl.mrow);
-                const long long hb = ((long long)h * p.nblk + tl.nblk) * SEG4;
+                    tma_load_2d(saddr(st + lane * ZT_A_PLANE), &tmA, &full_bar[s], c * 64, lane * p.Rpad + tl.mrow);
                 if (lane < 8) {
-                    const int2 sg = so[cl * 8 + bj];
+                    const int2 sg = so[c * 8 + bj];
                     const int Zs = bz + sg.y;
-                    const int cp = (Zs & 7) / ZT_NPH;
+                    const int cp = Zs & (ZT_NCOPY - 1);
                     const long long cell =
-                        (((long long)cp * p.nslot + slot) * ((long long)p.td0 * p.td1) + bxy + sg.x) * p.nzb + (Zs >> 3);
-                    bulk_load(saddr(st + NPL * ZT_A_PLANE + bj * SEG4), tq + cell * cellb + hb, SEG4, &full_bar[s]);
+                        (((long long)cp * p.nslot + slot) * ((long long)p.td0 * p.td1) + bxy + sg.x) * p.nzb + Zs / ZT_SEGZ;
+                    bulk_load(saddr(st + NPL * ZT_A_PLANE + bj * SEG4), tq + (cell * p.nblk + tl.nblk) * SEG4, SEG4,
+                              &full_bar[s]);
                 }
                 ++issued;
                 if (++s == ZT_STAGES) { s = 0; ph ^= 1; }
@@ -302,7 +294,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             bool ok = true;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
                 const ZTile tm0 = p.tiles[t];
-                const int nchunk = 2 * p.nchunk[p.wxyz[tm0.w].w * p.nmtile + tm0.mrow / ZT_BM];
+                const int nchunk = p.nchunk[tm0.mrow / ZT_BM];
                 for (int g0 = 0; g0 < nchunk && ok; g0 += ZT_GROUP) {
                     if (!mbar_wait(&tempty_bar, eph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                     tc_fence_after();
@@ -343,7 +335,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             const ZTile tl = p.tiles[t];
             const int4 W = p.wxyz[tl.w];
-            const int ngroups = (2 * p.nchunk[W.w * p.nmtile + tl.mrow / ZT_BM] + ZT_GROUP - 1) / ZT_GROUP;
+            const int ngroups = (p.nchunk[tl.mrow / ZT_BM] + ZT_GROUP - 1) / ZT_GROUP;
             uint64_t hr[NH / 2], lr[NH / 2], hm[NH / 2], lm[NH / 2];   // packed pairs of columns
 #pragma unroll
             for (int j = 0; j < NH / 2; ++j) { hr[j] = 0; lr[j] = 0; hm[j] = 0; lm[j] = 0; }
@@ -441,7 +433,7 @@ struct ZipwPlan {
     ZParams p;
     size_t o_rowk = 0, o_rowm = 0, o_line = 0, o_sst = 0, o_sz0 = 0, o_tp = 0, o_a = 0, o_aexp = 0, o_eT = 0, o_kslot = 0;
     size_t a_elems = 0;
-    int R = 0, Rpad = 0, nzb = 0, NBt = 0, nblk = 0, nbpad = 0, nslot = 0, Kh = 0, nL = 0, gx0 = 0, gy0 = 0, By = 0, nmtile = 0;
+    int R = 0, Rpad = 0, nzb = 0, NBt = 0, nblk = 0, nbpad = 0, nslot = 0, Kp = 0, nL = 0, gx0 = 0, gy0 = 0, By = 0, nmtile = 0;
 };
 
 // FNV-1a over everything the tables depend on
@@ -535,11 +527,10 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         std::vector<std::vector<int>> tile_k(nmtile);
         for (int r = 0; r < R; ++r)
             if (tile_k[r / ZT_BM].empty() || tile_k[r / ZT_BM].back() != rowk[r]) tile_k[r / ZT_BM].push_back(rowk[r]);
-        // segment grid per (z phase, row tile): the lines of the tile's spheres;
-        // segments of a line start at z0 = ph (mod ZT_NPH)
-        const int ngt = ZT_NPH * nmtile;
-        std::vector<int> segstart((size_t)ngt * nL, 0), segz0((size_t)ngt * nL, 0), nseg(ngt);
-        std::vector<std::vector<int4>> segs(ngt);
+        // segment grid per row tile: the lines of the tile's spheres, each cut
+        // into segments of ZT_SEGZ z values from its lowest z
+        std::vector<int> segstart((size_t)nmtile * nL, 0), segz0((size_t)nmtile * nL, 0), nseg(nmtile);
+        std::vector<std::vector<int4>> segs(nmtile);
         std::vector<int> tzlo(nL), tzhi(nL);
         for (int t = 0; t < nmtile; ++t) {
             std::fill(tzlo.begin(), tzlo.end(), 1 << 29);
@@ -552,33 +543,28 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                     tzhi[l] = std::max(tzhi[l], G[i + 2]);
                 }
             }
-            for (int ph = 0; ph < ZT_NPH; ++ph) {
-                const int g = ph * nmtile + t;
-                for (int l = 0; l < nL; ++l) {
-                    if (tzlo[l] > tzhi[l]) continue;
-                    int z0 = tzlo[l] - (((tzlo[l] - ph) % ZT_NPH) + ZT_NPH) % ZT_NPH;
-                    segstart[(size_t)g * nL + l] = (int)segs[g].size();
-                    segz0[(size_t)g * nL + l] = z0;
-                    for (int z = z0; z <= tzhi[l]; z += 8) segs[g].push_back(make_int4(lx[l], ly[l], z, 0));
-                }
-                if (segs[g].empty()) segs[g].push_back(make_int4(lx[0], ly[0], lzlo[0] - (((lzlo[0] - ph) % ZT_NPH) + ZT_NPH) % ZT_NPH, 0));
-                nseg[g] = (int)segs[g].size();
+            for (int l = 0; l < nL; ++l) {
+                if (tzlo[l] > tzhi[l]) continue;
+                segstart[(size_t)t * nL + l] = (int)segs[t].size();
+                segz0[(size_t)t * nL + l] = tzlo[l];
+                for (int z = tzlo[l]; z <= tzhi[l]; z += ZT_SEGZ) segs[t].push_back(make_int4(lx[l], ly[l], z, 0));
             }
+            if (segs[t].empty()) segs[t].push_back(make_int4(lx[0], ly[0], lzlo[0], 0));
+            nseg[t] = (int)segs[t].size();
         }
         int nsegp_max = 0;
-        for (int g = 0; g < ngt; ++g) nsegp_max = std::max(nsegp_max, (nseg[g] + 7) / 8 * 8);
-        const int Kh = nsegp_max * 8;
-        const int nzb = (in.tdim[2] + 7) / 8;
-        // every segment: (x td1 + y) of its line and z0 - ph, offsets from the tile
-        // shift (W_x - tlo_x) td1 + (W_y - tlo_y) and W_z + ph - tlo_z
-        std::vector<int2> segtab((size_t)ngt * nsegp_max);
-        std::vector<int> nchunk(ngt);
-        for (int g = 0; g < ngt; ++g) {
-            const int ph = g / nmtile;
-            nchunk[g] = (nseg[g] + 7) / 8;
+        for (int t = 0; t < nmtile; ++t) nsegp_max = std::max(nsegp_max, (nseg[t] + 7) / 8 * 8);
+        const int Kp = nsegp_max * 8;   // K values of an A row: 8 per segment
+        const int nzb = (in.tdim[2] + ZT_SEGZ - 1) / ZT_SEGZ;
+        // every segment: (x td1 + y) of its line and its z0, offsets from the tile
+        // shift (W_x - tlo_x) td1 + (W_y - tlo_y) and W_z - tlo_z
+        std::vector<int2> segtab((size_t)nmtile * nsegp_max);
+        std::vector<int> nchunk(nmtile);
+        for (int t = 0; t < nmtile; ++t) {
+            nchunk[t] = (nseg[t] + 7) / 8;
             for (int s2 = 0; s2 < nsegp_max; ++s2) {
-                const int4 sg = s2 < nseg[g] ? segs[g][s2] : segs[g][0];   // padding: any valid block
-                segtab[(size_t)g * nsegp_max + s2] = make_int2(sg.x * in.tdim[1] + sg.y, sg.z - ph);
+                const int4 sg = s2 < nseg[t] ? segs[t][s2] : segs[t][0];   // padding: any valid block
+                segtab[(size_t)t * nsegp_max + s2] = make_int2(sg.x * in.tdim[1] + sg.y, sg.z);
             }
         }
         const int NBt = pick_nb(in.nb_max);
@@ -636,45 +622,35 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                 if (!any) continue;
                 const int widx = (int)wxyz.size();
                 const int w2 = (int)(wi % wd[2]), w1 = (int)((wi / wd[2]) % wd[1]), w0 = (int)(wi / ((size_t)wd[1] * wd[2]));
-                const int Wz = w2 + amin[2];
-                // z phase: the T z index of every segment start is a multiple of ZT_NPH
-                wxyz.push_back(make_int4(w0 + amin[0], w1 + amin[1], Wz, (((in.tlo[2] - Wz) % ZT_NPH) + ZT_NPH) % ZT_NPH));
+                wxyz.push_back(make_int4(w0 + amin[0], w1 + amin[1], w2 + amin[2], 0));
                 for (int t = 0; t < nmtile; ++t)
                     if (need[wi * nmtile + t])
                         for (int b = 0; b < nblk; ++b) tiles.push_back(ZTile{ik, widx, t * ZT_BM, b});
             }
         }
         if (tiles.empty()) return HFX_OK;
-        // tiles of one z phase together: the C slices of a phase (8.4 MB for 512
-        // rows) and T of one k stay in L2 while the CTAs sweep that k's shifts
-        std::stable_sort(tiles.begin(), tiles.end(),
-                         [&](const ZTile &a, const ZTile &b) { return wxyz[a.w].w < wxyz[b.w].w; });
+        // tiles stay k-major: T of one k and the C slices (4 planes x 512 rows x
+        // Kp values) stay in L2 while the CTAs sweep that k's shifts
         {
             // every B segment of every tile must be one whole z block inside the sliced T box
-            int sx0 = 1 << 29, sx1 = -(1 << 29), sy0 = 1 << 29, sy1 = -(1 << 29), z00[ZT_NPH], z01[ZT_NPH];
-            for (int ph = 0; ph < ZT_NPH; ++ph) {
-                z00[ph] = 1 << 29;
-                z01[ph] = -(1 << 29);
-            }
-            for (int g = 0; g < ngt; ++g) {
-                const int ph = g / nmtile;
-                for (const int4 &sg : segs[g]) {
+            int sx0 = 1 << 29, sx1 = -(1 << 29), sy0 = 1 << 29, sy1 = -(1 << 29), sz0 = 1 << 29, sz1 = -(1 << 29);
+            for (int t = 0; t < nmtile; ++t)
+                for (const int4 &sg : segs[t]) {
                     sx0 = std::min(sx0, sg.x); sx1 = std::max(sx1, sg.x);
                     sy0 = std::min(sy0, sg.y); sy1 = std::max(sy1, sg.y);
-                    z00[ph] = std::min(z00[ph], sg.z); z01[ph] = std::max(z01[ph], sg.z);
+                    sz0 = std::min(sz0, sg.z); sz1 = std::max(sz1, sg.z);
                 }
-            }
             for (const int4 &W : wxyz) {
-                const int Z0 = W.z + z00[W.w] - in.tlo[2], Z1 = W.z + z01[W.w] - in.tlo[2];
+                const int Z0 = W.z + sz0 - in.tlo[2], Z1 = W.z + sz1 - in.tlo[2];
                 if (W.x + sx0 - in.tlo[0] < 0 || W.x + sx1 - in.tlo[0] >= in.tdim[0] || W.y + sy0 - in.tlo[1] < 0 ||
-                    W.y + sy1 - in.tlo[1] >= in.tdim[1] || Z0 < 0 || (Z0 % ZT_NPH) != 0 || (Z1 >> 3) >= nzb)
+                    W.y + sy1 - in.tlo[1] >= in.tdim[1] || Z0 < 0 || Z1 / ZT_SEGZ >= nzb)
                     return set_err(ctx, HFX_EUNSUPPORTED, "interstitial segment outside the step-function box");
             }
         }
         // ---- device buffers (scratch s_zipw)
         const int nbpad = nblk * NBt;
-        const size_t tp_elems = (size_t)ZT_NCOPY * nslot * NPL * ZT_NPART * nbpad * in.tdim[0] * in.tdim[1] * nzb * 8;
-        const size_t a_elems = (size_t)ZT_NPH * NPL * Rpad * 2 * Kh;
+        const size_t tp_elems = (size_t)ZT_NCOPY * nslot * in.tdim[0] * in.tdim[1] * nzb * NPL * 2 * nbpad * 8;
+        const size_t a_elems = (size_t)NPL * Rpad * Kp;
         size_t off = 0;
         auto place = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
         const size_t o_tp = place(tp_elems * 2), o_a = place(a_elems * 2), o_aexp = place((size_t)Rpad * 4),
@@ -721,14 +697,12 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         p.nblk = nblk;
         p.nslot = nslot;
         p.nchunk = reinterpret_cast<int *>(b + o_nch);
-        p.nmtile = nmtile;
         p.Z = in.d_Z;
         p.RSc = in.RSc;
         p.nmt = ctx->nmt;
         p.nk = nk;
         p.R = R;
         p.Rpad = Rpad;
-        p.Kh = Kh;
         p.nbmax = in.nb_max;
         p.tlo0 = in.tlo[0]; p.tlo1 = in.tlo[1]; p.tlo2 = in.tlo[2];
         p.rs = 1.0 / sqrt(ctx->omega);
@@ -737,7 +711,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
             plan->o_tp = o_tp; plan->o_a = o_a; plan->o_aexp = o_aexp; plan->o_eT = o_eT; plan->o_kslot = o_kslot;
             plan->a_elems = a_elems;
             plan->R = R; plan->Rpad = Rpad; plan->nzb = nzb; plan->NBt = NBt; plan->nblk = nblk; plan->nbpad = nbpad;
-            plan->nslot = nslot; plan->Kh = Kh; plan->nL = nL; plan->gx0 = gmin[0]; plan->gy0 = gmin[1]; plan->By = By;
+            plan->nslot = nslot; plan->Kp = Kp; plan->nL = nL; plan->gx0 = gmin[0]; plan->gy0 = gmin[1]; plan->By = By;
         plan->nmtile = nmtile;
             plan->sig = sig;
             plan->base = ctx->s_zipw.p;
@@ -751,9 +725,9 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     cudaMemsetAsync(A, 0, P.a_elems * 2, st);
     c_slices_kernel<<<P.R, 256, 0, st>>>(in.d_ck, in.d_Gk, in.d_npw, reinterpret_cast<int *>(b + P.o_rowk),
                                          reinterpret_cast<int *>(b + P.o_rowm), reinterpret_cast<int *>(b + P.o_line), P.gx0,
-                                         P.gy0, P.By, P.nL, P.nmtile, reinterpret_cast<int *>(b + P.o_sst),
+                                         P.gy0, P.By, P.nL, reinterpret_cast<int *>(b + P.o_sst),
                                          reinterpret_cast<int *>(b + P.o_sz0),
-                                         P.Kh, P.Rpad, A, aexp);
+                                         P.Kp, P.Rpad, A, aexp);
     t_exp_kernel<<<dim3(in.nb_max, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], in.nb_max,
                                                       reinterpret_cast<int *>(b + P.o_kslot), eT);
     {
@@ -765,7 +739,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
     if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw slices"))) return rc;
     // ---- tensor maps and launch
     CUtensorMap mA;
-    if ((rc = make_map_2d(ctx, &mA, A, (long long)ZT_NPH * NPL * P.Rpad, 2LL * P.Kh, ZT_BM))) return rc;
+    if ((rc = make_map_2d(ctx, &mA, A, (long long)NPL * P.Rpad, P.Kp, ZT_BM))) return rc;
     ZParams p = P.p;   // per-call pointers: the batch's pairs and projections, the error word
     p.pairs = in.d_pairs;
     p.Z = in.d_Z;
