@@ -39,11 +39,6 @@ constexpr int ZT_EPI = 8;
 constexpr int ZT_SEGZ = 4;                 // z values per segment (8 K values: real and imaginary parts)
 constexpr int ZT_NCOPY = ZT_SEGZ;          // z-shifted copies of the sliced T box
 
-// slice-product term t: weight class w, slice of A, slice of B (a + b = w)
-__device__ __forceinline__ constexpr int term_w(int t) { return t < 1 ? 0 : t < 3 ? 1 : t < 6 ? 2 : 3; }
-__device__ __forceinline__ constexpr int term_a(int t) { return t - term_w(t) * (term_w(t) + 1) / 2; }
-__device__ __forceinline__ constexpr int term_b(int t) { return term_w(t) - term_a(t); }
-
 __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
@@ -290,7 +285,11 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
         if (lane == 0) {
             int s = 0;
             uint32_t ph = 0, eph = 0;
-            constexpr uint32_t idesc = idesc_bf16(ZT_BM, N);
+            // A slice a times the B slices b = 0 .. 3 - a, stacked in N (the B planes
+            // are contiguous), lands in the class columns (a + b) N: five MMAs per
+            // K step cover the ten slice products
+            constexpr uint32_t id1 = idesc_bf16(ZT_BM, N), id2 = idesc_bf16(ZT_BM, 2 * N), id3 = idesc_bf16(ZT_BM, 3 * N);
+            static_assert(3 * N <= 256 && (N % 16) == 0, "stacked B planes exceed the MMA width");
             bool ok = true;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
                 const ZTile tm0 = p.tiles[t];
@@ -305,15 +304,20 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                         const uint32_t a0 = saddr(st), b0 = saddr(st + NPL * ZT_A_PLANE);
                         const bool first = c == g0;
 #pragma unroll
-                        for (int tm = 0; tm < NTERM; ++tm) {
-                            const uint64_t da = desc_sw128(a0 + term_a(tm) * ZT_A_PLANE);
-                            const bool lead = tm == 0 || tm == 1 || tm == 3 || tm == 6;
-#pragma unroll
-                            for (int ks = 0; ks < 4; ++ks) {
-                                // K step ks: segments 2 ks and 2 ks + 1 (plane term_b of each)
-                                const uint64_t db = desc_ns(b0 + 2 * ks * SEG4 + term_b(tm) * SEGB, SEG4, 128);
-                                umma_bf16(tmem + term_w(tm) * N, da + 2 * ks, db, idesc, (first && lead && ks == 0) ? 0u : 1u);
-                            }
+                        for (int ks = 0; ks < 4; ++ks) {
+                            // K step ks: segments 2 ks and 2 ks + 1 (B planes from plane b on)
+                            const uint64_t d0 = desc_sw128(a0) + 2 * ks;
+                            const uint64_t d1 = desc_sw128(a0 + ZT_A_PLANE) + 2 * ks;
+                            const uint64_t d2 = desc_sw128(a0 + 2 * ZT_A_PLANE) + 2 * ks;
+                            const uint64_t d3 = desc_sw128(a0 + 3 * ZT_A_PLANE) + 2 * ks;
+                            const uint64_t e0 = desc_ns(b0 + 2 * ks * SEG4, SEG4, 128);
+                            const uint64_t e2 = desc_ns(b0 + 2 * ks * SEG4 + 2 * SEGB, SEG4, 128);
+                            const uint32_t acc = (first && ks == 0) ? 0u : 1u;   // the two a = 0 MMAs set all classes
+                            umma_bf16(tmem, d0, e0, id2, acc);                 // classes 0, 1
+                            umma_bf16(tmem + 2 * N, d0, e2, id2, acc);         // classes 2, 3
+                            umma_bf16(tmem + N, d1, e0, id3, 1u);              // classes 1, 2, 3
+                            umma_bf16(tmem + 2 * N, d2, e0, id2, 1u);          // classes 2, 3
+                            umma_bf16(tmem + 3 * N, d3, e0, id1, 1u);          // class 3
                         }
                         umma_commit(&empty_bar[s]);
                         if (++s == ZT_STAGES) { s = 0; ph ^= 1; }
