@@ -53,11 +53,6 @@ struct CgParams {
     int *err;
 };
 
-// slice-product term t: weight class w, slice of A, slice of B (a + b = w)
-__device__ __forceinline__ constexpr int term_w(int t) { return t < 1 ? 0 : t < 3 ? 1 : t < 6 ? 2 : 3; }
-__device__ __forceinline__ constexpr int term_a(int t) { return t - term_w(t) * (term_w(t) + 1) / 2; }
-__device__ __forceinline__ constexpr int term_b(int t) { return term_w(t) - term_a(t); }
-
 // d * 2^k by exponent arithmetic (d normal or zero, result normal)
 __device__ __forceinline__ double scale2(double d, int k) {
     long long b = __double_as_longlong(d);
@@ -128,7 +123,11 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
             uint32_t ph = 0;
             int buf = 0;
             uint32_t buf_ph[2] = {0, 0};
-            constexpr uint32_t idesc = idesc_bf16(CG_BM, CG_BN);
+            // A slice a times the B slices b = 0 .. 3 - a stacked in N (the B planes
+            // are contiguous) lands in the class columns (a + b) CG_BN: four MMAs
+            // per K step cover the ten slice products
+            constexpr uint32_t id1 = idesc_bf16(CG_BM, CG_BN), id2 = idesc_bf16(CG_BM, 2 * CG_BN);
+            constexpr uint32_t id3 = idesc_bf16(CG_BM, 3 * CG_BN), id4 = idesc_bf16(CG_BM, 4 * CG_BN);
             bool ok = true;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
                 const int nchunk = p.tiles[t].nchunk;
@@ -143,15 +142,13 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
                         uint32_t a0 = saddr(st), b0 = saddr(st + NPL * CG_A_PLANE);
                         const bool first = kc == g0;
 #pragma unroll
-                        for (int tm = 0; tm < NTERM; ++tm) {
-                            uint64_t da = desc_sw128(a0 + term_a(tm) * CG_A_PLANE);
-                            uint64_t db = desc_sw128(b0 + term_b(tm) * CG_B_PLANE);
-                            // the first term of each class in a group overwrites the accumulator
-                            const bool lead = tm == 0 || tm == 1 || tm == 3 || tm == 6;
-#pragma unroll
-                            for (int ks = 0; ks < CG_KC / 16; ++ks)
-                                umma_bf16(dt + term_w(tm) * CG_BN, da + 2 * ks, db + 2 * ks, idesc,
-                                          (first && lead && ks == 0) ? 0u : 1u);
+                        for (int ks = 0; ks < CG_KC / 16; ++ks) {
+                            const uint64_t e0 = desc_sw128(b0) + 2 * ks;
+                            // the a = 0 MMA of a group's first K step overwrites every class
+                            umma_bf16(dt, desc_sw128(a0) + 2 * ks, e0, id4, (first && ks == 0) ? 0u : 1u);
+                            umma_bf16(dt + CG_BN, desc_sw128(a0 + CG_A_PLANE) + 2 * ks, e0, id3, 1u);
+                            umma_bf16(dt + 2 * CG_BN, desc_sw128(a0 + 2 * CG_A_PLANE) + 2 * ks, e0, id2, 1u);
+                            umma_bf16(dt + 3 * CG_BN, desc_sw128(a0 + 3 * CG_A_PLANE) + 2 * ks, e0, id1, 1u);
                         }
                         umma_commit(&empty_bar[s]);
                         if (++s == CG_STAGES) { s = 0; ph ^= 1; }

@@ -37,11 +37,6 @@ using namespace tc;
 
 namespace {
 
-// ------------------------------------------------------------- slice terms
-__device__ __constant__ int kSA[NTERM] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-__device__ __constant__ int kSB[NTERM] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
-__device__ __constant__ int kSW[NTERM] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
-
 // ------------------------------------------------------------- column slicing
 // For every column of the batch: exponent over its rows (real and imaginary
 // parts of rows [0, N0) and [N0, N0 + D_q) of Zc), then slices into
@@ -241,7 +236,10 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
         } else if (warp == 1 && lane == 0) {
             int s = 0;
             uint32_t ph = 0, eph = 0;
-            constexpr uint32_t idesc = idesc_bf16(G1_BM, G1_BN);
+            // A slice a times B slices stacked in N (the B planes are contiguous)
+            // lands in the class columns (a + b) G1_BN: six MMAs per K step cover
+            // the ten slice products
+            constexpr uint32_t id1 = idesc_bf16(G1_BM, G1_BN), id2 = idesc_bf16(G1_BM, 2 * G1_BN);
             bool ok = true;
             for (int g = cid; g < p.ngroups && ok; g += ncl) {
                 G1Tile tl = p.tiles[g * CS + rank];
@@ -256,14 +254,18 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                         const uint32_t a0 = saddr(st), b0 = saddr(st + NPL * G1_A_PLANE);
                         const bool first = kc == g0;
 #pragma unroll
-                        for (int tm = 0; tm < NTERM; ++tm) {
-                            const uint64_t da = desc_sw64(a0 + slice_term_a(tm) * G1_A_PLANE);
-                            const uint64_t db = desc_sw64(b0 + slice_term_b(tm) * G1_B_PLANE);
-                            const bool lead = tm == 0 || tm == 1 || tm == 3 || tm == 6;
-#pragma unroll
-                            for (int ks = 0; ks < G1_KC / 16; ++ks)
-                                umma_bf16(tmem + slice_term_w(tm) * G1_BN, da + 2 * ks, db + 2 * ks, idesc,
-                                          (first && lead && ks == 0) ? 0u : 1u);
+                        for (int ks = 0; ks < G1_KC / 16; ++ks) {
+                            const uint64_t d0 = desc_sw64(a0) + 2 * ks, d1 = desc_sw64(a0 + G1_A_PLANE) + 2 * ks;
+                            const uint64_t d2 = desc_sw64(a0 + 2 * G1_A_PLANE) + 2 * ks;
+                            const uint64_t d3 = desc_sw64(a0 + 3 * G1_A_PLANE) + 2 * ks;
+                            const uint64_t e0 = desc_sw64(b0) + 2 * ks, e2 = desc_sw64(b0 + 2 * G1_B_PLANE) + 2 * ks;
+                            const uint32_t acc = (first && ks == 0) ? 0u : 1u;   // the two a = 0 MMAs set all classes
+                            umma_bf16(tmem, d0, e0, id2, acc);                    // classes 0, 1
+                            umma_bf16(tmem + 2 * G1_BN, d0, e2, id2, acc);        // classes 2, 3
+                            umma_bf16(tmem + G1_BN, d1, e0, id2, 1u);             // classes 1, 2
+                            umma_bf16(tmem + 3 * G1_BN, d1, e2, id1, 1u);         // class 3
+                            umma_bf16(tmem + 2 * G1_BN, d2, e0, id2, 1u);         // classes 2, 3
+                            umma_bf16(tmem + 3 * G1_BN, d3, e0, id1, 1u);         // class 3
                         }
                         if (CS == 1) umma_commit(&empty_bar[s]);
                         else umma_commit_mc(&empty_bar[s], kMask);
@@ -446,7 +448,12 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
             int s = 0;
             uint32_t ph = 0;
             uint32_t tph = 0;
-            constexpr uint32_t idesc = idesc_bf16(128, W);
+            // A slice a times B slices stacked in N (the B planes are contiguous)
+            // lands in the class columns (a + b) W: five (3 W <= 256) or six MMAs
+            // per K step cover the ten slice products
+            constexpr uint32_t id1 = idesc_bf16(128, W), id2 = idesc_bf16(128, 2 * W);
+            constexpr bool three = 3 * W <= 256;
+            constexpr uint32_t id3 = idesc_bf16(128, three ? 3 * W : W);
             bool ok = true;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
                 G2Tile tl = p.tiles[t];
@@ -457,21 +464,28 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                     for (int g0 = 0; g0 < nc && ok; g0 += G2_GROUP) {
                         if (!mbar_wait(&tempty_bar, tph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                         tc_fence_after();
-                        int started = 0;
                         for (int c = g0; c < min(nc, g0 + G2_GROUP); ++c) {
                             if (!mbar_wait(&full_bar[s], ph, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                             tc_fence_after();
                             unsigned char *st = stages + (size_t)s * SB;
                             uint32_t a0 = saddr(st), b0 = saddr(st + NPL * G2_A_PLANE);
-                            for (int tm = 0; tm < NTERM; ++tm) {
-                                int w = kSW[tm];
-                                uint64_t da = desc_sw128(a0 + kSA[tm] * G2_A_PLANE);
-                                uint64_t db = desc_sw128(b0 + kSB[tm] * B_PLANE);
 #pragma unroll
-                                for (int ks = 0; ks < 4; ++ks) {
-                                    umma_bf16(tmem + w * W, da + 2 * ks, db + 2 * ks, idesc, ((started >> w) & 1) ? 1u : 0u);
-                                    started |= 1 << w;
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t d0 = desc_sw128(a0) + 2 * ks, d1 = desc_sw128(a0 + G2_A_PLANE) + 2 * ks;
+                                const uint64_t d2 = desc_sw128(a0 + 2 * G2_A_PLANE) + 2 * ks;
+                                const uint64_t d3 = desc_sw128(a0 + 3 * G2_A_PLANE) + 2 * ks;
+                                const uint64_t e0 = desc_sw128(b0) + 2 * ks, e2 = desc_sw128(b0 + 2 * B_PLANE) + 2 * ks;
+                                const uint32_t acc = (c == g0 && ks == 0) ? 0u : 1u;   // the two a = 0 MMAs set all classes
+                                umma_bf16(tmem, d0, e0, id2, acc);                  // classes 0, 1
+                                umma_bf16(tmem + 2 * W, d0, e2, id2, acc);          // classes 2, 3
+                                if (three) {
+                                    umma_bf16(tmem + W, d1, e0, id3, 1u);           // classes 1, 2, 3
+                                } else {
+                                    umma_bf16(tmem + W, d1, e0, id2, 1u);           // classes 1, 2
+                                    umma_bf16(tmem + 3 * W, d1, e2, id1, 1u);       // class 3
                                 }
+                                umma_bf16(tmem + 2 * W, d2, e0, id2, 1u);           // classes 2, 3
+                                umma_bf16(tmem + 3 * W, d3, e0, id1, 1u);           // class 3
                             }
                             umma_commit(&empty_bar[s]);
                             if (++s == NS) { s = 0; ph ^= 1; }

@@ -186,10 +186,11 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t addr) {
     return d;
 }
 
-// slice-product term t of the ten kept (i + j <= 3): weight class, slice of A, slice of B
-__device__ __forceinline__ constexpr int slice_term_w(int t) { return t < 1 ? 0 : t < 3 ? 1 : t < 6 ? 2 : 3; }
-__device__ __forceinline__ constexpr int slice_term_a(int t) { return t - slice_term_w(t) * (slice_term_w(t) + 1) / 2; }
-__device__ __forceinline__ constexpr int slice_term_b(int t) { return slice_term_w(t) - slice_term_a(t); }
+// The ten kept slice products s_a t_b (a + b <= 3) fall in four weight classes
+// w = a + b, one TMEM accumulator of N columns each, class w at columns w N.
+// The slice planes of B sit back to back in shared memory, so the products of
+// one A slice a with B slices b, b + 1, ... form one MMA of width (count) N
+// whose output starts at column (a + b) N.
 
 // Instruction descriptor: BF16 x BF16 -> FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
