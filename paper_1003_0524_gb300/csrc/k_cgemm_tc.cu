@@ -53,13 +53,6 @@ struct CgParams {
     int *err;
 };
 
-// d * 2^k by exponent arithmetic (d normal or zero, result normal)
-__device__ __forceinline__ double scale2(double d, int k) {
-    long long b = __double_as_longlong(d);
-    if ((b << 1) == 0) return d;
-    return __longlong_as_double(b + ((long long)k << 52));
-}
-
 // warp 0: TMA producer; warp 1: MMA issuer; warps 2..9: epilogue
 // (TMEM lane quarter = warp % 4, column half = (warp - 2) / 4)
 __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -207,8 +200,8 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
                     const long long co = co_tab[c >> 1];
                     if (co >= 0) {
                         const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
-                        double re = scale2((double)h.x + (double)l.x, ea + p.bexp[c]);
-                        double im = scale2((double)h.y + (double)l.y, ea + p.bexp[c + 1]);
+                        double re = f32pair_to_f64(h.x, l.x, ea + p.bexp[c]);
+                        double im = f32pair_to_f64(h.y, l.y, ea + p.bexp[c + 1]);
                         if (p.phase) {
                             const double2 f = p.phase[tl.phb + p.pkey[c >> 1]];
                             const double x = re * f.x - im * f.y;

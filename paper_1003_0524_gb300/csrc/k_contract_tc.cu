@@ -552,8 +552,8 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
 #pragma unroll
                 for (int j = 0; j < CW; j += 2) {
                     const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
-                    out[j] = (double)h.x + (double)l.x;
-                    out[j + 1] = (double)h.y + (double)l.y;
+                    out[j] = f32pair_to_f64(h.x, l.x, 0);
+                    out[j + 1] = f32pair_to_f64(h.y, l.y, 0);
                 }
             }
         }

@@ -43,14 +43,9 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__device__ __forceinline__ double scale2(double d, int k) {
-    long long b = __double_as_longlong(d);
-    if ((b << 1) == 0) return d;
-    return __longlong_as_double(b + ((long long)k << 52));
-}
-
 // ------------------------------------------------------------- C slices
-// One block per row r = (k', m): exponent over |Re c|, |Im c| of the row, then
+// One block per row r = (k', m) of c scaled by Omega^{-1/2}: exponent over
+// |Re c|, |Im c| of the row, then
 // Re C = c_r at K = 8 s + j and Im C = -c_i at K = 8 s + 4 + j, where segment
 // s = segstart + (z - z0) / 4 and j = (z - z0) mod 4 on the segment grid of the
 // row's tile.
@@ -58,7 +53,7 @@ __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int
                                 const int *__restrict__ npw_k, const int *__restrict__ rowk, const int *__restrict__ rowm,
                                 const int *__restrict__ line_of, int gx0, int gy0, int By, int nL,
                                 const int *__restrict__ segstart, const int *__restrict__ segz0, int Kp, int Rpad,
-                                __nv_bfloat16 *__restrict__ A, int *__restrict__ aexp) {
+                                double rs, __nv_bfloat16 *__restrict__ A, int *__restrict__ aexp) {
     int r = blockIdx.x;
     int kp = rowk[r], m = rowm[r];
     int npw = npw_k[kp];
@@ -66,7 +61,7 @@ __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int
     const int *G = Gk[kp];
     __shared__ unsigned long long red[256];
     unsigned long long mx = 0;
-    for (int i = threadIdx.x; i < npw; i += blockDim.x) mx = max(mx, max(abs_bits(c[i].x), abs_bits(c[i].y)));
+    for (int i = threadIdx.x; i < npw; i += blockDim.x) mx = max(mx, max(abs_bits(rs * c[i].x), abs_bits(rs * c[i].y)));
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
@@ -80,8 +75,8 @@ __global__ void c_slices_kernel(const double2 *const *__restrict__ ck, const int
         int li = line_of[(G[3 * i] - gx0) * By + (G[3 * i + 1] - gy0)];
         int z = G[3 * i + 2];
         __nv_bfloat16 sr[NPL], si[NPL];
-        slice4(c[i].x, e, sr);
-        slice4(-c[i].y, e, si);
+        slice4(rs * c[i].x, e, sr);
+        slice4(-(rs * c[i].y), e, si);
         const size_t sl = (size_t)(r / ZT_BM) * nL + li;   // segment grid of the row's tile
         const int dz = z - segz0[sl];
         const long long K = (long long)(segstart[sl] + dz / ZT_SEGZ) * 8 + dz % ZT_SEGZ;
@@ -192,6 +187,7 @@ struct ZParams {
     const int2 *segoff;           // [row tile][segment] (x td1 + y of its line, z0)
     int nsegp_max;
     const int *nchunk;            // [row tile] 64-K chunks
+    const int *runs;              // [row tile][chunk] bit j: segment j of the chunk starts a bulk copy; bits 8..: live segments
     const __nv_bfloat16 *Tq;      // sliced T blocks (t_slices_kernel layout)
     int td0, td1, nzb, nblk, nslot;
     double2 *Z;
@@ -216,6 +212,12 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    // B segments of every stage start as zeros: padding segments are never loaded
+    for (int s = 0; s < ZT_STAGES; ++s) {
+        uint4 *bz = reinterpret_cast<uint4 *>(stages + (size_t)s * STAGE + NPL * ZT_A_PLANE);
+        for (int i = threadIdx.x; i < 8 * SEG4 / 16; i += blockDim.x) bz[i] = make_uint4(0, 0, 0, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
         for (int s = 0; s < ZT_STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
@@ -234,11 +236,13 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
 
     if (warp == 0) {
         // producer warp: lane 0 waits for the stage and arms its barrier, then
-        // lanes 0..3 load the four A planes and lanes 0..7 the eight B segments
+        // lanes 0..3 load the four A planes and the lanes of the segments that
+        // start a run (consecutive z blocks of one line, contiguous in T) one
+        // bulk copy each; padding segments are not loaded (their A is zero and
+        // their shared memory holds finite data of earlier chunks or zeros)
         int s = 0;
         uint32_t ph = 0;
         int issued = 0;
-        const int bj = lane & 7;
         const char *tq = reinterpret_cast<const char *>(p.Tq);
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
             const ZTile tl = p.tiles[t];
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             const int gt = tl.mrow / ZT_BM, nch = p.nchunk[gt];
             const int slot = p.kslot[tl.k];
             const int2 *so = p.segoff + (size_t)gt * p.nsegp_max;
+            const int *runs = p.runs + (size_t)gt * (p.nsegp_max / 8);
             // a segment starts at X = W_x + x - tlo_x, Y likewise, and T z index
             // Zs = W_z - tlo_z + z0: copy Zs mod 4, z block Zs / 4 -- inside the
             // box by construction
@@ -253,24 +258,27 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             const int bz = W.z - p.tlo2;
             bool stop = false;
             for (int c = 0; c < nch; ++c) {
+                const int ri = runs[c], live = ri >> 8, starts = ri & 0xff;
                 int ok = 1;
                 if (lane == 0) {
                     ok = mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma) ? 1 : 0;
-                    if (ok) mbar_expect_tx(&full_bar[s], STAGE);
+                    if (ok) mbar_expect_tx(&full_bar[s], NPL * ZT_A_PLANE + live * SEG4);
                 }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { stop = true; break; }
                 unsigned char *st = stages + (size_t)s * STAGE;
                 if (lane < NPL)
                     tma_load_2d(saddr(st + lane * ZT_A_PLANE), &tmA, &full_bar[s], c * 64, lane * p.Rpad + tl.mrow);
-                if (lane < 8) {
-                    const int2 sg = so[c * 8 + bj];
+                if (lane < live && ((starts >> lane) & 1)) {
+                    const int rest = starts >> (lane + 1);
+                    const int len = rest ? __ffs(rest) : live - lane;   // segments up to the next run
+                    const int2 sg = so[c * 8 + lane];
                     const int Zs = bz + sg.y;
                     const int cp = Zs & (ZT_NCOPY - 1);
                     const long long cell =
                         (((long long)cp * p.nslot + slot) * ((long long)p.td0 * p.td1) + bxy + sg.x) * p.nzb + Zs / ZT_SEGZ;
-                    bulk_load(saddr(st + NPL * ZT_A_PLANE + bj * SEG4), tq + (cell * p.nblk + tl.nblk) * SEG4, SEG4,
-                              &full_bar[s]);
+                    bulk_load(saddr(st + NPL * ZT_A_PLANE + lane * SEG4), tq + (cell * p.nblk + tl.nblk) * SEG4,
+                              (uint32_t)(len * SEG4), &full_bar[s]);
                 }
                 ++issued;
                 if (++s == ZT_STAGES) { s = 0; ph ^= 1; }
@@ -340,6 +348,32 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             const ZTile tl = p.tiles[t];
             const int4 W = p.wxyz[tl.w];
             const int ngroups = (p.nchunk[tl.mrow / ZT_BM] + ZT_GROUP - 1) / ZT_GROUP;
+            // everything the output of this row needs, fetched now so that the
+            // dependent loads overlap the first K group instead of following it:
+            // the output row g, the first column and the live bands, the scales
+            int g = -1, nlive = 0;
+            long long col = 0;
+            int ex[NH];
+            {
+                const int r = tl.mrow + quarter * 32 + lane;
+                if (r < p.R) {
+                    const int kp = p.rowk[r], m = p.rowm[r];
+                    const ZPairInfo pi = p.pinfo[(size_t)tl.k * p.nk + kp];
+                    if (pi.pair >= 0) {
+                        const PairDesc pr = p.pairs[pi.pair];
+                        const int Gx = W.x + pi.g0x - p.ax0, Gy = W.y + pi.g0y - p.ay0, Gz = W.z + pi.g0z - p.az0;
+                        if (Gx >= 0 && Gx < p.ad0 && Gy >= 0 && Gy < p.ad1 && Gz >= 0 && Gz < p.ad2)
+                            g = p.gtab[(((size_t)pr.qslot * p.ad0 + Gx) * p.ad1 + Gy) * p.ad2 + Gz];
+                        const int n0 = tl.nblk * NB + cs * NH;
+                        nlive = min(NH, pr.nb - n0);
+                        col = pr.col0 + (long long)m * pr.nb + n0;
+                        const int ea = p.aexp[r] - 16;
+                        const int *eTk = p.eT + (size_t)tl.k * p.nbmax;
+#pragma unroll
+                        for (int jj = 0; jj < NH; ++jj) ex[jj] = jj < nlive ? ea + eTk[n0 + jj] : 0;
+                    }
+                }
+            }
             uint64_t hr[NH / 2], lr[NH / 2], hm[NH / 2], lm[NH / 2];   // packed pairs of columns
 #pragma unroll
             for (int j = 0; j < NH / 2; ++j) { hr[j] = 0; lr[j] = 0; hm[j] = 0; lm[j] = 0; }
@@ -375,34 +409,18 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                 eph ^= 1;
             }
             if (!ok) break;
-            const int r = tl.mrow + quarter * 32 + lane;
-            if (r < p.R) {
-                const int kp = p.rowk[r], m = p.rowm[r];
-                const ZPairInfo pi = p.pinfo[(size_t)tl.k * p.nk + kp];
-                if (pi.pair >= 0) {
-                    const PairDesc pr = p.pairs[pi.pair];
-                    const int Gx = W.x + pi.g0x - p.ax0, Gy = W.y + pi.g0y - p.ay0, Gz = W.z + pi.g0z - p.az0;
-                    int g = -1;
-                    if (Gx >= 0 && Gx < p.ad0 && Gy >= 0 && Gy < p.ad1 && Gz >= 0 && Gz < p.ad2)
-                        g = p.gtab[(((size_t)pr.qslot * p.ad0 + Gx) * p.ad1 + Gy) * p.ad2 + Gz];
-                    if (g >= 0) {
-                        const int ea = p.aexp[r] - 16;
-                        const int *eTk = p.eT + (size_t)tl.k * p.nbmax;
+            if (g >= 0) {
+                double2 *out = p.Z + col * p.RSc + p.nmt + g;
 #pragma unroll
-                        for (int jj = 0; jj < NH; ++jj) {
-                            const int n = tl.nblk * NB + cs * NH + jj;
-                            if (n < pr.nb) {
-                                const int ex = ea + eTk[n];
-                                const float2 h1 = f2_unpack(hr[jj / 2]), l1 = f2_unpack(lr[jj / 2]);
-                                const float2 h2 = f2_unpack(hm[jj / 2]), l2 = f2_unpack(lm[jj / 2]);
-                                const bool odd = jj & 1;
-                                double2 v;
-                                v.x = scale2((double)(odd ? h1.y : h1.x) + (double)(odd ? l1.y : l1.x), ex) * p.rs;
-                                v.y = scale2((double)(odd ? h2.y : h2.x) + (double)(odd ? l2.y : l2.x), ex) * p.rs;
-                                long long col = pr.col0 + (long long)m * pr.nb + n;
-                                __stcs(p.Z + col * p.RSc + p.nmt + g, v);   // streaming: keep the operands in L2
-                            }
-                        }
+                for (int jj = 0; jj < NH; ++jj) {
+                    if (jj < nlive) {
+                        const float2 h1 = f2_unpack(hr[jj / 2]), l1 = f2_unpack(lr[jj / 2]);
+                        const float2 h2 = f2_unpack(hm[jj / 2]), l2 = f2_unpack(lm[jj / 2]);
+                        const bool odd = jj & 1;
+                        double2 v;   // Omega^{-1/2} is in the C slices
+                        v.x = f32pair_to_f64(odd ? h1.y : h1.x, odd ? l1.y : l1.x, ex[jj]);
+                        v.y = f32pair_to_f64(odd ? h2.y : h2.x, odd ? l2.y : l2.x, ex[jj]);
+                        __stcs(out + jj * p.RSc, v);   // streaming: keep the operands in L2
                     }
                 }
             }
@@ -573,6 +591,21 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         }
         const int NBt = pick_nb(in.nb_max);
         const int nblk = (in.nb_max + NBt - 1) / NBt;
+        // bulk-copy runs per 64-K chunk: consecutive segments of one line are
+        // consecutive z blocks of T, contiguous for a single band block
+        std::vector<int> runs((size_t)nmtile * (nsegp_max / 8), 0);
+        for (int t = 0; t < nmtile; ++t)
+            for (int c = 0; c < nsegp_max / 8; ++c) {
+                const int live = std::max(0, std::min(8, nseg[t] - 8 * c));
+                int starts = 0;
+                for (int j = 0; j < live; ++j) {
+                    const int s2 = 8 * c + j;
+                    const bool cont = j > 0 && nblk == 1 && segs[t][s2].x == segs[t][s2 - 1].x &&
+                                      segs[t][s2].y == segs[t][s2 - 1].y && segs[t][s2].z == segs[t][s2 - 1].z + ZT_SEGZ;
+                    if (!cont) starts |= 1 << j;
+                }
+                runs[(size_t)t * (nsegp_max / 8) + c] = starts | (live << 8);
+            }
         // ---- aux lookup tables over the batch's q
         int amin[3] = {1 << 29, 1 << 29, 1 << 29}, amax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
         for (int iq : in.qs)
@@ -663,7 +696,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                      o_seg = place(segtab.size() * sizeof(int2)), o_gtab = place(gtab.size() * 4),
                      o_pinfo = place(pinfo.size() * sizeof(ZPairInfo)), o_w = place(wxyz.size() * sizeof(int4)),
                      o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4),
-                     o_nch = place(nchunk.size() * 4);
+                     o_nch = place(nchunk.size() * 4), o_runs = place(runs.size() * 4);
         if ((rc = scratch_reserve(ctx, ctx->s_zipw, off))) return rc;
         char *b = reinterpret_cast<char *>(ctx->s_zipw.p);
         auto up = [&](size_t o, const void *src, size_t bytes) {
@@ -676,7 +709,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
             (rc = up(o_pinfo, pinfo.data(), pinfo.size() * sizeof(ZPairInfo))) ||
             (rc = up(o_w, wxyz.data(), wxyz.size() * sizeof(int4))) ||
             (rc = up(o_tiles, tiles.data(), tiles.size() * sizeof(ZTile))) || (rc = up(o_kslot, kslot.data(), nk * 4)) ||
-            (rc = up(o_nch, nchunk.data(), nchunk.size() * 4)))
+            (rc = up(o_nch, nchunk.data(), nchunk.size() * 4)) || (rc = up(o_runs, runs.data(), runs.size() * 4)))
             return rc;
         ZParams &p = plan->p;
         p.tiles = reinterpret_cast<ZTile *>(b + o_tiles);
@@ -701,6 +734,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         p.nblk = nblk;
         p.nslot = nslot;
         p.nchunk = reinterpret_cast<int *>(b + o_nch);
+        p.runs = reinterpret_cast<int *>(b + o_runs);
         p.Z = in.d_Z;
         p.RSc = in.RSc;
         p.nmt = ctx->nmt;
@@ -731,7 +765,7 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
                                          reinterpret_cast<int *>(b + P.o_rowm), reinterpret_cast<int *>(b + P.o_line), P.gx0,
                                          P.gy0, P.By, P.nL, reinterpret_cast<int *>(b + P.o_sst),
                                          reinterpret_cast<int *>(b + P.o_sz0),
-                                         P.Kp, P.Rpad, A, aexp);
+                                         P.Kp, P.Rpad, P.p.rs, A, aexp);
     t_exp_kernel<<<dim3(in.nb_max, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], in.nb_max,
                                                       reinterpret_cast<int *>(b + P.o_kslot), eT);
     {

@@ -346,6 +346,40 @@ __device__ __forceinline__ void class_accumulate2_sc(uint64_t a0, uint64_t a1, u
     lo = f2_add(lo, f2_fma(c, f2_mul(s8, sc), er));
 }
 
+// (h + l) * 2^k as a double for FP32 h, l, by integer operations only: the
+// epilogues convert one value per output, and GB300's FP64 pipe (about two
+// operations per clock per SM) would otherwise stall them.  Both terms are
+// put on a common 62-bit fixed point 38 bits below the larger exponent, added,
+// and rounded to 53 bits, to nearest even: the correctly rounded sum when the
+// exponents of h and l are within 38 of each other; a smaller term further
+// below is truncated there (at most one unit in the last place).  The result
+// must be a normal double or zero (results below the normal range give 0).
+__device__ __forceinline__ double f32pair_to_f64(float h, float l, int k) {
+    const uint32_t bh = __float_as_uint(h), bl = __float_as_uint(l);
+    const int beh = (bh >> 23) & 0xff, bel = (bl >> 23) & 0xff;
+    long long mh = (long long)((bh & 0x7fffffu) | (beh ? 0x800000u : 0u));
+    long long ml = (long long)((bl & 0x7fffffu) | (bel ? 0x800000u : 0u));
+    if (bh >> 31) mh = -mh;
+    if (bl >> 31) ml = -ml;
+    const int eh = (beh ? beh : 1) - 150, el = (bel ? bel : 1) - 150;   // value = m * 2^e
+    const int emax = mh ? (ml ? max(eh, el) : eh) : el;
+    const int e0 = emax - 38;
+    const int dh = eh - e0, dl = el - e0;                                // the larger term: shift 38
+    const long long S = (dh >= 0 ? mh << dh : (dh > -63 ? mh >> -dh : (mh < 0 ? -1 : 0))) +
+                        (dl >= 0 ? ml << dl : (dl > -63 ? ml >> -dl : (ml < 0 ? -1 : 0)));
+    if (S == 0) return 0.0;
+    const unsigned long long sgn = S < 0 ? (1ULL << 63) : 0ULL;
+    unsigned long long a = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+    const int lz = __clzll(a);
+    a <<= lz;                                                           // bit 63 set
+    unsigned long long m = a >> 11;                                     // 53 bits
+    const unsigned long long rem = a & 0x7ffULL;
+    if (rem > 0x400ULL || (rem == 0x400ULL && (m & 1ULL))) ++m;         // may carry to 2^53: exponent + 1 below
+    const long long bexp = (long long)(e0 + k - lz) + 63 + 1023;        // biased exponent of the leading bit
+    if (bexp < 1) return 0.0;
+    return __longlong_as_double((long long)(sgn | (((unsigned long long)(bexp - 1) << 52) + m)));
+}
+
 int make_map_2d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows);
 int make_map_2d_sw(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows,
                    int box_cols, int swizzle_bytes);
