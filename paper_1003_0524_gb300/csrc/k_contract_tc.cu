@@ -122,13 +122,6 @@ __global__ void block_y_kernel(const QDesc *__restrict__ qd, const double2 *cons
     }
 }
 
-// d * 2^k by exponent arithmetic (d normal or zero, result normal)
-__device__ __forceinline__ double scale2(double d, int k) {
-    long long b = __double_as_longlong(d);
-    if ((b << 1) == 0) return d;
-    return __longlong_as_double(b + ((long long)k << 52));
-}
-
 // ------------------------------------------------------------- GEMM1
 // Tile: 128 rows of A' (one q) x 128 columns of Z; K chunks of 32 (one
 // 64-byte swizzled row per operand row), the four slices of both operands per
@@ -287,6 +280,14 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
             const QDesc q = p.qd[tl.qslot];
             int nchunk = 2 * (tl.klen / G1_KC);
             int ngroups = (nchunk + G1_GROUP - 1) / G1_GROUP;
+            // output scales: the row exponent, and the exponents of the 64 columns of
+            // this half, fetched together before the stores (lane l holds columns
+            // l and 32 + l; the store loop shuffles them)
+            const int r = tl.mrow + quarter * 32 + lane;     // row of A' in this q: [0, D) real, [D, 2D) imaginary
+            const bool im = r >= q.D;
+            const int rr = im ? r - q.D : r;
+            const bool live = rr < q.D && tl.out;
+            const long long c0 = tl.ncol0 + half * 64, cend = q.colbase + q.ncols;
             uint64_t hi[32], lo[32];   // packed pairs of columns
 #pragma unroll
             for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
@@ -315,20 +316,18 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                 eph ^= 1;
             }
             if (!ok) break;
-            int r = tl.mrow + quarter * 32 + lane;           // row of A' in this q: [0, D) real, [D, 2D) imaginary
-            bool im = r >= q.D;
-            int rr = im ? r - q.D : r;
-            if (rr < q.D && tl.out) {
-                const int ea = p.aexp[(size_t)q.iq * p.MP + r] - 16;
-                const long long c0 = tl.ncol0 + half * 64, cend = q.colbase + q.ncols;
-                double *dst = reinterpret_cast<double *>(p.Y + c0 * p.RSc + p.N0 + rr) + (im ? 1 : 0);
-                const long long cstride = 2 * p.RSc;
+            const int ea = live ? p.aexp[(size_t)q.iq * p.MP + r] - 16 : 0;
+            const int zx0 = c0 + lane < cend ? p.zexp[c0 + lane] : 0;
+            const int zx1 = c0 + 32 + lane < cend ? p.zexp[c0 + 32 + lane] : 0;
+            double *dst = reinterpret_cast<double *>(p.Y + c0 * p.RSc + p.N0 + (live ? rr : 0)) + (im ? 1 : 0);
+            const long long cstride = 2 * p.RSc;
 #pragma unroll
-                for (int j = 0; j < 64; j += 2) {
-                    const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
-                    if (c0 + j < cend) dst[j * cstride] = scale2((double)h.x + (double)l.x, ea + p.zexp[c0 + j]);
-                    if (c0 + j + 1 < cend) dst[(j + 1) * cstride] = scale2((double)h.y + (double)l.y, ea + p.zexp[c0 + j + 1]);
-                }
+            for (int j = 0; j < 64; j += 2) {
+                const int e0 = __shfl_sync(0xffffffffu, j < 32 ? zx0 : zx1, j & 31);
+                const int e1 = __shfl_sync(0xffffffffu, j + 1 < 32 ? zx0 : zx1, (j + 1) & 31);
+                const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
+                if (live && c0 + j < cend) dst[j * cstride] = f32pair_to_f64(h.x, l.x, ea + e0);
+                if (live && c0 + j + 1 < cend) dst[(j + 1) * cstride] = f32pair_to_f64(h.y, l.y, ea + e1);
             }
         }
     }
@@ -515,6 +514,10 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                 long long cola = pr.col0 + (long long)m * pr.nb + tl.bi * NB + (row % NB);
                 long long colb0 = pr.col0 + (long long)m * pr.nb + tl.bj * NB;
                 int ea = p.zexp[min(cola, p.NC - 1)] - 16;
+                // exponents of the NB columns of Y, fetched once per m: lane l holds
+                // columns l and 32 + l (the drain loop shuffles them)
+                const int yx0 = p.yexp[min(colb0 + lane, p.NC - 1)];
+                const int yx1 = p.yexp[min(colb0 + 32 + lane, p.NC - 1)];
                 for (int g0 = 0; g0 < nc; g0 += G2_GROUP) {
                     if (!mbar_wait(&tfull_bar, tph, &abort_flag, p.err, kDevTimeoutEpi)) { ok = false; break; }
                     tc_fence_after();
@@ -529,9 +532,9 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                         tmem_wait_ld();
 #pragma unroll
                         for (int j = 0; j < 8; j += 2) {
-                            int b = cg * CW + c0 + j;
-                            float s0 = ldexpf(1.0f, ea + p.yexp[min(colb0 + (b % NB), p.NC - 1)]);
-                            float s1 = ldexpf(1.0f, ea + p.yexp[min(colb0 + ((b + 1) % NB), p.NC - 1)]);
+                            const int b = cg * CW + c0 + j, j0 = b % NB, j1 = (b + 1) % NB;
+                            const float s0 = ldexpf(1.0f, ea + __shfl_sync(0xffffffffu, j0 < 32 ? yx0 : yx1, j0 & 31));
+                            const float s1 = ldexpf(1.0f, ea + __shfl_sync(0xffffffffu, j1 < 32 ? yx0 : yx1, j1 & 31));
                             class_accumulate2_sc(f2_pack(a0[j], a0[j + 1]), f2_pack(a1[j], a1[j + 1]),
                                                  f2_pack(a2[j], a2[j + 1]), f2_pack(a3[j], a3[j + 1]),
                                                  f2_pack(__float_as_uint(s0), __float_as_uint(s1)), hi[(c0 + j) / 2],

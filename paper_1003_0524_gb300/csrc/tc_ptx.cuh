@@ -346,15 +346,31 @@ __device__ __forceinline__ void class_accumulate2_sc(uint64_t a0, uint64_t a1, u
     lo = f2_add(lo, f2_fma(c, f2_mul(s8, sc), er));
 }
 
-// (h + l) * 2^k as a double for FP32 h, l, by integer operations only: the
-// epilogues convert one value per output, and GB300's FP64 pipe (about two
-// operations per clock per SM) would otherwise stall them.  Both terms are
-// put on a common 62-bit fixed point 38 bits below the larger exponent, added,
-// and rounded to 53 bits, to nearest even: the correctly rounded sum when the
-// exponents of h and l are within 38 of each other; a smaller term further
-// below is truncated there (at most one unit in the last place).  The result
-// must be a normal double or zero (results below the normal range give 0).
+// x * 2^k as a double for a normal FP32 x (or zero), built from the bits of x
+// with 32-bit integer operations: no FP64 conversion.  FP32 subnormals give 0.
+// The scaled exponent must stay in the normal FP64 range.
+__device__ __forceinline__ double f32_to_f64_scaled(float x, int k) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xffu;
+    const uint32_t hi = e ? (b & 0x80000000u) | ((e + 896u + (uint32_t)k) << 20) | ((b & 0x7fffffu) >> 3) : 0u;
+    const uint32_t lo = e ? b << 29 : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// (h + l) * 2^k for FP32 h, l: the two exact scaled conversions and one FP64
+// add, the correctly rounded sum (exact when the exponents of h and l are
+// within 29).  One FP64 operation per output: GB300's FP64 pipe is narrow, and
+// the epilogues convert one value per output element.
 __device__ __forceinline__ double f32pair_to_f64(float h, float l, int k) {
+    return f32_to_f64_scaled(h, k) + f32_to_f64_scaled(l, k);
+}
+
+// The same value by integer operations only (no FP64 operation): both terms
+// on a common 62-bit fixed point 38 bits below the larger exponent, added, and
+// rounded to 53 bits, to nearest even.  Correctly rounded when the exponents
+// of h and l are within 38; a smaller term further below is truncated there
+// (at most one unit in the last place).  Results below the normal range give 0.
+__device__ __forceinline__ double f32pair_to_f64_int(float h, float l, int k) {
     const uint32_t bh = __float_as_uint(h), bl = __float_as_uint(l);
     const int beh = (bh >> 23) & 0xff, bel = (bl >> 23) & 0xff;
     long long mh = (long long)((bh & 0x7fffffu) | (beh ? 0x800000u : 0u));
