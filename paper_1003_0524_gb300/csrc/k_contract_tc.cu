@@ -27,6 +27,7 @@
 // error code, stops issuing work, lets its in-flight copies and MMAs drain
 // (again bounded), frees its TMEM and returns.
 #include <algorithm>
+#include <type_traits>
 #include <string>
 
 #include "tc_ptx.cuh"
@@ -119,6 +120,86 @@ __global__ void block_y_kernel(const QDesc *__restrict__ qd, const double2 *cons
             acc = cfma(row[s], make_double2((double)zs.x, (double)zs.y), acc);
         }
         Y[col * RSc + u] = acc;
+    }
+}
+
+// x = hi + lo to within 2^-47 |x|, hi and lo FP32, from the bits of x with
+// integer operations (no FP64 conversion): hi keeps the sign, the exponent and
+// the top 23 stored mantissa bits (truncated), lo the remaining 29 bits (the
+// integer conversion rounds them to 24).  For |x| < 2^-74 (and zero) lo = 0,
+// for |x| < 2^-126 hi = 0 as well; |x| must stay below 2^128.
+__device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+    const uint32_t sg = bh & 0x80000000u;
+    const int e = (int)((bh >> 20) & 0x7ffu);
+    const bool nh = e >= 897, nl = e >= 949;
+    hi = __uint_as_float(nh ? sg | ((uint32_t)(e - 896) << 23) | ((bh & 0xfffffu) << 3) | (bl >> 29) : sg);
+    const float r = __uint2float_rn(bl & 0x1fffffffu);                   // the 29 low bits, as an integer
+    lo = nl ? __uint_as_float(__float_as_uint(r * __uint_as_float((uint32_t)(e - 948) << 23)) | sg) : 0.0f;
+}
+
+// S + E += a * b for double-FP32 a = (ah, al), b = (bh, bl): the product's
+// rounding error from an FMA, the cross terms to first order, S updated by an
+// exact two-sum whose error joins E.  Relative error about 2^-46.
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float &S, float &E) {
+    const float p = ah * bh;
+    const float pe = fmaf(ah, bh, -p);
+    const float cross = fmaf(ah, bl, al * bh);
+    const float s = S + p;
+    const float bb = s - S;
+    const float err = (S - (s - bb)) + (p - bb);
+    S = s;
+    E += err + (pe + cross);
+}
+
+// Y rows of the mu = 0 functions (on-site blocks of Fig. 1): for channel ch,
+// Y[ch (P-1) + i] = v_B[ch, i, 0] Z[N0 + ch] + sum_{s >= 1} v_B[ch, i, s] Z[ch (P-1) + s - 1].
+// One thread per (column, channel) computes its P - 1 rows in double-FP32
+// arithmetic (about 2^-44 relative; the rows are sliced to 2^-32 of the column
+// maximum next), so the kernel runs on the FP32 units rather than GB300's
+// narrow FP64 pipe.  The blocks of q are split into shared memory once.
+template <int P>
+__global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *const *__restrict__ VB,
+                                  const double2 *__restrict__ Z, double2 *__restrict__ Y, long long RSc, int N0) {
+    extern __shared__ float4 vbs[];   // [N0 * P]: (hi re, lo re, hi im, lo im)
+    const QDesc q = qd[blockIdx.y];
+    const double2 *vb = VB[blockIdx.y];
+    for (int i = threadIdx.x; i < N0 * P; i += blockDim.x) {
+        const double2 v = vb[i];
+        float4 f;
+        split_f64(v.x, f.x, f.y);
+        split_f64(v.y, f.z, f.w);
+        vbs[i] = f;
+    }
+    __syncthreads();
+    const int nch = N0 / (P - 1);
+    const long long total = q.ncols * nch;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(e % nch);
+        const long long col = q.colbase + e / nch;
+        const double2 *z = Z + col * RSc;
+        float zrh[P], zrl[P], zih[P], zil[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            const double2 v = z[s == 0 ? N0 + ch : ch * (P - 1) + s - 1];
+            split_f64(v.x, zrh[s], zrl[s]);
+            split_f64(v.y, zih[s], zil[s]);
+        }
+#pragma unroll
+        for (int i = 0; i < P - 1; ++i) {
+            const float4 *row = vbs + (size_t)(ch * (P - 1) + i) * P;
+            float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f;
+#pragma unroll
+            for (int s = 0; s < P; ++s) {
+                const float4 v = row[s];
+                df_mac(v.x, v.y, zrh[s], zrl[s], Sr, Er);
+                df_mac(-v.z, -v.w, zih[s], zil[s], Sr, Er);
+                df_mac(v.x, v.y, zih[s], zil[s], Si, Ei);
+                df_mac(v.z, v.w, zrh[s], zrl[s], Si, Ei);
+            }
+            Y[col * RSc + ch * (P - 1) + i] = make_double2(f32pair_to_f64(Sr, Er, 0), f32pair_to_f64(Si, Ei, 0));
+        }
     }
 }
 
@@ -674,6 +755,17 @@ void launch_block_y(const QDesc *d_q, int nq, const double2 *const *d_VB, const 
     long long g = (per + 255) / 256;
     if (g > 8192) g = 8192;
     dim3 grid((unsigned)g, (unsigned)nq);
+    if constexpr (std::is_same<V, double2>::value) {
+        if (P >= 2 && P <= 4 && N0 % (P - 1) == 0) {
+            const long long per_df = maxcols * (N0 / (P - 1));
+            const dim3 grid_df((unsigned)std::min<long long>(8192, (per_df + 255) / 256), (unsigned)nq);
+            const size_t sm = (size_t)N0 * P * sizeof(float4);
+            if (P == 2) block_y_df_kernel<2><<<grid_df, 256, sm, st>>>(d_q, d_VB, d_Z, d_Y, RSc, N0);
+            else if (P == 3) block_y_df_kernel<3><<<grid_df, 256, sm, st>>>(d_q, d_VB, d_Z, d_Y, RSc, N0);
+            else block_y_df_kernel<4><<<grid_df, 256, sm, st>>>(d_q, d_VB, d_Z, d_Y, RSc, N0);
+            return;
+        }
+    }
     block_y_kernel<V><<<grid, 256, 0, st>>>(d_q, d_VB, d_Z, d_Y, RSc, P, N0);
 }
 template void launch_block_y<float2>(const QDesc *, int, const double2 *const *, const float2 *, double2 *, long long,
