@@ -50,7 +50,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 
 }
 
 template <typename V>
-__global__ void slice_cols_kernel(const V *__restrict__ Z, long long RSc, const QDesc *__restrict__ qd, int N0,
+__global__ void __launch_bounds__(256, 4) slice_cols_kernel(const V *__restrict__ Z, long long RSc, const QDesc *__restrict__ qd, int N0,
                                   int N0pad, int Dpad, int RS, long long NC, __nv_bfloat16 *__restrict__ XS,
                                   int *__restrict__ xexp) {
     const QDesc q = qd[blockIdx.y];
