@@ -46,7 +46,7 @@ struct CgParams {
     const long long *rowoff;         // per A row (double2 units); < 0: no output
     const long long *coloff;         // [grp * col_gstride + pair] (double2 units); < 0: no output
     long long col_gstride;
-    const double2 *phase;            // optional: phase[phb + pkey[pair]]
+    const float4 *phase;             // optional: phase[phb + pkey[pair]], split (hi re, lo re, hi im, lo im)
     const int *pkey;
     double2 *out;
     long long RA, RB;                // rows per slice plane of A and B
@@ -162,6 +162,23 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             const CgTile tl = p.tiles[t];
             int ngroups = (tl.nchunk + CG_GROUP - 1) / CG_GROUP;
+            // the output's row offset and row exponent, and per column pair l of
+            // this half (held by lane l < 16, shuffled in the store loop) its
+            // offset, the two column exponents and the phase: fetched now so that
+            // the loads overlap the K loop
+            const int r = tl.arow + quarter * 32 + lane;
+            const long long ro = p.rowoff[r];
+            const int ea = ro >= 0 ? p.aexp[r] - 16 : 0;
+            long long co_l = -1;
+            int br_l = 0, bi_l = 0;
+            float4 f_l = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+            if (lane < 16) {
+                const int c = tl.brow + half * 32 + 2 * lane;
+                co_l = p.coloff[(long long)tl.grp * p.col_gstride + (c >> 1)];
+                br_l = p.bexp[c];
+                bi_l = p.bexp[c + 1];
+                if (p.phase) f_l = p.phase[tl.phb + p.pkey[c >> 1]];
+            }
             uint64_t hi[16], lo[16];   // packed pairs of columns
 #pragma unroll
             for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
@@ -189,28 +206,39 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
                 buf ^= 1;
             }
             if (!ok) break;
-            const int r = tl.arow + quarter * 32 + lane;
-            const long long ro = p.rowoff[r];
-            if (ro >= 0) {
-                const int ea = p.aexp[r] - 16;
-                const long long *co_tab = p.coloff + (long long)tl.grp * p.col_gstride;
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
-                    const int c = tl.brow + half * 32 + j;
-                    const long long co = co_tab[c >> 1];
-                    if (co >= 0) {
-                        const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
-                        double re = f32pair_to_f64(h.x, l.x, ea + p.bexp[c]);
-                        double im = f32pair_to_f64(h.y, l.y, ea + p.bexp[c + 1]);
-                        if (p.phase) {
-                            const double2 f = p.phase[tl.phb + p.pkey[c >> 1]];
-                            const double x = re * f.x - im * f.y;
-                            im = re * f.y + im * f.x;
-                            re = x;
-                        }
-                        __stcs(p.out + ro + co, make_double2(re, im));   // streaming: keep the operands in L2
-                    }
+            for (int j = 0; j < 32; j += 2) {
+                const int src = j / 2;
+                const long long co = __shfl_sync(0xffffffffu, co_l, src);
+                const int br = __shfl_sync(0xffffffffu, br_l, src), bi = __shfl_sync(0xffffffffu, bi_l, src);
+                const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
+                double re, im;
+                if (p.phase) {
+                    // (re + i im) e^{-i q.tau} in double-FP32 on the FP32 units (about
+                    // 2^-44 relative; the projections are sliced to 2^-32 next), both
+                    // parts first brought to the larger of their two column scales
+                    float4 f;
+                    f.x = __shfl_sync(0xffffffffu, f_l.x, src);
+                    f.y = __shfl_sync(0xffffffffu, f_l.y, src);
+                    f.z = __shfl_sync(0xffffffffu, f_l.z, src);
+                    f.w = __shfl_sync(0xffffffffu, f_l.w, src);
+                    const int sm = max(br, bi);
+                    const float sr = pow2f_neg(br - sm), si = pow2f_neg(bi - sm);
+                    float rh, rl, ih, il;
+                    two_sum(h.x * sr, l.x * sr, rh, rl);
+                    two_sum(h.y * si, l.y * si, ih, il);
+                    float Sr = 0.0f, Er = 0.0f, Si = 0.0f, Ei = 0.0f;
+                    df_mac(rh, rl, f.x, f.y, Sr, Er);
+                    df_mac(-ih, -il, f.z, f.w, Sr, Er);
+                    df_mac(rh, rl, f.z, f.w, Si, Ei);
+                    df_mac(ih, il, f.x, f.y, Si, Ei);
+                    re = f32pair_to_f64(Sr, Er, ea + sm);
+                    im = f32pair_to_f64(Si, Ei, ea + sm);
+                } else {
+                    re = f32pair_to_f64(h.x, l.x, ea + br);
+                    im = f32pair_to_f64(h.y, l.y, ea + bi);
                 }
+                if (ro >= 0 && co >= 0) __stcs(p.out + ro + co, make_double2(re, im));   // streaming: keep the operands in L2
             }
         }
     }
@@ -608,7 +636,7 @@ int zmt_tc_launch(hfx_ctx *ctx, const ZmtTcState &zs, const std::vector<PairDesc
     const int npp = (int)(zs.RB / 2);
     // output column offsets per (k, pair) and phases e^{-i q.tau_a} per (k, a, k')
     std::vector<long long> coloff((size_t)nk * npp, -1);
-    std::vector<double2> phase((size_t)nk * na * nk, make_double2(0.0, 0.0));
+    std::vector<float4> phase((size_t)nk * na * nk, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
     std::vector<char> kin(nk, 0);
     for (const PairDesc &pr : pairs) {
         if (pr.no == 0) continue;
@@ -617,7 +645,11 @@ int zmt_tc_launch(hfx_ctx *ctx, const ZmtTcState &zs, const std::vector<PairDesc
         for (int a = 0; a < na; ++a) {
             const double *tau = ctx->pos.data() + 3 * a;
             double ph = 2.0 * M_PI * ((double)j0 / M[0] * tau[0] + (double)j1 / M[1] * tau[1] + (double)j2 / M[2] * tau[2]);
-            phase[((size_t)pr.ik * na + a) * nk + pr.ikp] = make_double2(std::cos(ph), -std::sin(ph));
+            // split into FP32 pairs: hi = fl(x), lo = fl(x - hi)
+            const double fr = std::cos(ph), fi = -std::sin(ph);
+            const float frh = (float)fr, fih = (float)fi;
+            phase[((size_t)pr.ik * na + a) * nk + pr.ikp] =
+                make_float4(frh, (float)(fr - (double)frh), fih, (float)(fi - (double)fih));
             for (int m = 0; m < pr.no; ++m) {
                 int ip = zs.kbase[pr.ikp] + m;
                 coloff[(size_t)pr.ik * npp + (size_t)a * zs.npairs_pad + ip] = (pr.col0 + (long long)m * pr.nb) * RSc;
@@ -658,7 +690,7 @@ int zmt_tc_launch(hfx_ctx *ctx, const ZmtTcState &zs, const std::vector<PairDesc
     p.rowoff = at<long long>(S, zs.oro);
     p.coloff = reinterpret_cast<long long *>(T + oco);
     p.col_gstride = npp;
-    p.phase = reinterpret_cast<double2 *>(T + oph);
+    p.phase = reinterpret_cast<float4 *>(T + oph);
     p.pkey = at<int>(S, zs.opk);
     p.out = d_Z;
     return launch_cgemm(ctx, at<__nv_bfloat16>(S, zs.oA), zs.RA, at<__nv_bfloat16>(S, zs.oB), zs.RB, 2 * zs.Kh, p);

@@ -139,20 +139,6 @@ __device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
     lo = nl ? __uint_as_float(__float_as_uint(r * __uint_as_float((uint32_t)(e - 948) << 23)) | sg) : 0.0f;
 }
 
-// S + E += a * b for double-FP32 a = (ah, al), b = (bh, bl): the product's
-// rounding error from an FMA, the cross terms to first order, S updated by an
-// exact two-sum whose error joins E.  Relative error about 2^-46.
-__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float &S, float &E) {
-    const float p = ah * bh;
-    const float pe = fmaf(ah, bh, -p);
-    const float cross = fmaf(ah, bl, al * bh);
-    const float s = S + p;
-    const float bb = s - S;
-    const float err = (S - (s - bb)) + (p - bb);
-    S = s;
-    E += err + (pe + cross);
-}
-
 // Y rows of the mu = 0 functions (on-site blocks of Fig. 1): for channel ch,
 // Y[ch (P-1) + i] = v_B[ch, i, 0] Z[N0 + ch] + sum_{s >= 1} v_B[ch, i, s] Z[ch (P-1) + s - 1].
 // One thread per (column, channel) computes its P - 1 rows in double-FP32

@@ -396,6 +396,30 @@ __device__ __forceinline__ double f32pair_to_f64_int(float h, float l, int k) {
     return __longlong_as_double((long long)(sgn | (((unsigned long long)(bexp - 1) << 52) + m)));
 }
 
+// S + E += a * b for double-FP32 a = (ah, al), b = (bh, bl): the product's
+// rounding error from an FMA, the cross terms to first order, S updated by an
+// exact two-sum whose error joins E.  Relative error about 2^-46.
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float &S, float &E) {
+    const float p = ah * bh;
+    const float pe = fmaf(ah, bh, -p);
+    const float cross = fmaf(ah, bl, al * bh);
+    const float s = S + p;
+    const float bb = s - S;
+    const float err = (S - (s - bb)) + (p - bb);
+    S = s;
+    E += err + (pe + cross);
+}
+
+// (h, l) -> (s, e) with s = fl(h + l) and s + e = h + l exactly (two-sum)
+__device__ __forceinline__ void two_sum(float h, float l, float &s, float &e) {
+    s = h + l;
+    const float bb = s - h;
+    e = (h - (s - bb)) + (l - bb);
+}
+
+// 2^d as a float for d <= 0 (0 below the normal range)
+__device__ __forceinline__ float pow2f_neg(int d) { return d >= -126 ? __int_as_float((127 + d) << 23) : 0.0f; }
+
 int make_map_2d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows);
 int make_map_2d_sw(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows,
                    int box_cols, int swizzle_bytes);
