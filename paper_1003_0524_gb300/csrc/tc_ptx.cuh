@@ -241,6 +241,15 @@ __device__ __forceinline__ int line_exp_bits(unsigned long long b) {
 
 __device__ __forceinline__ int line_exp(double mx) { return line_exp_bits(abs_bits(mx)); }
 
+// An integer d with |d| <= 256 as BF16, exactly, without conversion
+// instructions: 1.5 2^23 + d has the bit pattern of 1.5 2^23 plus d (its ulp is
+// 1), subtracting 1.5 2^23 leaves d exactly, and d has at most 8 significant
+// bits, so the upper half of its FP32 pattern is its BF16 pattern.
+__device__ __forceinline__ __nv_bfloat16 small_int_bf16(int d) {
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
+}
+
 // x (|x| < 2^e) as four balanced base-256 digits s_0..s_3 of
 // N = round(x 2^(32-e)) (nearest, ties to even): x ~ sum_i s_i 2^(e-8(i+1)),
 // |s_0| <= 256, |s_1..3| <= 128, each exact in BF16.
@@ -265,10 +274,10 @@ __device__ __forceinline__ void slice4(double x, int e, __nv_bfloat16 *o /* 4 */
     N = (N - d2) >> 8;
     long long d1 = ((N + 128) & 255) - 128;
     N = (N - d1) >> 8;
-    o[0] = __float2bfloat16_rn((float)N);
-    o[1] = __float2bfloat16_rn((float)d1);
-    o[2] = __float2bfloat16_rn((float)d2);
-    o[3] = __float2bfloat16_rn((float)d3);
+    o[0] = small_int_bf16((int)N);
+    o[1] = small_int_bf16((int)d1);
+    o[2] = small_int_bf16((int)d2);
+    o[3] = small_int_bf16((int)d3);
 }
 
 // Combine the four exact class sums of one K group (units 2^(eA+eB-16)) and
