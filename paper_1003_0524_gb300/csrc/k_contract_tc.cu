@@ -700,23 +700,6 @@ int num_sms() {
     return n;
 }
 
-
-int make_map_5d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, const unsigned long long dims[5],
-                const unsigned long long strides_bytes[4], const unsigned int box[5], int swizzle_bytes) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return set_err(ctx, HFX_EDEVICE, "cuTensorMapEncodeTiled unavailable");
-    cuuint64_t d[5], st[4];
-    cuuint32_t b[5], es[5] = {1, 1, 1, 1, 1};
-    for (int i = 0; i < 5; ++i) { d[i] = dims[i]; b[i] = box[i]; }
-    for (int i = 0; i < 4; ++i) st[i] = strides_bytes[i];
-    CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
-                            : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
-                            : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(ptr), d, st, b, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return set_err(ctx, HFX_EDEVICE, "cuTensorMapEncodeTiled (5-D) failed (" + std::to_string((int)r) + ")");
-    return HFX_OK;
-}
 }  // namespace tc
 
 template <typename V>

@@ -198,30 +198,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 }
 
 
-// K-major operand with 32-byte swizzle (rows of 16 BF16): 8-row atoms of
-// 256 bytes.
-__device__ __forceinline__ uint64_t desc_sw32(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(256 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)6 << 61;
-    return d;
-}
-
-__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
-                                            int c3, int c4) {
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::
-            "r"(dst),
-        "l"((uint64_t)map), "r"(saddr(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
-        : "memory");
-}
-
 // ------------------------------------------------------------- slices
 constexpr int NPL = 4;      // slices per operand
-constexpr int NTERM = 10;   // slice products s_i t_j with i + j <= 3
 
 // The slicing below runs on the integer units: GB300's FP64 pipe is far too
 // narrow for a pass over every element of the projections.
@@ -238,8 +216,6 @@ __device__ __forceinline__ int line_exp_bits(unsigned long long b) {
     int E = (int)(b >> 52);
     return E == 0 ? -1021 : E - 1022;
 }
-
-__device__ __forceinline__ int line_exp(double mx) { return line_exp_bits(abs_bits(mx)); }
 
 // An integer d with |d| <= 256 as BF16, exactly, without conversion
 // instructions: 1.5 2^23 + d has the bit pattern of 1.5 2^23 plus d (its ulp is
@@ -432,8 +408,6 @@ __device__ __forceinline__ float pow2f_neg(int d) { return d >= -126 ? __int_as_
 int make_map_2d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows);
 int make_map_2d_sw(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows,
                    int box_cols, int swizzle_bytes);
-int make_map_5d(hfx_ctx *ctx, CUtensorMap *m, const void *ptr, const unsigned long long dims[5],
-                const unsigned long long strides_bytes[4], const unsigned int box[5], int swizzle_bytes);
 int num_sms();
 
 }  // namespace tc
