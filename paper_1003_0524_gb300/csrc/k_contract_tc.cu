@@ -1,6 +1,6 @@
 // k_contract_tc.cu -- the contraction on the 5th-generation tensor cores
 // (tcgen05.mma kind::f16 with BF16 operands, FP32 accumulators in TMEM,
-// operands staged by TMA into 128-byte-swizzled shared memory), in
+// operands staged by TMA into swizzled shared memory), in
 // fixed-point slice arithmetic that makes every tensor-core sum exact.
 //
 // Slices.  Every operand line (a row of A, a column of B) shares one power of
