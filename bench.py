@@ -188,8 +188,13 @@ def run_ours(args):
     stream = torch.cuda.current_stream().cuda_stream
     ctx = hfx.Context(s, precision=args.precision, stream=stream, device=local)
     ctx.load_system()
-    for _ in range(args.warmup):
-        ctx.build_all()
+    # the first build after set_coulomb also runs the once-per-SCF-cycle work
+    # (multipole transform of every v(q), sparse check, slices of v_t, q->0 bracket)
+    first_ms = None
+    for i in range(args.warmup):
+        st0 = ctx.build_all()
+        if i == 0:
+            first_ms = st0["ms_total"]
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
@@ -315,6 +320,11 @@ def run_ours(args):
             "fp64_gpu": fp64,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(sum(st["n_launches"] for st in stats)),
+            "once_per_scf_cycle": {
+                "first_build_ms": first_ms,
+                "coulomb_setup_ms": (first_ms - ms) if first_ms is not None else None,
+                "what": "v(q) multipole transform, sparse check, v_t slices and q->0 bracket, run by the "
+                        "first build after set_coulomb (first build minus a timed step); not in value"},
             "clocks": ck,
         }
         print(json.dumps(line), flush=True)
