@@ -323,8 +323,9 @@ def run_ours(args):
             "once_per_scf_cycle": {
                 "first_build_ms": first_ms,
                 "coulomb_setup_ms": (first_ms - ms) if first_ms is not None else None,
-                "what": "v(q) multipole transform, sparse check, v_t slices and q->0 bracket, run by the "
-                        "first build after set_coulomb (first build minus a timed step); not in value"},
+                "what": "first build minus a timed step: the v(q) multipole transform, sparse check, v_t slices "
+                        "and q->0 bracket run by the first build after set_coulomb, plus the first-use allocation "
+                        "of the scratch buffers; not in value"},
             "clocks": ck,
         }
         print(json.dumps(line), flush=True)

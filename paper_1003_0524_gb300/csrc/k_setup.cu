@@ -182,10 +182,6 @@ __device__ __forceinline__ PIdx classify(int p, int N0, int nch, int P) {
     return r;
 }
 
-__device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
-    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
-}
-
 // v_t[p][q] = sum_{s,s'} T_p[s] v[orig(p,s)][orig(q,s')] T_q[s'] in the permuted
 // order [mu=0 | mu!=0 | IPW] (sparse) or the original order without transform.
 __global__ void transform_v_kernel(const double2 *v, double2 *VD, double2 *VB, const double *T, int n_atoms,
@@ -195,13 +191,16 @@ __global__ void transform_v_kernel(const double2 *v, double2 *VD, double2 *VB, c
     int nch = n_atoms * nLM, nmt = nch * P, naux = nmt + nipw;
     int N0 = sparse ? nch * (P - 1) : 0;
     long long total = (long long)naux * naux;
+    // running maxima of |v_t| and of the elements off the pattern, per thread
+    // (non-negative doubles order like their bit patterns), one atomic per warp
+    unsigned long long tabs = 0, toff = 0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         int p = (int)(e / naux), q = (int)(e % naux);
         if (!sparse) {
             double2 val = v[e];
             VD[e] = val;
-            atomic_max_pos(absmax, fabs(val.x) + fabs(val.y));
+            tabs = max(tabs, (unsigned long long)__double_as_longlong(fabs(val.x) + fabs(val.y)));
             continue;
         }
         PIdx a = classify(p, N0, nch, P), b = classify(q, N0, nch, P);
@@ -237,13 +236,13 @@ __global__ void transform_v_kernel(const double2 *v, double2 *VD, double2 *VB, c
             }
         }
         double mag = fabs(acc.x) + fabs(acc.y);
-        atomic_max_pos(absmax, mag);
+        tabs = max(tabs, (unsigned long long)__double_as_longlong(mag));
         // pattern of Fig. 1: a mu=0 function couples only inside its own channel
         bool allowed = true;
         if (a.kind == 0 && b.ch != a.ch) allowed = false;
         if (b.kind == 0 && a.ch != b.ch) allowed = false;
         if (!allowed) {
-            atomic_max_pos(offmax, mag);
+            toff = max(toff, (unsigned long long)__double_as_longlong(mag));
             acc = make_double2(0.0, 0.0);
         }
         if (p >= N0) {
@@ -252,6 +251,15 @@ __global__ void transform_v_kernel(const double2 *v, double2 *VD, double2 *VB, c
             int slot = (b.kind == 1) ? 0 : b.i;  // 0: the channel's mu!=0 function
             VB[((size_t)a.ch * (P - 1) + (a.i - 1)) * P + slot] = acc;
         }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tabs = max(tabs, __shfl_xor_sync(0xffffffffu, tabs, o));
+        toff = max(toff, __shfl_xor_sync(0xffffffffu, toff, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (tabs) atomicMax(absmax, tabs);
+        if (toff) atomicMax(offmax, toff);
     }
 }
 
