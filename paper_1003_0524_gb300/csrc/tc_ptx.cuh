@@ -366,8 +366,9 @@ __device__ __forceinline__ double f32pair_to_f64_int(float h, float l, int k) {
     const int emax = mh ? (ml ? max(eh, el) : eh) : el;
     const int e0 = emax - 38;
     const int dh = eh - e0, dl = el - e0;                                // the larger term: shift 38
-    const long long S = (dh >= 0 ? mh << dh : (dh > -63 ? mh >> -dh : (mh < 0 ? -1 : 0))) +
-                        (dl >= 0 ? ml << dl : (dl > -63 ? ml >> -dl : (ml < 0 ? -1 : 0)));
+    // (a signed term times 2^d as a product: left shifts of negative values are not defined)
+    const long long S = (dh >= 0 ? mh * (1LL << dh) : (dh > -63 ? mh >> -dh : (mh < 0 ? -1 : 0))) +
+                        (dl >= 0 ? ml * (1LL << dl) : (dl > -63 ? ml >> -dl : (ml < 0 ? -1 : 0)));
     if (S == 0) return 0.0;
     const unsigned long long sgn = S < 0 ? (1ULL << 63) : 0ULL;
     unsigned long long a = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
