@@ -1,6 +1,7 @@
 // hfx_api.cu -- C ABI of the exchange-matrix library: input validation,
 // device-resident inputs, q batching and the two build pipelines
 // (FP64, and BF16x3 split products on the tensor cores).
+#include <type_traits>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -756,8 +757,11 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
             }
         }
         kstart.push_back((int)klpairs.size());
-        std::vector<const double2 *> hVB(nq);
-        for (int i = 0; i < nq; ++i) hVB[i] = ctx->qp[bt.qs[i]].d_VB;
+        std::vector<const double2 *> hVB(nq), hVD(nq);
+        for (int i = 0; i < nq; ++i) {
+            hVB[i] = ctx->qp[bt.qs[i]].d_VB;
+            hVD[i] = ctx->qp[bt.qs[i]].d_VD;
+        }
 
         // device descriptors
         size_t o2 = 0;
@@ -766,6 +770,7 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
                p_kpair = place2(kpair.size() * sizeof(int)), p_praw = place2(npairs * sizeof(long long)),
                p_klist = place2(klist.size() * sizeof(int)), p_kstart = place2(kstart.size() * sizeof(int)),
                p_klp = place2(std::max<size_t>(1, klpairs.size()) * sizeof(int)), p_vb = place2(nq * sizeof(void *)),
+               p_vd = place2(nq * sizeof(void *)),
                p_zg = place2(std::max(npairs, nq) * sizeof(ZGemmBatch)),
                p_tiles = place2((size_t)64 << 20);
         // per-batch tables of the tensor-core Z^MT product: offsets per (k, pair), phases, tiles
@@ -785,7 +790,8 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
             (rc = h2d(ctx, reinterpret_cast<int *>(dp + p_klist), klist.data(), klist.size())) ||
             (rc = h2d(ctx, reinterpret_cast<int *>(dp + p_kstart), kstart.data(), kstart.size())) ||
             (rc = h2d(ctx, reinterpret_cast<int *>(dp + p_klp), klpairs.data(), klpairs.size())) ||
-            (rc = h2d(ctx, reinterpret_cast<const double2 **>(dp + p_vb), hVB.data(), nq)))
+            (rc = h2d(ctx, reinterpret_cast<const double2 **>(dp + p_vb), hVB.data(), nq)) ||
+            (rc = h2d(ctx, reinterpret_cast<const double2 **>(dp + p_vd), hVD.data(), nq)))
             return rc;
         // working buffers
         if ((rc = scratch_reserve(ctx, ctx->s_zc, (size_t)bt.ncols * RSc * sizeof(V))) ||
@@ -873,15 +879,20 @@ int build_impl(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *
             double2 *Yd = as<double2>(ctx->s_y64);
             int *zexp = as<int>(ctx->s_xexp), *yexp = zexp + bt.ncols;
             launch_slice_cols<V>(Zc, RSc, d_qd, nq, bt.ncols, maxcols, N0, N0pad, Dpad, RS, ZS, zexp, ctx->stream);
-            launch_block_y<V>(d_qd, nq, reinterpret_cast<const double2 *const *>(dp + p_vb), Zc, Yd, RSc, P, N0, maxcols,
-                              ctx->stream);
             if ((rc = cuda_check(ctx, cudaGetLastError(), "slice kernels"))) return rc;
+            // the mu = 0 columns of the dense-block rows hold only each channel's
+            // mu != 0 -> mu = 0 couplings: gemm1 leaves them out and the channel
+            // block kernel, run after it, adds them
+            const bool couple = sparse && std::is_same<V, double2>::value && block_y_couples(P, N0);
             cudaEvent_t ea0 = evs.make(ctx);
             if ((rc = launch_gemm1_tc(ctx, as<__nv_bfloat16>(ctx->s_ap), (long long)nk * 4 * MP, as<int>(ctx->s_aexp),
-                                      bt.qd.data(), d_qd, nq, ZS, zexp, Yd, RSc, bt.ncols, N0, N0pad, Dpad, RS, dp + p_tiles,
-                                      (size_t)32 << 20)))
+                                      bt.qd.data(), d_qd, nq, ZS, zexp, Yd, RSc, bt.ncols, N0, N0pad, Dpad, RS, couple,
+                                      dp + p_tiles, (size_t)32 << 20)))
                 return rc;
             cudaEvent_t ea1 = evs.make(ctx);
+            launch_block_y<V>(d_qd, nq, reinterpret_cast<const double2 *const *>(dp + p_vb),
+                              couple ? reinterpret_cast<const double2 *const *>(dp + p_vd) : nullptr, Zc, Yd, RSc, P, N0,
+                              maxcols, ctx->stream);
             launch_slice_cols<double2>(Yd, RSc, d_qd, nq, bt.ncols, maxcols, N0, N0pad, Dpad, RS, YS, yexp, ctx->stream);
             cudaEvent_t ea2 = evs.make(ctx);
             if ((rc = launch_gemm2_tc(ctx, ZS, YS, zexp, yexp, bt.ncols, RS, HS, N0pad, bt.pairs.data(), d_pairs, npairs,

@@ -221,12 +221,19 @@ void launch_block64(const QDesc *d_q, int nq, const double2 *const *d_VB, const 
 template <typename V>
 void launch_slice_cols(const V *d_Z, long long RSc, const QDesc *d_q, int nq, long long NC, long long maxcols, int N0,
                        int N0pad, int Dpad, int RS, __nv_bfloat16 *d_XS, int *d_exp, cudaStream_t st);
+// The channel blocks of Y (rows [0, N0)).  With d_VD non-null (the double-FP32
+// kernel, block_y_couples(P, N0)) it also adds to each channel's mu != 0 row
+// N0 + ch its couplings to the channel's mu = 0 functions, v_t[N0+ch, mu=0 of ch]
+// Z[mu=0 of ch]: the only nonzeros of the dense-block rows in the mu = 0 columns,
+// which gemm1 then skips (launch it after gemm1).
 template <typename V>
-void launch_block_y(const QDesc *d_q, int nq, const double2 *const *d_VB, const V *d_Z, double2 *d_Y, long long RSc,
-                    int P, int N0, long long maxcols, cudaStream_t st);
+void launch_block_y(const QDesc *d_q, int nq, const double2 *const *d_VB, const double2 *const *d_VD, const V *d_Z,
+                    double2 *d_Y, long long RSc, int P, int N0, long long maxcols, cudaStream_t st);
+bool block_y_couples(int P, int N0);
+// skip_mu0: leave out the mu = 0 columns of v_t's dense-block rows (added by launch_block_y)
 int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *h_q,
                     const QDesc *d_q, int nq, const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc,
-                    long long NC, int N0, int N0pad, int Dpad, int RS, void *d_tiles_buf, size_t tiles_cap);
+                    long long NC, int N0, int N0pad, int Dpad, int RS, bool skip_mu0, void *d_tiles_buf, size_t tiles_cap);
 int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16 *d_YS, const int *d_zexp,
                     const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *h_pairs,
                     const PairDesc *d_pairs, int npairs, const QDesc *d_q, int NB, const long long *d_praw_off,

@@ -147,10 +147,12 @@ __device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
 // narrow FP64 pipe.  The blocks of q are split into shared memory once.
 template <int P>
 __global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *const *__restrict__ VB,
-                                  const double2 *__restrict__ Z, double2 *__restrict__ Y, long long RSc, int N0) {
-    extern __shared__ float4 vbs[];   // [N0 * P]: (hi re, lo re, hi im, lo im)
+                                  const double2 *const *__restrict__ VD, const double2 *__restrict__ Z,
+                                  double2 *__restrict__ Y, long long RSc, int N0) {
+    extern __shared__ float4 vbs[];   // [N0 * P] blocks, then [N0] couplings: (hi re, lo re, hi im, lo im)
     const QDesc q = qd[blockIdx.y];
     const double2 *vb = VB[blockIdx.y];
+    const int nch = N0 / (P - 1);
     for (int i = threadIdx.x; i < N0 * P; i += blockDim.x) {
         const double2 v = vb[i];
         float4 f;
@@ -158,8 +160,19 @@ __global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *c
         split_f64(v.y, f.z, f.w);
         vbs[i] = f;
     }
+    float4 *vcs = vbs + N0 * P;   // v_t[N0 + ch, ch (P-1) + i]: row ch of the dense block
+    if (VD) {
+        const double2 *vd = VD[blockIdx.y];
+        for (int i = threadIdx.x; i < N0; i += blockDim.x) {
+            const int ch = i / (P - 1);
+            const double2 v = vd[(size_t)ch * q.naux + i];
+            float4 f;
+            split_f64(v.x, f.x, f.y);
+            split_f64(v.y, f.z, f.w);
+            vcs[i] = f;
+        }
+    }
     __syncthreads();
-    const int nch = N0 / (P - 1);
     const long long total = q.ncols * nch;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         const int ch = (int)(e % nch);
@@ -186,6 +199,21 @@ __global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *c
             }
             Y[col * RSc + ch * (P - 1) + i] = make_double2(f32pair_to_f64(Sr, Er, 0), f32pair_to_f64(Si, Ei, 0));
         }
+        if (VD) {
+            // the channel's mu != 0 row: add its couplings to the mu = 0 functions
+            float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f;
+#pragma unroll
+            for (int s = 1; s < P; ++s) {
+                const float4 v = vcs[ch * (P - 1) + s - 1];
+                df_mac(v.x, v.y, zrh[s], zrl[s], Sr, Er);
+                df_mac(-v.z, -v.w, zih[s], zil[s], Sr, Er);
+                df_mac(v.x, v.y, zih[s], zil[s], Si, Ei);
+                df_mac(v.z, v.w, zrh[s], zrl[s], Si, Ei);
+            }
+            double2 *y = Y + col * RSc + N0 + ch;
+            const double2 y0 = *y;
+            *y = make_double2(y0.x + f32pair_to_f64(Sr, Er, 0), y0.y + f32pair_to_f64(Si, Ei, 0));
+        }
     }
 }
 
@@ -207,6 +235,7 @@ struct G1Params {
     long long RSc;
     long long NC;          // columns of the batch (plane stride in rows of ZS)
     int RS, HS, MP, N0pad, Dpad, N0;
+    int k0;                // first K column of each half (N0pad: the mu = 0 columns left out)
     int *err;
 };
 
@@ -272,7 +301,7 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                 bool stop = false;
                 for (int kc = 0; kc < 2 * nk; ++kc) {
                     if (!mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma)) { stop = true; break; }
-                    int x = (kc < nk) ? kc * G1_KC : p.HS + (kc - nk) * G1_KC;
+                    int x = p.k0 + ((kc < nk) ? kc * G1_KC : p.HS + (kc - nk) * G1_KC);
                     unsigned char *st = stages + (size_t)s * G1_STAGE;
                     mbar_expect_tx(&full_bar[s], G1_STAGE);
 #pragma unroll
@@ -716,42 +745,45 @@ template void launch_slice_cols<float2>(const float2 *, long long, const QDesc *
 template void launch_slice_cols<double2>(const double2 *, long long, const QDesc *, int, long long, long long, int, int,
                                          int, int, __nv_bfloat16 *, int *, cudaStream_t);
 
+bool block_y_couples(int P, int N0) { return P >= 2 && P <= 4 && N0 > 0 && N0 % (P - 1) == 0; }
+
 template <typename V>
-void launch_block_y(const QDesc *d_q, int nq, const double2 *const *d_VB, const V *d_Z, double2 *d_Y, long long RSc,
-                    int P, int N0, long long maxcols, cudaStream_t st) {
+void launch_block_y(const QDesc *d_q, int nq, const double2 *const *d_VB, const double2 *const *d_VD, const V *d_Z,
+                    double2 *d_Y, long long RSc, int P, int N0, long long maxcols, cudaStream_t st) {
     if (N0 == 0 || nq == 0) return;
     long long per = maxcols * N0;
     long long g = (per + 255) / 256;
     if (g > 8192) g = 8192;
     dim3 grid((unsigned)g, (unsigned)nq);
     if constexpr (std::is_same<V, double2>::value) {
-        if (P >= 2 && P <= 4 && N0 % (P - 1) == 0) {
+        if (block_y_couples(P, N0)) {
             const long long per_df = maxcols * (N0 / (P - 1));
             const dim3 grid_df((unsigned)std::min<long long>(8192, (per_df + 255) / 256), (unsigned)nq);
-            const size_t sm = (size_t)N0 * P * sizeof(float4);
-            if (P == 2) block_y_df_kernel<2><<<grid_df, 256, sm, st>>>(d_q, d_VB, d_Z, d_Y, RSc, N0);
-            else if (P == 3) block_y_df_kernel<3><<<grid_df, 256, sm, st>>>(d_q, d_VB, d_Z, d_Y, RSc, N0);
-            else block_y_df_kernel<4><<<grid_df, 256, sm, st>>>(d_q, d_VB, d_Z, d_Y, RSc, N0);
+            const size_t sm = (size_t)N0 * (P + 1) * sizeof(float4);
+            if (P == 2) block_y_df_kernel<2><<<grid_df, 256, sm, st>>>(d_q, d_VB, d_VD, d_Z, d_Y, RSc, N0);
+            else if (P == 3) block_y_df_kernel<3><<<grid_df, 256, sm, st>>>(d_q, d_VB, d_VD, d_Z, d_Y, RSc, N0);
+            else block_y_df_kernel<4><<<grid_df, 256, sm, st>>>(d_q, d_VB, d_VD, d_Z, d_Y, RSc, N0);
             return;
         }
     }
     block_y_kernel<V><<<grid, 256, 0, st>>>(d_q, d_VB, d_Z, d_Y, RSc, P, N0);
 }
-template void launch_block_y<float2>(const QDesc *, int, const double2 *const *, const float2 *, double2 *, long long,
-                                     int, int, long long, cudaStream_t);
-template void launch_block_y<double2>(const QDesc *, int, const double2 *const *, const double2 *, double2 *, long long,
-                                      int, int, long long, cudaStream_t);
+template void launch_block_y<float2>(const QDesc *, int, const double2 *const *, const double2 *const *, const float2 *,
+                                     double2 *, long long, int, int, long long, cudaStream_t);
+template void launch_block_y<double2>(const QDesc *, int, const double2 *const *, const double2 *const *,
+                                      const double2 *, double2 *, long long, int, int, long long, cudaStream_t);
 
 int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *h_q,
                     const QDesc *d_q, int nq, const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc,
-                    long long NC, int N0, int N0pad, int Dpad, int RS, void *d_tiles_buf, size_t tiles_cap) {
+                    long long NC, int N0, int N0pad, int Dpad, int RS, bool skip_mu0, void *d_tiles_buf, size_t tiles_cap) {
     int HS = N0pad + Dpad, MP = 2 * Dpad;
+    const int k0 = skip_mu0 ? N0pad : 0;   // K of each half starts here
     // clusters of G1_CS CTAs share the A rows of their tiles (multicast A)
     constexpr int CS = G1_CS;
     std::vector<G1Tile> tiles;
     for (int s = 0; s < nq; ++s) {
         const QDesc &q = h_q[s];
-        int klen = ((N0pad + q.D + G1_KC - 1) / G1_KC) * G1_KC;
+        int klen = ((N0pad - k0 + q.D + G1_KC - 1) / G1_KC) * G1_KC;
         int mt = (2 * q.D + G1_BM - 1) / G1_BM;   // row tiles over the D real and D imaginary rows
         // all row tiles of one column group back to back: the Z columns are read
         // from HBM once and the Re and Im rows of Y meet in L2
@@ -787,6 +819,7 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
     p.MP = MP;
     p.N0pad = N0pad;
     p.Dpad = Dpad;
+    p.k0 = k0;
     p.err = ctx->d_err;
     size_t smem = (size_t)G1_STAGES * G1_STAGE + 1024;
     auto kern = gemm1_kernel<CS>;
