@@ -19,7 +19,8 @@
 // needs, with no systematic bias.
 //
 // Complex arithmetic uses the real embedding [[Re, -Im], [Im, Re]].
-//   GEMM1 (per q, all k of the batch):  Y_D = v_t[D, all] Z          (Fig. 1 dense block)
+//   GEMM1 (per q, all k of the batch):  Y_D = v_t[D, D] Z_D          (Fig. 1 dense block; the mu = 0
+//        columns of these rows hold only each channel's couplings, added with the channel blocks)
 //   GEMM2 (per pair (k,q)):             P = sum_m Z_m^H Y_m          (Eq. vec-mat-vec)
 // The q sum is then done in FP64 (k_finish.cu).
 //
