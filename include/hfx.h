@@ -101,8 +101,33 @@ typedef struct {
                                  transformed v(q) */
     void *stream;             /* cudaStream_t (NULL: legacy default stream) */
     int device;               /* CUDA device ordinal */
-    size_t work_bytes;        /* device budget for per-q working buffers (0: auto) */
+    size_t work_bytes;        /* device budget for the working buffers of one batch of
+                                 (k, q) pairs (0: what the device has free after the
+                                 per-build buffers); a batch holds whole pairs, so the
+                                 k points of one q may be split over several batches */
+    int use_graph;            /* nonzero: the first build of a plan is captured as one
+                                 CUDA graph (on a private stream) and later builds with
+                                 the same inputs structure replay it on `stream` */
+    int tile_nb_zhy;          /* band block of the Z^H Y tiles: 8..64, multiple of 8
+                                 (0: least padded work) */
+    int tile_nb_zipw;         /* band block of the interstitial tiles: 8..40, multiple
+                                 of 8 (0: fewest padded bands) */
+    int test_fail_wait;       /* fault-injection hook for tests: nonzero makes the next
+                                 build's Z^H Y kernel wait on a barrier that nothing
+                                 completes; the bounded wait expires after about 1 ms,
+                                 the kernel drains its copies and MMAs, frees its TMEM
+                                 and returns, and the build returns HFX_ETIMEOUT.  The
+                                 flag clears itself after that build. */
 } hfx_options;
+
+/* Layout of the Coulomb matrix passed to hfx_set_coulomb. */
+enum {
+    HFX_LAYOUT_DENSE = 0,       /* v(q) in the MPB order above (Eq. coulomb matrix) */
+    HFX_LAYOUT_TRANSFORMED = 1  /* v_t = T v T^T in the same index positions, T the
+                                   multipole transform of hfx_get_transform (Sec. III.C):
+                                   MT function P' = 0 of every (a, L, M) is the one with
+                                   a multipole, P' >= 1 are multipole-free */
+};
 
 /* Per-build statistics (filled if the pointer is non-NULL). */
 typedef struct {
@@ -122,6 +147,9 @@ typedef struct {
     double flops_apply;       /* useful flops of the dense-block apply: 8 D^2 per column */
     double flops_zhy;         /* useful flops of Z^H Y: 8 N_aux n per column */
     double flops_zipw;        /* useful flops of the interstitial projection */
+    int graph_replayed;       /* 1 if the build was the replay of a captured CUDA graph */
+    int tile_nb_zhy;          /* band block of the Z^H Y tiles used */
+    int tile_nb_zipw;         /* band block of the interstitial tiles used (0: FP64 build) */
 } hfx_stats;
 
 /* ------------------------------------------------------------ entry points */
@@ -155,12 +183,22 @@ HFX_API int hfx_set_kpoint(hfx_ctx *ctx, int ik, int n_bands, int n_occ, int npw
 
 /* Coulomb matrix of one q point (Eq. coulomb matrix), built once per SCF cycle.
  *   n_ipw, G_aux  [n_ipw][3] integer G of the interstitial plane waves M^q_G
- *   v             [N_aux][N_aux] complex, Hermitian (HFX_ENOTHERM beyond herm_tol),
- *                 in the MPB order above; v(q=0) is the finite part v'(0) of
- *                 Eq. (div + nondiv part).
- * The library applies the multipole transform v_t = T v T^T in FP64 on the
- * device at the next build (after every hfx_set_radial). */
-HFX_API int hfx_set_coulomb(hfx_ctx *ctx, int iq, int n_ipw, const int *G_aux, const double *v);
+ *   v             N_aux x N_aux complex, row-major with row stride ld (complex
+ *                 elements, ld >= N_aux); Hermitian (HFX_ENOTHERM beyond
+ *                 herm_tol); v(q=0) is the finite part v'(0) of Eq. (div + nondiv part)
+ *   layout        HFX_LAYOUT_DENSE: v in the MPB order above; the library applies
+ *                 the multipole transform v_t = T v T^T in FP64 on the device at
+ *                 the next build (after every hfx_set_radial).
+ *                 HFX_LAYOUT_TRANSFORMED: v is already v_t (Sec. III.C, Fig. 1) for
+ *                 the T of hfx_get_transform; it is used as given.
+ * Errors: HFX_EINVAL (index, size, ld or layout), HFX_ENONFINITE, HFX_ENOTHERM. */
+HFX_API int hfx_set_coulomb(hfx_ctx *ctx, int iq, int n_ipw, const int *G_aux, const double *v, int ld, int layout);
+
+/* The multipole transform T_aL of one atom and L (Sec. III.C), P x P real,
+ * row-major: row 0 is mu_aL / |mu_aL| (the function with a multipole), rows
+ * 1..P-1 an orthonormal basis of the multipole-free functions (Gram-Schmidt
+ * on the unit vectors, in order).  Requires hfx_set_radial for the atom. */
+HFX_API int hfx_get_transform(hfx_ctx *ctx, int atom, int L, double *T);
 
 /* Supply the projection vectors of one (k, q) pair directly instead of
  * computing them from the wave functions (Eq. vec-mat-vec):
@@ -200,30 +238,32 @@ HFX_API int hfx_get_energy(hfx_ctx *ctx, double *Ex);
 HFX_API int hfx_get_q0_bracket(hfx_ctx *ctx, double *b);
 
 /* Allocation-free q->0 bracket (no counterpart in the paper: an interface
- * choice of this library).  Computes the same number as hfx_get_q0_bracket,
- * b of Eq. (div final), but needs no context and allocates no device memory,
- * for callers that cannot allocate at that point: processes whose device
- * memory is entirely owned by another allocator (for example a framework's
- * caching pool), and code that must avoid the device-wide synchronisation
- * that cudaMalloc/cudaFree may perform.
+ * choice of this library).  Writes the same value as hfx_get_q0_bracket, but
+ * needs no context and allocates no device memory, for callers that cannot
+ * allocate at that point: processes whose device memory is entirely owned by
+ * another allocator (for example a framework's caching pool), and code that
+ * must avoid the device-wide synchronisation that cudaMalloc/cudaFree may
+ * perform.
  *   lattice      [9] rows a_i (bohr)
  *   mesh         [3] k mesh, each 1..64
- *   beta         Eq. (F(q)) parameter in (0, 1)
+ *   beta         the decay parameter of the auxiliary function, in (0, 1);
+ *                q0 follows from e^{-beta q0^2} = beta
  *   bracket_dev  DEVICE pointer to one double owned by the caller; written
  *                asynchronously on `stream`
  *   stream       cudaStream_t (NULL: legacy default stream), current device
  * The partial sums of the reduction live in a fixed 512 KiB device array
- * inside the library (65536 doubles): each GPU that loads the library holds
- * it until the process exits.  Sizes needing more partial sums than that
- * (k points x (2 ceil(q0 |a_1| / 2 pi) + 5) > 65536) return HFX_EUNSUPPORTED.
- * The first call on a device resolves the array's device address (one-time
- * set-up); make that first call before any stream capture.  All calls share
- * the array: calls that overlap on the GPU (different streams, or devices
- * sharing nothing but the same call site) race on it and must be ordered by
- * the caller.  Every partial sum is written before it is read, so nothing
- * needs clearing between calls.  Errors: HFX_EINVAL (bad pointer, mesh or
- * beta), HFX_ENONFINITE, HFX_EUNSUPPORTED, HFX_EDEVICE (no device or launch
- * failure). */
+ * inside the library (65536 doubles): each GPU on which the library is used
+ * holds its own copy until the process exits.  Sizes needing more partial
+ * sums than that (k points x (2 ceil(q0 |a_1| / 2 pi) + 5) > 65536) return
+ * HFX_EUNSUPPORTED.  Every call looks up the array's address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing; the first call on a
+ * device also loads the library's module there, so make that first call
+ * before any stream capture).  Calls that overlap on the same device (for
+ * example on two streams) race on that device's array and must be ordered by
+ * the caller; calls on different devices use separate copies.  Every partial
+ * sum is written before it is read, so nothing needs clearing between calls.
+ * Errors: HFX_EINVAL (bad pointer, mesh or beta), HFX_ENONFINITE,
+ * HFX_EUNSUPPORTED, HFX_EDEVICE (no device or launch failure). */
 HFX_API int hfx_q0_bracket_noalloc(const double *lattice, const int *mesh, double beta, double *bracket_dev,
                                    void *stream);
 

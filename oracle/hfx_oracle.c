@@ -229,10 +229,12 @@ static const cplx *cptr(const double *base, long long off) { return (const cplx 
  * The phase comes from the Bloch sum Eq. (MT functions) evaluated in the home
  * cell; the MT coefficients of phi_{m,k-q} are those of phi_{m,k'}.
  * Output Z[I][m][n], I over the MT product basis, m < n_occ(k'), n < n_bands(k). */
-int ora_zmt(const OraSys *s, int ik, int iq, double *Zout) {
+/* Bands n of the projection: sel[j] for j < nsel (all bands 0..nb-1 when sel
+ * is NULL).  inner != 0 spreads the rows over the OpenMP threads. */
+static void zmt_core(const OraSys *s, int ik, int iq, const int *sel, int nsel, int inner, double *Zout) {
     int ikp, G0[3];
     ora_fold(s, ik, iq, &ikp, G0);
-    int nb = s->n_bands[ik], no = s->n_occ[ikp];
+    int nb = nsel, no = s->n_occ[ikp];
     int nlmp = n_lmp(s), nlp = n_lp(s), P = s->P;
     int nLP = (s->Lmax + 1) * P;
     int nlm = (s->lmax + 1) * (s->lmax + 1), nLM = (s->Lmax + 1) * (s->Lmax + 1);
@@ -251,38 +253,42 @@ int ora_zmt(const OraSys *s, int ik, int iq, double *Zout) {
     const cplx *Ak = cptr(s->A, s->A_off[ik]);
     const cplx *Akp = cptr(s->A, s->A_off[ikp]);
     cplx *Z = (cplx *)Zout;
-    for (int a = 0; a < s->n_atoms; ++a) {
+    const int nI = s->n_atoms * nLM * P;
+#pragma omp parallel for schedule(dynamic) if (inner)
+    for (int I = 0; I < nI; ++I) {
+        const int a = I / (nLM * P), LM = (I / P) % nLM, Pi = I % P;
+        const int L = (int)floor(sqrt((double)LM) + 1e-9), M = LM - L * L - L;
         /* e^{-i q.R_a}, q.R_a = 2 pi sum_i qf_i f_i */
         double ph = 2.0 * M_PI * (qf[0] * s->pos_frac[3 * a] + qf[1] * s->pos_frac[3 * a + 1] + qf[2] * s->pos_frac[3 * a + 2]);
         cplx phase = {cos(ph), -sin(ph)};
-        for (int L = 0; L <= s->Lmax; ++L)
-            for (int M = -L; M <= L; ++M)
-                for (int Pi = 0; Pi < P; ++Pi) {
-                    int I = (a * nLM + lm_idx(L, M)) * P + Pi;
-                    const double *Rap = s->R + ((size_t)a * nLP + (size_t)L * P + Pi) * nlp * nlp;
-                    for (int m = 0; m < no; ++m)
-                        for (int n = 0; n < nb; ++n) {
-                            cplx acc = {0.0, 0.0};
-                            for (int l = 0; l <= s->lmax; ++l)
-                                for (int m1 = -l; m1 <= l; ++m1)
-                                    for (int p = 0; p < 2; ++p)
-                                        for (int l2 = 0; l2 <= s->lmax; ++l2) {
-                                            int m2 = m1 + M;
-                                            if (m2 < -l2 || m2 > l2) continue;
-                                            double g = gt[((size_t)lm_idx(L, M) * nlm + lm_idx(l, m1)) * (s->lmax + 1) + l2];
-                                            if (g == 0.0) continue;
-                                            for (int p2 = 0; p2 < 2; ++p2) {
-                                                double r = Rap[(2 * l + p) * nlp + 2 * l2 + p2];
-                                                cplx am = Akp[((size_t)m * s->n_atoms + a) * nlmp + 2 * lm_idx(l, m1) + p];
-                                                cplx an = Ak[((size_t)n * s->n_atoms + a) * nlmp + 2 * lm_idx(l2, m2) + p2];
-                                                acc = cadd(acc, cscale(cconjmul(am, an), g * r));
-                                            }
-                                        }
-                            Z[((size_t)I * no + m) * nb + n] = cmul(phase, acc);
-                        }
-                }
+        const double *Rap = s->R + ((size_t)a * nLP + (size_t)L * P + Pi) * nlp * nlp;
+        for (int m = 0; m < no; ++m)
+            for (int n = 0; n < nb; ++n) {
+                cplx acc = {0.0, 0.0};
+                for (int l = 0; l <= s->lmax; ++l)
+                    for (int m1 = -l; m1 <= l; ++m1)
+                        for (int p = 0; p < 2; ++p)
+                            for (int l2 = 0; l2 <= s->lmax; ++l2) {
+                                int m2 = m1 + M;
+                                if (m2 < -l2 || m2 > l2) continue;
+                                double g = gt[((size_t)lm_idx(L, M) * nlm + lm_idx(l, m1)) * (s->lmax + 1) + l2];
+                                if (g == 0.0) continue;
+                                for (int p2 = 0; p2 < 2; ++p2) {
+                                    double r = Rap[(2 * l + p) * nlp + 2 * l2 + p2];
+                                    cplx am = Akp[((size_t)m * s->n_atoms + a) * nlmp + 2 * lm_idx(l, m1) + p];
+                                    const int nn = sel ? sel[n] : n;
+                                    cplx an = Ak[((size_t)nn * s->n_atoms + a) * nlmp + 2 * lm_idx(l2, m2) + p2];
+                                    acc = cadd(acc, cscale(cconjmul(am, an), g * r));
+                                }
+                            }
+                Z[((size_t)I * no + m) * nb + n] = cmul(phase, acc);
+            }
     }
     free(gt);
+}
+
+int ora_zmt(const OraSys *s, int ik, int iq, double *Zout) {
+    zmt_core(s, ik, iq, NULL, s->n_bands[ik], 0, Zout);
     return 0;
 }
 
@@ -334,8 +340,8 @@ int ora_zipw_direct(const OraSys *s, int ik, int iq, double *Zout) {
  * differs from the direct sum only in the order of the two finite sums. */
 typedef struct { int lo[3], dim[3]; cplx *T; } ThetaPsi;
 
-static void thetapsi_build(const OraSys *s, int ik, const int *lo, const int *hi, ThetaPsi *tp) {
-    int nb = s->n_bands[ik], npk = s->npw[ik];
+static void thetapsi_build(const OraSys *s, int ik, const int *lo, const int *hi, const int *sel, int nsel, ThetaPsi *tp) {
+    int nb = nsel, npk = s->npw[ik];
     const int *Gk = s->Gk + 3 * s->pw_off[ik];
     const cplx *ck = cptr(s->c, s->c_off[ik]);
     for (int x = 0; x < 3; ++x) { tp->lo[x] = lo[x]; tp->dim[x] = hi[x] - lo[x] + 1; }
@@ -368,7 +374,7 @@ static void thetapsi_build(const OraSys *s, int ik, const int *lo, const int *hi
                 int d0 = K[0] - Gk[3 * i2] - dlo[0], d1 = K[1] - Gk[3 * i2 + 1] - dlo[1], d2 = K[2] - Gk[3 * i2 + 2] - dlo[2];
                 size_t di = ((size_t)d0 * dd[1] + d1) * dd[2] + d2;
                 cplx t = {th[2 * di], th[2 * di + 1]};
-                acc = cadd(acc, cmul(t, ck[(size_t)n * npk + i2]));
+                acc = cadd(acc, cmul(t, ck[(size_t)(sel ? sel[n] : n) * npk + i2]));
             }
             tp->T[(size_t)n * nbox + ib] = acc;
         }
@@ -397,16 +403,18 @@ static void thetapsi_bounds(const OraSys *s, int ik, int *lo, int *hi) {
     for (int x = 0; x < 3; ++x) if (lo[x] > hi[x]) { lo[x] = 0; hi[x] = 0; }
 }
 
-static void zipw_from_thetapsi(const OraSys *s, int ik, int iq, const ThetaPsi *tp, cplx *Z) {
+/* nb: bands of the ThetaPsi table (all of k, or the selected ones) */
+static void zipw_from_thetapsi(const OraSys *s, int ik, int iq, const ThetaPsi *tp, int nb, int inner, cplx *Z) {
     int ikp, G0[3];
     ora_fold(s, ik, iq, &ikp, G0);
-    int nb = s->n_bands[ik], no = s->n_occ[ikp];
+    int no = s->n_occ[ikp];
     int npp = s->npw[ikp], ng = s->n_ipw[iq];
     const int *Gp = s->Gk + 3 * s->pw_off[ikp];
     const int *Ga = s->Gaux + 3 * s->gaux_off[iq];
     const cplx *cp = cptr(s->c, s->c_off[ikp]);
     size_t nbox = (size_t)tp->dim[0] * tp->dim[1] * tp->dim[2];
     double rs = 1.0 / sqrt(ora_omega(s));
+#pragma omp parallel for schedule(dynamic) if (inner)
     for (int g = 0; g < ng; ++g)
         for (int m = 0; m < no; ++m)
             for (int n = 0; n < nb; ++n) {
@@ -426,8 +434,8 @@ int ora_zipw(const OraSys *s, int ik, int iq, double *Zout) {
     int lo[3], hi[3];
     thetapsi_bounds(s, ik, lo, hi);
     ThetaPsi tp;
-    thetapsi_build(s, ik, lo, hi, &tp);
-    zipw_from_thetapsi(s, ik, iq, &tp, (cplx *)Zout);
+    thetapsi_build(s, ik, lo, hi, NULL, s->n_bands[ik], &tp);
+    zipw_from_thetapsi(s, ik, iq, &tp, s->n_bands[ik], 0, (cplx *)Zout);
     free(tp.T);
     return 0;
 }
@@ -473,13 +481,13 @@ void ora_transform_T(int P, const double *mu, double *T) {
 
 /* Full projection vector of a pair, Z[I][m][n] over the whole MPB (MT part
  * first, then the interstitial plane waves in list order). */
-static void z_pair(const OraSys *s, int ik, int iq, const ThetaPsi *tp, cplx *Z) {
+static void z_pair(const OraSys *s, int ik, int iq, const ThetaPsi *tp, const int *sel, int nsel, int inner, cplx *Z) {
     int ikp, G0[3];
     ora_fold(s, ik, iq, &ikp, G0);
-    int nb = s->n_bands[ik], no = s->n_occ[ikp];
+    int nb = nsel, no = s->n_occ[ikp];
     size_t mt = (size_t)n_mt(s) * no * nb;
-    ora_zmt(s, ik, iq, (double *)Z);
-    zipw_from_thetapsi(s, ik, iq, tp, Z + mt);
+    zmt_core(s, ik, iq, sel, nsel, inner, (double *)Z);
+    zipw_from_thetapsi(s, ik, iq, tp, nsel, inner, Z + mt);
 }
 
 /* Apply the multipole transform of every (a, L, M) to the MT rows of Z
@@ -570,24 +578,35 @@ double ora_vdiv(const OraSys *s) {
  * plus, if q0term, -delta_nn' f_nk b (Eq. div final; f_nk = 1 for
  * n < n_occ(k)).  transformed = 1 evaluates the same sum in the multipole-
  * transformed basis (Z_t = T Z, v_t = T v T^T, Sec. III.C) with dense loops.
- * Output V[n][n'] complex, n_bands(k)^2.  OpenMP distributes the q sum; the
- * per-q results are added in q order. */
-int ora_vx(const OraSys *s, int ik, int transformed, int q0term, double *Vout) {
-    int nk = n_k(s), nb = s->n_bands[ik];
+ * Bands n, n' run over sel[0..nsel) (all bands when sel is NULL); the m sum
+ * always takes every occupied band of k - q.  Output V[j][j'] complex,
+ * nsel^2.  OpenMP distributes the q sum (or, on meshes with fewer q points
+ * than threads, the rows inside each pair); every element is summed in the
+ * same order either way, and the per-q results are added in q order. */
+static int vx_core(const OraSys *s, int ik, int transformed, int q0term, const int *sel, int nsel, int nql,
+                   const int *qlist, double *Vout) {
+    int nk = n_k(s), nb = nsel;
     int lo[3], hi[3];
     thetapsi_bounds(s, ik, lo, hi);
     ThetaPsi tp;
-    thetapsi_build(s, ik, lo, hi, &tp);
+    thetapsi_build(s, ik, lo, hi, sel, nsel, &tp);
     cplx *part = (cplx *)calloc((size_t)nk * nb * nb, sizeof(cplx));
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int iq = 0; iq < nk; ++iq) {
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    const int nqs = qlist ? nql : nk;
+    const int inner = nqs < nthr;
+#pragma omp parallel for schedule(dynamic, 1) if (!inner)
+    for (int iqs = 0; iqs < nqs; ++iqs) {
+        const int iq = qlist ? qlist[iqs] : iqs;
         int ikp, G0[3];
         ora_fold(s, ik, iq, &ikp, G0);
         int no = s->n_occ[ikp];
         int n_aux = n_mt(s) + s->n_ipw[iq];
         int ncol = no * nb;
-        cplx *Z = (cplx *)malloc(sizeof(cplx) * (size_t)n_aux * ncol);
-        z_pair(s, ik, iq, &tp, Z);
+        cplx *Z = (cplx *)malloc(sizeof(cplx) * ((size_t)n_aux * ncol + 1));
+        z_pair(s, ik, iq, &tp, sel, nsel, inner, Z);
         const cplx *vq = cptr(s->v, s->v_off[iq]);
         cplx *vw = (cplx *)vq;
         cplx *vcopy = NULL;
@@ -598,7 +617,8 @@ int ora_vx(const OraSys *s, int ik, int transformed, int q0term, double *Vout) {
             vw = vcopy;
         }
         /* Y = v Z (each Y[I][c] summed over J in ascending order) */
-        cplx *Y = (cplx *)calloc((size_t)n_aux * ncol, sizeof(cplx));
+        cplx *Y = (cplx *)calloc((size_t)n_aux * ncol + 1, sizeof(cplx));
+#pragma omp parallel for schedule(dynamic) if (inner)
         for (int I = 0; I < n_aux; ++I)
             for (int J = 0; J < n_aux; ++J) {
                 cplx vij = vw[(size_t)I * n_aux + J];
@@ -607,31 +627,55 @@ int ora_vx(const OraSys *s, int ik, int transformed, int q0term, double *Vout) {
                 for (int cc = 0; cc < ncol; ++cc) yr[cc] = cadd(yr[cc], cmul(vij, zr[cc]));
             }
         /* P[n][n'] = sum_m sum_I conj(Z[I,m,n]) Y[I,m,n'] (m outer, I inner) */
-        cplx *Pq = part + (size_t)iq * nb * nb;
-        for (int m = 0; m < no; ++m)
-            for (int I = 0; I < n_aux; ++I) {
-                const cplx *zr = Z + (size_t)I * ncol + (size_t)m * nb;
-                const cplx *yr = Y + (size_t)I * ncol + (size_t)m * nb;
-                for (int n = 0; n < nb; ++n)
+        cplx *Pq = part + (size_t)iqs * nb * nb;
+#pragma omp parallel for schedule(dynamic) if (inner)
+        for (int n = 0; n < nb; ++n)
+            for (int m = 0; m < no; ++m)
+                for (int I = 0; I < n_aux; ++I) {
+                    const cplx zc = Z[(size_t)I * ncol + (size_t)m * nb + n];
+                    const cplx *yr = Y + (size_t)I * ncol + (size_t)m * nb;
                     for (int n2 = 0; n2 < nb; ++n2)
-                        Pq[(size_t)n * nb + n2] = cadd(Pq[(size_t)n * nb + n2], cconjmul(zr[n], yr[n2]));
-            }
+                        Pq[(size_t)n * nb + n2] = cadd(Pq[(size_t)n * nb + n2], cconjmul(zc, yr[n2]));
+                }
         free(Y);
         free(Z);
         free(vcopy);
     }
     cplx *V = (cplx *)Vout;
     for (int i = 0; i < nb * nb; ++i) { V[i].re = 0.0; V[i].im = 0.0; }
-    for (int iq = 0; iq < nk; ++iq)
-        for (int i = 0; i < nb * nb; ++i) V[i] = cadd(V[i], part[(size_t)iq * nb * nb + i]);
+    for (int iqs = 0; iqs < nqs; ++iqs)
+        for (int i = 0; i < nb * nb; ++i) V[i] = cadd(V[i], part[(size_t)iqs * nb * nb + i]);
     for (int i = 0; i < nb * nb; ++i) V[i] = cscale(V[i], -1.0 / nk);
     if (q0term) {
         double b = ora_vdiv(s);
-        for (int n = 0; n < s->n_occ[ik] && n < nb; ++n) V[(size_t)n * nb + n].re -= b;
+        for (int j = 0; j < nb; ++j)
+            if ((sel ? sel[j] : j) < s->n_occ[ik]) V[(size_t)j * nb + j].re -= b;
     }
     free(part);
     free(tp.T);
     return 0;
+}
+
+int ora_vx(const OraSys *s, int ik, int transformed, int q0term, double *Vout) {
+    return vx_core(s, ik, transformed, q0term, NULL, s->n_bands[ik], 0, NULL, Vout);
+}
+
+/* The sub-block V^x[sel][sel] of ora_vx for the bands sel[0..nsel) of k. */
+int ora_vx_sub(const OraSys *s, int ik, int nsel, const int *sel, int q0term, double *Vout) {
+    for (int j = 0; j < nsel; ++j)
+        if (sel[j] < 0 || sel[j] >= s->n_bands[ik]) return -1;
+    return vx_core(s, ik, 0, q0term, sel, nsel, 0, NULL, Vout);
+}
+
+/* The terms of q in qlist[0..nq) only (no q->0 term): -(1/N_k) sum_{q in
+ * qlist} of the pair products of ora_vx_sub.  A bounded piece of the sum,
+ * for timing the oracle on large workloads. */
+int ora_vx_part(const OraSys *s, int ik, int nsel, const int *sel, int nq, const int *qlist, double *Vout) {
+    for (int j = 0; j < nsel; ++j)
+        if (sel[j] < 0 || sel[j] >= s->n_bands[ik]) return -1;
+    for (int i = 0; i < nq; ++i)
+        if (qlist[i] < 0 || qlist[i] >= n_k(s)) return -1;
+    return vx_core(s, ik, 0, 0, sel, nsel, nq, qlist, Vout);
 }
 
 int ora_num_threads(void) {

@@ -92,6 +92,10 @@ def lib():
             L.ora_vdiv.argtypes = [vp]
             L.ora_vx.restype = ip
             L.ora_vx.argtypes = [vp, ip, ip, ip, vp]
+            L.ora_vx_sub.restype = ip
+            L.ora_vx_sub.argtypes = [vp, ip, ip, vp, ip, vp]
+            L.ora_vx_part.restype = ip
+            L.ora_vx_part.argtypes = [vp, ip, ip, vp, ip, vp, vp]
             L.ora_num_threads.restype = ip
             L.ora_num_threads.argtypes = []
             _lib = L
@@ -196,6 +200,29 @@ class Oracle:
         nb = int(self.sys.n_bands[ik])
         out = np.zeros((nb, nb), np.complex128)
         self._L.ora_vx(self._sp, ik, int(transformed), int(q0term), _ptr(out))
+        return out
+
+
+    def vx_sub(self, ik: int, bands, q0term: bool = True) -> np.ndarray:
+        """The sub-block V^x(k)[bands][bands] (every occupied band of k - q
+        in the m sum), at the cost of len(bands) bands."""
+        sel = np.ascontiguousarray(np.asarray(bands, dtype=np.int32).ravel())
+        out = np.zeros((sel.size, sel.size), np.complex128)
+        rc = self._L.ora_vx_sub(self._sp, ik, int(sel.size), _ptr(sel), int(q0term), _ptr(out))
+        if rc != 0:
+            raise ValueError("band index out of range")
+        return out
+
+
+    def vx_part(self, ik: int, bands, qs) -> np.ndarray:
+        """The terms of the q in qs of the sub-block vx_sub(ik, bands), without
+        the q->0 term (a bounded piece of the q sum, for timing)."""
+        sel = np.ascontiguousarray(np.asarray(bands, dtype=np.int32).ravel())
+        ql = np.ascontiguousarray(np.asarray(qs, dtype=np.int32).ravel())
+        out = np.zeros((sel.size, sel.size), np.complex128)
+        rc = self._L.ora_vx_part(self._sp, ik, int(sel.size), _ptr(sel), int(ql.size), _ptr(ql), _ptr(out))
+        if rc != 0:
+            raise ValueError("band or q index out of range")
         return out
 
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
 #include <map>
 #include <memory>
 #include <string>
@@ -90,13 +91,40 @@ struct QPoint {
     // derived (after the transform): dense-block rows of v_t, all columns
     double2 *d_VD = nullptr;     // [D][naux]   permuted order
     double2 *d_VB = nullptr;     // [n_ch][P-1][P]  mu=0 rows inside their channel
-    __nv_bfloat16 *d_Ap = nullptr;  // unused (the slices of every q live in hfx_ctx::s_ap)
+    size_t vd_cap = 0, vb_cap = 0;  // allocated elements of d_VD, d_VB
+    int layout = HFX_LAYOUT_DENSE;  // how v was given (dense, or already transformed)
 };
 
 struct Scratch {                 // growable device buffers
     void *p = nullptr;
     size_t bytes = 0;
 };
+
+// Host-side image of device tables: every put() starts at a 256-byte boundary
+// and returns its offset; the image is uploaded once and the offsets resolve
+// against the device copy.
+struct HostArena {
+    std::vector<unsigned char> buf;
+    size_t put(const void *src, size_t bytes) {
+        size_t o = (buf.size() + 255) / 256 * 256;
+        buf.resize(o + (bytes ? bytes : 1), 0);
+        if (bytes) std::memcpy(buf.data() + o, src, bytes);
+        return o;
+    }
+    template <typename T> size_t put(const std::vector<T> &v) { return put(v.data(), v.size() * sizeof(T)); }
+};
+
+// Offsets of 256-byte aligned sub-buffers of one device allocation.
+struct Layout {
+    size_t off = 0;
+    size_t place(size_t bytes) {
+        size_t o = off;
+        off = (off + bytes + 255) / 256 * 256;
+        return o;
+    }
+};
+
+struct BuildPlan;   // hfx_api.cu
 
 }  // namespace hfx
 
@@ -117,6 +145,8 @@ struct hfx_ctx {
     double *d_R = nullptr;       // [n_atoms][(Lmax+1)P][nlp][nlp]
     double *d_mu = nullptr;      // [n_atoms][(Lmax+1)P]
     double *d_T = nullptr;       // [n_atoms][Lmax+1][P][P] multipole transforms
+    double *d_Tid = nullptr;     // the same shape, identity blocks (v given already transformed)
+    bool T_valid = false;        // d_T matches the current multipoles
     double *d_gaunt = nullptr;   // [nLM][nlm][lmax+1]
     double *d_posf = nullptr;    // [n_atoms][3]
     int *d_err = nullptr;        // device error word
@@ -146,13 +176,22 @@ struct hfx_ctx {
     // bumped whenever a plane-wave list, an aux list or a band window changes;
     // host tables built from the structure are reused while it stays the same
     uint64_t struct_epoch = 0;
-    std::shared_ptr<void> zipw_plan;
+    // the cached build plan (device tables, scratch layout, captured graph)
+    std::shared_ptr<hfx::BuildPlan> plan;
 };
 
 namespace hfx {
 
 // ------------------------------------------------------------ host helpers
 int set_err(hfx_ctx *ctx, int code, const std::string &msg);
+// Record a timing event (an event node of the graph while the stream captures).
+void record_event(cudaEvent_t e, cudaStream_t st);
+// k' = k - q folded into the mesh and G0 = k - q - k'
+void fold_kq(const hfx_ctx *ctx, int ik, int iq, int *ikp, int *g0);
+// Build V^x(k) for every k of kset (hfx_plan.cu): plan cache, graph capture, execution.
+int build_run(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *st);
+// Drop the cached plan and every build buffer.
+void plan_release(hfx_ctx *ctx);
 int cuda_check(hfx_ctx *ctx, cudaError_t e, const char *what);
 int scratch_reserve(hfx_ctx *ctx, Scratch &s, size_t bytes);
 
@@ -230,50 +269,83 @@ template <typename V>
 void launch_block_y(const QDesc *d_q, int nq, const double2 *const *d_VB, const double2 *const *d_VD, const V *d_Z,
                     double2 *d_Y, long long RSc, int P, int N0, long long maxcols, cudaStream_t st);
 bool block_y_couples(int P, int N0);
-// skip_mu0: leave out the mu = 0 columns of v_t's dense-block rows (added by launch_block_y)
-int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *h_q,
-                    const QDesc *d_q, int nq, const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc,
-                    long long NC, int N0, int N0pad, int Dpad, int RS, bool skip_mu0, void *d_tiles_buf, size_t tiles_cap);
+// GEMM1 tiles of one batch (host) and its launch; skip_mu0 leaves out the mu = 0
+// columns of v_t's dense-block rows (added by launch_block_y).
+int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, bool skip_mu0, std::vector<unsigned char> &out);
+int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *d_q,
+                    const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc, long long NC, int N0,
+                    int N0pad, int Dpad, int RS, bool skip_mu0, const void *d_tiles, int ntiles);
+int gemm2_tiles(const PairDesc *h_pairs, int npairs, int NB, std::vector<unsigned char> &out);
+int gemm2_check_nb(int NB);
 int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16 *d_YS, const int *d_zexp,
-                    const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *h_pairs,
-                    const PairDesc *d_pairs, int npairs, const QDesc *d_q, int NB, const long long *d_praw_off,
-                    double *d_praw, void *d_tiles_buf, size_t tiles_cap);
+                    const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *d_pairs, const QDesc *d_q,
+                    int NB, const long long *d_praw_off, double *d_praw, const void *d_tiles, int ntiles,
+                    int fail_wait);
 
 // ------------------------------------------------------------ interstitial projections on the tensor cores (k_zipw_tc.cu)
-struct ZipwTcInput {
-    std::vector<int> kset, qs;              // k points with pairs; q of the batch
-    std::vector<PairDesc> pairs;            // host copy of the batch pairs
-    const PairDesc *d_pairs;
-    const double2 *const *d_ck;             // per k: c [nb][npw]
-    const int *const *d_Gk;                 // per k: G [npw][3]
-    const int *d_npw, *d_nb;
-    const double2 *const *d_Tk;             // per k: T_n(K) [nb][box] (FP64)
-    int nb_max;
-    int tlo[3], tdim[3];                    // T box
-    double2 *d_Z;                           // projections [col][RSc]
-    long long RSc;
-    cudaEvent_t ev_gemm0 = nullptr, ev_gemm1 = nullptr;   // recorded around the GEMM launch if set
+struct ZipwBuild {                          // per build: rows (k', m), segment grid, C slices
+    bool ok = false;
+    int R = 0, Rpad = 0, nmtile = 0, nL = 0, gx0 = 0, gy0 = 0, By = 0, nsegp_max = 0, Kp = 0;
+    int NBt = 0, nblk = 0, nbpad = 0, nzb = 0, nb_max = 0;
+    int tlo[3] = {0, 0, 0}, tdim[3] = {0, 0, 0};
+    int sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0, sz0 = 0, sz1 = 0;   // extent of the segment starts
+    std::vector<int> rowbase;               // first row of every k'
+    size_t o_rowk = 0, o_rowm = 0, o_line = 0, o_sst = 0, o_sz0 = 0, o_seg = 0, o_nch = 0, o_runs = 0, o_kall = 0;
+    size_t s_a = 0, s_aexp = 0, s_eT = 0, scratch_bytes = 0, a_elems = 0;
+    size_t tq_bytes_per_slot = 0;           // sliced T of one k (all copies, planes, bands)
 };
-int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in);
+struct ZipwBatch {                          // per batch: shifts, tiles, aux lookup
+    bool ok = false;
+    int ntiles = 0, nslot = 0;
+    int amin[3] = {0, 0, 0}, ad[3] = {1, 1, 1};
+    size_t o_gtab = 0, o_pinfo = 0, o_w = 0, o_tiles = 0, o_kslot = 0;
+    size_t tq_bytes = 0;
+};
+int zipw_tc_valid_nb(int nb);
+int zipw_tc_plan_build(hfx_ctx *ctx, const std::vector<int> &kset, int nb_max, const int tlo[3], const int tdim[3],
+                       int nb_tile, HostArena &tab, ZipwBuild &zb);
+int zipw_tc_plan_batch(hfx_ctx *ctx, const ZipwBuild &zb, const std::vector<int> &qs, const std::vector<PairDesc> &pairs,
+                       HostArena &tab, ZipwBatch &bt);
+int zipw_tc_run_build(hfx_ctx *ctx, const ZipwBuild &zb, const char *dtab, char *dscr, const double2 *const *d_ck,
+                      const int *const *d_Gk, const int *d_npw, const double2 *const *d_Tk, const int *d_nb);
+int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, const char *dtab, const char *dscr,
+                      __nv_bfloat16 *dTq, const PairDesc *d_pairs, const double2 *const *d_Tk, const int *d_nb,
+                      double2 *d_Z, long long RSc, cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch);
 
 // ------------------------------------------------------------ stage-1 products on the tensor cores (k_cgemm_tc.cu)
-// T_n(K) of every k of kset (Sec. III.B), written to d_T + toff[k] + n * box.
-int thetapsi_tc(hfx_ctx *ctx, const std::vector<int> &kset, const double2 *d_theta, const int dlo[3], const int ddim[3],
-                const int tlo[3], const int tdim[3], double2 *d_T, const std::vector<size_t> &toff);
-struct ZmtTcState {                         // operand slices of Z^MT, valid for one build
-    bool ready = false;
-    int Kh = 0, npairs_a = 0, npairs_pad = 0;
+struct TpPlan {                             // T_n(K) of every k of the build (Sec. III.B)
+    bool ok = false;
+    int NU = 0, Kh = 0, npairs = 0, ntiles = 0;
     long long RA = 0, RB = 0;
-    std::vector<long long> blk_row0, blk_rows;   // [k][a]
-    std::vector<int> kbase, pk, pm;              // (k', m) pair list of every atom block
-    std::vector<std::pair<int, int>> blocks;     // (k, a) of the A blocks
-    size_t oA = 0, oB = 0, oae = 0, obe = 0, oro = 0, opk = 0, fixed_bytes = 0;
+    size_t o_uo = 0, o_ui = 0, o_uio = 0, o_rk = 0, o_rn = 0, o_co = 0, o_ro = 0, o_ti = 0, o_hc = 0, o_np = 0;
+    size_t s_A = 0, s_B = 0, s_ae = 0, s_be = 0, scratch_bytes = 0;
 };
-int zmt_tc_prepare(hfx_ctx *ctx, ZmtTcState &zs, const std::vector<int> &kset, const std::vector<double2 *> &hB,
-                   long long RSc, int N0, int sparse);
-// Z^MT of the pairs of one batch (Sec. III.A) into d_Z; d_tables: device scratch for per-batch tables.
-int zmt_tc_launch(hfx_ctx *ctx, const ZmtTcState &zs, const std::vector<PairDesc> &pairs, long long RSc, double2 *d_Z,
-                  void *d_tables, size_t tables_cap);
+int thetapsi_tc_plan(hfx_ctx *ctx, const std::vector<int> &kset, const int ddim[3], const int tdim[3],
+                     const std::vector<size_t> &toff, HostArena &tab, TpPlan &tp);
+int thetapsi_tc_run(hfx_ctx *ctx, const TpPlan &tp, const char *dtab, char *dscr, const double2 *d_theta, const int dlo[3],
+                    const int ddim[3], const int tlo[3], const int tdim[3], double2 *d_T, int *nlaunch);
+struct ZmtPlan {                            // operand slices of Z^MT, per build
+    bool ok = false;
+    int Kh = 0, npairs_a = 0, npairs_pad = 0, nblocks = 0;
+    long long RA = 0, RB = 0, maxrows = 0;
+    std::vector<long long> blk_row0, blk_rows;   // [k][a]
+    std::vector<int> kbase;                      // first (k', m) pair of every k'
+    std::vector<std::pair<int, int>> blocks;     // (k, a) of the A blocks
+    size_t o_ro = 0, o_pk = 0, o_bk = 0, o_ba = 0, o_br = 0, o_nb = 0, o_hb = 0, o_ha = 0, o_pk2 = 0, o_pm = 0, o_br0 = 0;
+    size_t s_A = 0, s_B = 0, s_ae = 0, s_be = 0, scratch_bytes = 0;
+};
+struct ZmtBatch {
+    bool ok = false;
+    int ntiles = 0;
+    size_t o_co = 0, o_ph = 0, o_ti = 0;
+};
+int zmt_tc_plan(hfx_ctx *ctx, const std::vector<int> &kset, const std::vector<double2 *> &hB, long long RSc, int N0,
+                int sparse, HostArena &tab, ZmtPlan &zs);
+int zmt_tc_run_prepare(hfx_ctx *ctx, const ZmtPlan &zs, const char *dtab, char *dscr, int *nlaunch);
+int zmt_tc_plan_batch(hfx_ctx *ctx, const ZmtPlan &zs, const std::vector<PairDesc> &pairs, long long RSc, HostArena &tab,
+                      ZmtBatch &zb);
+int zmt_tc_run_batch(hfx_ctx *ctx, const ZmtPlan &zs, const ZmtBatch &zb, const char *dtab, char *dscr, double2 *d_Z,
+                     int *nlaunch);
 
 // ------------------------------------------------------------ kernels (finish, k_finish.cu)
 void launch_reduce_pairs(const PairDesc *d_pairs, const int *d_kstart, const int *d_klist_pairs, int nk_in_batch,

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
     extern __shared__ __align__(1024) unsigned char cg_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(cg_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
-    __shared__ uint64_t full_bar[CG_STAGES], empty_bar[CG_STAGES], tfull_bar[2], tempty_bar[2];
+    __shared__ uint64_t full_bar[CG_STAGES], empty_bar[CG_STAGES], tfull_bar[2], tempty_bar[2], mma_done;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
             mbar_init(&tfull_bar[b], 1);
             mbar_init(&tempty_bar[b], CG_EPI);
         }
+        mbar_init(&mma_done, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(64 + 32 * CG_EPI, 1) cgemm_kernel(const __grid
                     buf ^= 1;
                 }
             }
+            umma_drain(&mma_done);
         }
     } else {
         int e = warp - 2;
@@ -407,30 +409,16 @@ int launch_cgemm(hfx_ctx *ctx, const __nv_bfloat16 *A, long long RA, const __nv_
     return cuda_check(ctx, cudaGetLastError(), "slice product kernel");
 }
 
-// Arena layout helper (256-byte aligned sub-buffers).
-struct Arena {
-    size_t off = 0;
-    size_t place(size_t bytes) {
-        size_t o = off;
-        off = (off + bytes + 255) / 256 * 256;
-        return o;
-    }
-};
-
-template <typename T> T *at(Scratch &s, size_t o) { return reinterpret_cast<T *>(reinterpret_cast<char *>(s.p) + o); }
-
-int up(hfx_ctx *ctx, void *dst, const void *src, size_t bytes) {
-    if (bytes == 0) return HFX_OK;
-    return cuda_check(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream), "slice product tables");
-}
-
 }  // namespace
 
 // =====================================================================
 // T_n(K) of every k of kset:  T_k[n][K] at d_T + toff[k] + n * box.
-int thetapsi_tc(hfx_ctx *ctx, const std::vector<int> &kset, const double2 *d_theta, const int dlo[3], const int ddim[3],
-                const int tlo[3], const int tdim[3], double2 *d_T, const std::vector<size_t> &toff) {
-    int rc;
+// Plan: the common plane-wave list, the operand rows and the tiles (host
+// tables, uploaded once with the build plan); run: the operand slices and the
+// product, every build.
+int thetapsi_tc_plan(hfx_ctx *ctx, const std::vector<int> &kset, const int ddim[3], const int tdim[3],
+                     const std::vector<size_t> &toff, HostArena &tab, TpPlan &tp) {
+    tp = TpPlan();
     if (kset.empty()) return HFX_OK;
     const long long box = (long long)tdim[0] * tdim[1] * tdim[2];
     // common plane-wave list U over every k of the mesh (not only kset: the
@@ -481,59 +469,74 @@ int thetapsi_tc(hfx_ctx *ctx, const std::vector<int> &kset, const double2 *d_the
     std::vector<const double2 *> hc(ctx->nk, nullptr);
     std::vector<int> hnpw(ctx->nk, 0);
     for (int k = 0; k < ctx->nk; ++k) { hc[k] = ctx->kp[k].d_c; hnpw[k] = ctx->kp[k].npw; }
+    tp.o_uo = tab.put(uoff);
+    tp.o_ui = tab.put(uidx);
+    tp.o_uio = tab.put(uidx_off);
+    tp.o_rk = tab.put(rk);
+    tp.o_rn = tab.put(rn);
+    tp.o_co = tab.put(coloff);
+    tp.o_ro = tab.put(rowoff);
+    tp.o_ti = tab.put(tiles);
+    tp.o_hc = tab.put(hc);
+    tp.o_np = tab.put(hnpw);
+    Layout lay;
+    tp.s_A = lay.place((size_t)NPL * RA * Kw * 2);
+    tp.s_B = lay.place((size_t)NPL * RB * Kw * 2);
+    tp.s_ae = lay.place(RA * 4);
+    tp.s_be = lay.place(RB * 4);
+    tp.scratch_bytes = lay.off;
+    tp.NU = NU;
+    tp.Kh = Kh;
+    tp.RA = RA;
+    tp.RB = RB;
+    tp.npairs = npairs;
+    tp.ntiles = (int)tiles.size();
+    tp.ok = true;
+    return HFX_OK;
+}
 
-    Arena ar;
-    size_t oA = ar.place((size_t)NPL * RA * Kw * 2), oB = ar.place((size_t)NPL * RB * Kw * 2),
-           oae = ar.place(RA * 4), obe = ar.place(RB * 4), ouo = ar.place(uoff.size() * 4),
-           oui = ar.place(uidx.size() * 4), ouio = ar.place(ctx->nk * 8), ork = ar.place(rk.size() * 4),
-           orn = ar.place(rn.size() * 4), oco = ar.place(coloff.size() * 8), oro = ar.place(rowoff.size() * 8),
-           oti = ar.place(tiles.size() * sizeof(CgTile)), ohc = ar.place(ctx->nk * sizeof(void *)),
-           onp = ar.place(ctx->nk * 4);
-    if ((rc = scratch_reserve(ctx, ctx->s_cgT, ar.off))) return rc;
-    Scratch &S = ctx->s_cgT;
-    if ((rc = up(ctx, at<int>(S, ouo), uoff.data(), uoff.size() * 4)) ||
-        (rc = up(ctx, at<int>(S, oui), uidx.data(), uidx.size() * 4)) ||
-        (rc = up(ctx, at<long long>(S, ouio), uidx_off.data(), ctx->nk * 8)) ||
-        (rc = up(ctx, at<int>(S, ork), rk.data(), rk.size() * 4)) || (rc = up(ctx, at<int>(S, orn), rn.data(), rn.size() * 4)) ||
-        (rc = up(ctx, at<long long>(S, oco), coloff.data(), coloff.size() * 8)) ||
-        (rc = up(ctx, at<long long>(S, oro), rowoff.data(), rowoff.size() * 8)) ||
-        (rc = up(ctx, at<CgTile>(S, oti), tiles.data(), tiles.size() * sizeof(CgTile))) ||
-        (rc = up(ctx, at<const double2 *>(S, ohc), hc.data(), ctx->nk * sizeof(void *))) ||
-        (rc = up(ctx, at<int>(S, onp), hnpw.data(), ctx->nk * 4)))
-        return rc;
-    __nv_bfloat16 *A = at<__nv_bfloat16>(S, oA), *B = at<__nv_bfloat16>(S, oB);
-    cudaMemsetAsync(B, 0, (size_t)NPL * RB * Kw * 2, ctx->stream);
-    cudaMemsetAsync(at<int>(S, obe), 0, RB * 4, ctx->stream);
-    theta_toep_kernel<<<grid_rows(RA, 8), 256, 0, ctx->stream>>>(d_theta, dlo[0], dlo[1], dlo[2], ddim[1], ddim[2], tlo[0],
-                                                                 tlo[1], tlo[2], tdim[0], tdim[1], tdim[2], at<int>(S, ouo), NU,
-                                                                 Kh, RA, A, at<int>(S, oae));
-    cband_slices_kernel<<<grid_rows(npairs, 8), 256, 0, ctx->stream>>>(
-        at<const double2 *>(S, ohc), at<int>(S, onp), at<int>(S, oui), at<long long>(S, ouio), at<int>(S, ork),
-        at<int>(S, orn), npairs, Kh, RB, B, at<int>(S, obe));
+int thetapsi_tc_run(hfx_ctx *ctx, const TpPlan &tp, const char *dtab, char *dscr, const double2 *d_theta, const int dlo[3],
+                    const int ddim[3], const int tlo[3], const int tdim[3], double2 *d_T, int *nlaunch) {
+    if (!tp.ok) return HFX_OK;
+    int rc;
+    const int Kw = 2 * tp.Kh;
+    __nv_bfloat16 *A = reinterpret_cast<__nv_bfloat16 *>(dscr + tp.s_A), *B = reinterpret_cast<__nv_bfloat16 *>(dscr + tp.s_B);
+    int *ae = reinterpret_cast<int *>(dscr + tp.s_ae), *be = reinterpret_cast<int *>(dscr + tp.s_be);
+    cudaMemsetAsync(B, 0, (size_t)NPL * tp.RB * Kw * 2, ctx->stream);
+    cudaMemsetAsync(be, 0, tp.RB * 4, ctx->stream);
+    theta_toep_kernel<<<grid_rows(tp.RA, 8), 256, 0, ctx->stream>>>(
+        d_theta, dlo[0], dlo[1], dlo[2], ddim[1], ddim[2], tlo[0], tlo[1], tlo[2], tdim[0], tdim[1], tdim[2],
+        reinterpret_cast<const int *>(dtab + tp.o_uo), tp.NU, tp.Kh, tp.RA, A, ae);
+    cband_slices_kernel<<<grid_rows(tp.npairs, 8), 256, 0, ctx->stream>>>(
+        reinterpret_cast<const double2 *const *>(dtab + tp.o_hc), reinterpret_cast<const int *>(dtab + tp.o_np),
+        reinterpret_cast<const int *>(dtab + tp.o_ui), reinterpret_cast<const long long *>(dtab + tp.o_uio),
+        reinterpret_cast<const int *>(dtab + tp.o_rk), reinterpret_cast<const int *>(dtab + tp.o_rn), tp.npairs, tp.Kh,
+        tp.RB, B, be);
     if ((rc = cuda_check(ctx, cudaGetLastError(), "step-function product slices"))) return rc;
     CgParams p{};
-    p.tiles = at<CgTile>(S, oti);
-    p.ntiles = (int)tiles.size();
-    p.aexp = at<int>(S, oae);
-    p.bexp = at<int>(S, obe);
-    p.rowoff = at<long long>(S, oro);
-    p.coloff = at<long long>(S, oco);
+    p.tiles = reinterpret_cast<const CgTile *>(dtab + tp.o_ti);
+    p.ntiles = tp.ntiles;
+    p.aexp = ae;
+    p.bexp = be;
+    p.rowoff = reinterpret_cast<const long long *>(dtab + tp.o_ro);
+    p.coloff = reinterpret_cast<const long long *>(dtab + tp.o_co);
     p.col_gstride = 0;
     p.phase = nullptr;
     p.pkey = nullptr;
     p.out = d_T;
-    return launch_cgemm(ctx, A, RA, B, RB, Kw, p);
+    if (nlaunch) *nlaunch += 3;
+    return launch_cgemm(ctx, A, tp.RA, B, tp.RB, Kw, p);
 }
 
 // =====================================================================
-// Z^MT on the tensor cores.  Prepare: slices of B_k (A operand, rows per
-// (k, a) block) and of A_{k'} (B operand, row pairs per atom block), once per
-// build; launch: per q batch, output offsets, phases and tiles.
-int zmt_tc_prepare(hfx_ctx *ctx, ZmtTcState &zs, const std::vector<int> &kset, const std::vector<double2 *> &hB,
-                   long long RSc, int N0, int sparse) {
-    int rc;
+// Z^MT on the tensor cores.  Plan (per build): rows of the B_k slices (A
+// operand, per (k, a) block) and of the A_{k'} slices (B operand, row pairs
+// per atom block); run: the slices, every build.  Per batch: output offsets,
+// phases and tiles (plan) and the product (run).
+int zmt_tc_plan(hfx_ctx *ctx, const std::vector<int> &kset, const std::vector<double2 *> &hB, long long RSc, int N0,
+                int sparse, HostArena &tab, ZmtPlan &zs) {
     const int nk = ctx->nk, na = ctx->sys.n_atoms, P = ctx->P, nLM = ctx->nLM, nLMP = nLM * P, nlmp = ctx->nlmp;
-    zs = ZmtTcState();
+    zs = ZmtPlan();
     zs.Kh = (nlmp + 63) / 64 * 64;
     const int Kw = 2 * zs.Kh;
     // A operand blocks (k, a)
@@ -581,8 +584,6 @@ int zmt_tc_prepare(hfx_ctx *ctx, ZmtTcState &zs, const std::vector<int> &kset, c
     std::vector<int> pkey(RB / 2);
     for (int a = 0; a < na; ++a)
         for (int ip = 0; ip < zs.npairs_pad; ++ip) pkey[(size_t)a * zs.npairs_pad + ip] = ip < zs.npairs_a ? pk[ip] : 0;
-    zs.pk = pk;
-    zs.pm = pm;
     zs.RA = RA;
     zs.RB = RB;
     zs.blocks.clear();
@@ -590,47 +591,52 @@ int zmt_tc_prepare(hfx_ctx *ctx, ZmtTcState &zs, const std::vector<int> &kset, c
     std::vector<const double2 *> hA(nk), hBc(nk);
     std::vector<int> hnb(nk);
     for (int k = 0; k < nk; ++k) { hA[k] = ctx->kp[k].d_A; hBc[k] = hB[k]; hnb[k] = ctx->kp[k].nb; }
-
-    Arena ar;
-    zs.oA = ar.place((size_t)NPL * RA * Kw * 2);
-    zs.oB = ar.place((size_t)NPL * RB * Kw * 2);
-    zs.oae = ar.place(RA * 4);
-    zs.obe = ar.place(RB * 4);
-    zs.oro = ar.place(RA * 8);
-    zs.opk = ar.place(pkey.size() * 4);
-    size_t obk = ar.place(blk_k.size() * 4), oba = ar.place(blk_a.size() * 4), obr = ar.place(blk_row0.size() * 8),
-           onb = ar.place(nk * 4), ohb = ar.place(nk * sizeof(void *)), oha = ar.place(nk * sizeof(void *)),
-           opk2 = ar.place(pk.size() * 4), opm = ar.place(pm.size() * 4), obr0 = ar.place(na * 8);
-    zs.fixed_bytes = ar.off;
-    if ((rc = scratch_reserve(ctx, ctx->s_cgZ, ar.off))) return rc;
-    Scratch &S = ctx->s_cgZ;
-    if ((rc = up(ctx, at<long long>(S, zs.oro), rowoff.data(), RA * 8)) ||
-        (rc = up(ctx, at<int>(S, zs.opk), pkey.data(), pkey.size() * 4)) ||
-        (rc = up(ctx, at<int>(S, obk), blk_k.data(), blk_k.size() * 4)) ||
-        (rc = up(ctx, at<int>(S, oba), blk_a.data(), blk_a.size() * 4)) ||
-        (rc = up(ctx, at<long long>(S, obr), blk_row0.data(), blk_row0.size() * 8)) ||
-        (rc = up(ctx, at<int>(S, onb), hnb.data(), nk * 4)) ||
-        (rc = up(ctx, at<const double2 *>(S, ohb), hBc.data(), nk * sizeof(void *))) ||
-        (rc = up(ctx, at<const double2 *>(S, oha), hA.data(), nk * sizeof(void *))) ||
-        (rc = up(ctx, at<int>(S, opk2), pk.data(), pk.size() * 4)) || (rc = up(ctx, at<int>(S, opm), pm.data(), pm.size() * 4)) ||
-        (rc = up(ctx, at<long long>(S, obr0), brow0.data(), na * 8)))
-        return rc;
+    zs.o_ro = tab.put(rowoff);
+    zs.o_pk = tab.put(pkey);
+    zs.o_bk = tab.put(blk_k);
+    zs.o_ba = tab.put(blk_a);
+    zs.o_br = tab.put(blk_row0);
+    zs.o_nb = tab.put(hnb);
+    zs.o_hb = tab.put(hBc);
+    zs.o_ha = tab.put(hA);
+    zs.o_pk2 = tab.put(pk);
+    zs.o_pm = tab.put(pm);
+    zs.o_br0 = tab.put(brow0);
+    zs.nblocks = (int)blk_k.size();
     int nbmax = 0;
     for (int k : kset) nbmax = std::max(nbmax, ctx->kp[k].nb);
-    long long maxrows = ((long long)nbmax * nLMP + CG_BM - 1) / CG_BM * CG_BM;
-    bk_slices_kernel<<<dim3(grid_rows(maxrows, 8), (unsigned)blk_k.size()), 256, 0, ctx->stream>>>(
-        at<const double2 *>(S, ohb), at<int>(S, obk), at<int>(S, oba), at<long long>(S, obr), at<int>(S, onb), nLMP, nlmp,
-        zs.Kh, RA, at<__nv_bfloat16>(S, zs.oA), at<int>(S, zs.oae));
+    zs.maxrows = ((long long)nbmax * nLMP + CG_BM - 1) / CG_BM * CG_BM;
+    Layout lay;
+    zs.s_A = lay.place((size_t)NPL * RA * Kw * 2);
+    zs.s_B = lay.place((size_t)NPL * RB * Kw * 2);
+    zs.s_ae = lay.place(RA * 4);
+    zs.s_be = lay.place(RB * 4);
+    zs.scratch_bytes = lay.off;
+    zs.ok = true;
+    return HFX_OK;
+}
+
+int zmt_tc_run_prepare(hfx_ctx *ctx, const ZmtPlan &zs, const char *dtab, char *dscr, int *nlaunch) {
+    if (!zs.ok) return HFX_OK;
+    const int na = ctx->sys.n_atoms, nLMP = ctx->nLM * ctx->P, nlmp = ctx->nlmp;
+    bk_slices_kernel<<<dim3(grid_rows(zs.maxrows, 8), (unsigned)zs.nblocks), 256, 0, ctx->stream>>>(
+        reinterpret_cast<const double2 *const *>(dtab + zs.o_hb), reinterpret_cast<const int *>(dtab + zs.o_bk),
+        reinterpret_cast<const int *>(dtab + zs.o_ba), reinterpret_cast<const long long *>(dtab + zs.o_br),
+        reinterpret_cast<const int *>(dtab + zs.o_nb), nLMP, nlmp, zs.Kh, zs.RA,
+        reinterpret_cast<__nv_bfloat16 *>(dscr + zs.s_A), reinterpret_cast<int *>(dscr + zs.s_ae));
     ak_slices_kernel<<<dim3(grid_rows(zs.npairs_pad, 8), (unsigned)na), 256, 0, ctx->stream>>>(
-        at<const double2 *>(S, oha), at<int>(S, opk2), at<int>(S, opm), zs.npairs_a, zs.npairs_pad, at<long long>(S, obr0),
-        na, nlmp, zs.Kh, RB, at<__nv_bfloat16>(S, zs.oB), at<int>(S, zs.obe));
-    zs.ready = true;
+        reinterpret_cast<const double2 *const *>(dtab + zs.o_ha), reinterpret_cast<const int *>(dtab + zs.o_pk2),
+        reinterpret_cast<const int *>(dtab + zs.o_pm), zs.npairs_a, zs.npairs_pad,
+        reinterpret_cast<const long long *>(dtab + zs.o_br0), na, nlmp, zs.Kh, zs.RB,
+        reinterpret_cast<__nv_bfloat16 *>(dscr + zs.s_B), reinterpret_cast<int *>(dscr + zs.s_be));
+    if (nlaunch) *nlaunch += 2;
     return cuda_check(ctx, cudaGetLastError(), "muffin-tin product slices");
 }
 
-int zmt_tc_launch(hfx_ctx *ctx, const ZmtTcState &zs, const std::vector<PairDesc> &pairs, long long RSc, double2 *d_Z,
-                  void *d_tables, size_t tables_cap) {
-    if (!zs.ready) return HFX_OK;
+int zmt_tc_plan_batch(hfx_ctx *ctx, const ZmtPlan &zs, const std::vector<PairDesc> &pairs, long long RSc, HostArena &tab,
+                      ZmtBatch &zb) {
+    zb = ZmtBatch();
+    if (!zs.ok) return HFX_OK;
     const int nk = ctx->nk, na = ctx->sys.n_atoms;
     const int *M = ctx->sys.mesh;
     const int npp = (int)(zs.RB / 2);
@@ -673,27 +679,31 @@ int zmt_tc_launch(hfx_ctx *ctx, const ZmtTcState &zs, const std::vector<PairDesc
         }
     }
     if (tiles.empty()) return HFX_OK;
-    Arena ar;
-    size_t oco = ar.place(coloff.size() * 8), oph = ar.place(phase.size() * 16), oti = ar.place(tiles.size() * sizeof(CgTile));
-    if (ar.off > tables_cap) return set_err(ctx, HFX_EUNSUPPORTED, "muffin-tin product tables exceed their buffer");
-    char *T = reinterpret_cast<char *>(d_tables);
-    int rc;
-    if ((rc = up(ctx, T + oco, coloff.data(), coloff.size() * 8)) || (rc = up(ctx, T + oph, phase.data(), phase.size() * 16)) ||
-        (rc = up(ctx, T + oti, tiles.data(), tiles.size() * sizeof(CgTile))))
-        return rc;
-    Scratch &S = ctx->s_cgZ;
+    zb.o_co = tab.put(coloff);
+    zb.o_ph = tab.put(phase);
+    zb.o_ti = tab.put(tiles);
+    zb.ntiles = (int)tiles.size();
+    zb.ok = true;
+    return HFX_OK;
+}
+
+int zmt_tc_run_batch(hfx_ctx *ctx, const ZmtPlan &zs, const ZmtBatch &zb, const char *dtab, char *dscr, double2 *d_Z,
+                     int *nlaunch) {
+    if (!zs.ok || !zb.ok) return HFX_OK;
     CgParams p{};
-    p.tiles = reinterpret_cast<CgTile *>(T + oti);
-    p.ntiles = (int)tiles.size();
-    p.aexp = at<int>(S, zs.oae);
-    p.bexp = at<int>(S, zs.obe);
-    p.rowoff = at<long long>(S, zs.oro);
-    p.coloff = reinterpret_cast<long long *>(T + oco);
-    p.col_gstride = npp;
-    p.phase = reinterpret_cast<float4 *>(T + oph);
-    p.pkey = at<int>(S, zs.opk);
+    p.tiles = reinterpret_cast<const CgTile *>(dtab + zb.o_ti);
+    p.ntiles = zb.ntiles;
+    p.aexp = reinterpret_cast<const int *>(dscr + zs.s_ae);
+    p.bexp = reinterpret_cast<const int *>(dscr + zs.s_be);
+    p.rowoff = reinterpret_cast<const long long *>(dtab + zs.o_ro);
+    p.coloff = reinterpret_cast<const long long *>(dtab + zb.o_co);
+    p.col_gstride = zs.RB / 2;
+    p.phase = reinterpret_cast<const float4 *>(dtab + zb.o_ph);
+    p.pkey = reinterpret_cast<const int *>(dtab + zs.o_pk);
     p.out = d_Z;
-    return launch_cgemm(ctx, at<__nv_bfloat16>(S, zs.oA), zs.RA, at<__nv_bfloat16>(S, zs.oB), zs.RB, 2 * zs.Kh, p);
+    if (nlaunch) *nlaunch += 1;
+    return launch_cgemm(ctx, reinterpret_cast<const __nv_bfloat16 *>(dscr + zs.s_A), zs.RA,
+                        reinterpret_cast<const __nv_bfloat16 *>(dscr + zs.s_B), zs.RB, 2 * zs.Kh, p);
 }
 
 }  // namespace hfx

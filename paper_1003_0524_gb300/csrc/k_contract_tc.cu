@@ -223,12 +223,12 @@ __global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *c
 // 64-byte swizzled row per operand row), the four slices of both operands per
 // stage, three stages; the four class accumulators fill TMEM (single buffer:
 // the MMA warp waits for the epilogue to read a K group before the next).
-// CTAs of a cluster share the A rows of their tiles (A multicast).
+// Each CTA loads the A and B tiles of its own output tile.
 struct G1Tile { int qslot, mrow, ncol0, klen, out, pad; };
 
 struct G1Params {
-    const G1Tile *tiles;          // ngroups x CS: the tiles of one group share their A rows
-    int ngroups;
+    const G1Tile *tiles;
+    int ntiles;
     const QDesc *qd;
     const int *aexp;       // per A' row: [nk][MP]
     const int *zexp;       // per column of the batch
@@ -248,7 +248,6 @@ constexpr int G1_STAGES = 3;
 constexpr int G1_GROUP = 8;                                // chunks per exact K group (256)
 constexpr int G1_TMEM = 512;                               // 4 classes x 128 columns
 constexpr int G1_THREADS = 384;                            // 3 warpgroups
-constexpr int G1_CS = 2;                                   // CTAs per cluster sharing A
 // register split (setmaxnreg): the control warpgroup gives its registers to
 // the two epilogue warpgroups; 4*32*64 + 8*32*216 <= 12*32*168
 constexpr int G1_REG_LAUNCH = 168, G1_REG_CTRL = 64, G1_REG_EPI = 216;
@@ -256,29 +255,23 @@ static_assert(4 * G1_REG_CTRL + 8 * G1_REG_EPI <= 12 * G1_REG_LAUNCH, "register 
 
 // warpgroup 0: warp 0 TMA producer, warp 1 MMA issuer (warps 2, 3 idle);
 // warpgroups 1, 2: epilogue (TMEM lane quarter = w % 4, column half = (w - 4) / 4).
-// With CS > 1 the CS CTAs of a cluster take the CS tiles of one group (same A
-// rows, different columns); each loads 128/CS rows of every A chunk and
-// multicasts them to all, and every CTA's MMA releases a stage in all CTAs.
-template <int CS>
 __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB, G1Params p) {
-    constexpr uint16_t kMask = (uint16_t)((1u << CS) - 1);
     extern __shared__ __align__(1024) unsigned char g1_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(g1_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
-    __shared__ uint64_t full_bar[G1_STAGES], empty_bar[G1_STAGES], tfull_bar, tempty_bar;
+    __shared__ uint64_t full_bar[G1_STAGES], empty_bar[G1_STAGES], tfull_bar, tempty_bar, mma_done;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int rank = CS > 1 ? (int)cluster_ctarank() : 0;
-    const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
     if (threadIdx.x == 0) {
         for (int s = 0; s < G1_STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], CS);
+            mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&tfull_bar, 1);
         mbar_init(&tempty_bar, 8);
+        mbar_init(&mma_done, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -286,7 +279,6 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (CS > 1) cluster_sync();   // every peer's barriers exist before the first multicast
     uint32_t tmem = tmem_slot;
 
     if (warp < 4) {
@@ -295,8 +287,8 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
             int s = 0;
             uint32_t ph = 0;
             int issued = 0;
-            for (int g = cid; g < p.ngroups && !abort_flag; g += ncl) {
-                G1Tile tl = p.tiles[g * CS + rank];
+            for (int t = blockIdx.x; t < p.ntiles && !abort_flag; t += gridDim.x) {
+                G1Tile tl = p.tiles[t];
                 int qi = p.qd[tl.qslot].iq;
                 int nk = tl.klen / G1_KC;
                 bool stop = false;
@@ -307,11 +299,7 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                     mbar_expect_tx(&full_bar[s], G1_STAGE);
 #pragma unroll
                     for (int pl = 0; pl < NPL; ++pl) {
-                        if (CS == 1)
-                            tma_load_2d(saddr(st + pl * G1_A_PLANE), &tmA, &full_bar[s], x, (qi * NPL + pl) * p.MP + tl.mrow);
-                        else
-                            tma_load_2d_mc(saddr(st + pl * G1_A_PLANE + rank * (G1_A_PLANE / CS)), &tmA, &full_bar[s], x,
-                                           (qi * NPL + pl) * p.MP + tl.mrow + rank * (G1_BM / CS), kMask);
+                        tma_load_2d(saddr(st + pl * G1_A_PLANE), &tmA, &full_bar[s], x, (qi * NPL + pl) * p.MP + tl.mrow);
                         tma_load_2d(saddr(st + NPL * G1_A_PLANE + pl * G1_B_PLANE), &tmB, &full_bar[s], x,
                                     (int)(pl * p.NC + tl.ncol0));
                     }
@@ -331,8 +319,8 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
             // the ten slice products
             constexpr uint32_t id1 = idesc_bf16(G1_BM, G1_BN), id2 = idesc_bf16(G1_BM, 2 * G1_BN);
             bool ok = true;
-            for (int g = cid; g < p.ngroups && ok; g += ncl) {
-                G1Tile tl = p.tiles[g * CS + rank];
+            for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+                G1Tile tl = p.tiles[t];
                 int nchunk = 2 * (tl.klen / G1_KC);
                 for (int g0 = 0; g0 < nchunk && ok; g0 += G1_GROUP) {
                     if (!mbar_wait(&tempty_bar, eph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
@@ -357,8 +345,7 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                             umma_bf16(tmem + 2 * G1_BN, d2, e0, id2, 1u);         // classes 2, 3
                             umma_bf16(tmem + 3 * G1_BN, d3, e0, id1, 1u);         // class 3
                         }
-                        if (CS == 1) umma_commit(&empty_bar[s]);
-                        else umma_commit_mc(&empty_bar[s], kMask);
+                        umma_commit(&empty_bar[s]);
                         if (++s == G1_STAGES) { s = 0; ph ^= 1; }
                     }
                     if (!ok) break;
@@ -366,14 +353,15 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                     eph ^= 1;
                 }
             }
+            umma_drain(&mma_done);
         }
     } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(G1_REG_EPI));
         const int quarter = warp % 4, half = (warp - 4) / 4;
         uint32_t eph = 0;
         bool ok = true;
-        for (int g = cid; g < p.ngroups && ok; g += ncl) {
-            G1Tile tl = p.tiles[g * CS + rank];
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+            G1Tile tl = p.tiles[t];
             const QDesc q = p.qd[tl.qslot];
             int nchunk = 2 * (tl.klen / G1_KC);
             int ngroups = (nchunk + G1_GROUP - 1) / G1_GROUP;
@@ -430,8 +418,6 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
     }
     tc_fence_before();
     __syncthreads();
-    // no CTA leaves while a peer may still multicast into it or release its stages
-    if (CS > 1) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, G1_TMEM);
@@ -451,6 +437,7 @@ struct G2Params {
     const int *zexp, *yexp;      // per column of the batch
     long long NC;
     int HS, N0pad, nstages, stage_bytes;
+    int fail_wait;               // test hook: the epilogue first waits on a barrier nothing completes
     int *err;
 };
 
@@ -474,7 +461,7 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
     extern __shared__ __align__(1024) unsigned char g2_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(g2_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
-    __shared__ uint64_t full_bar[G2_MAX_STAGES], empty_bar[G2_MAX_STAGES], tfull_bar, tempty_bar;
+    __shared__ uint64_t full_bar[G2_MAX_STAGES], empty_bar[G2_MAX_STAGES], tfull_bar, tempty_bar, mma_done, never_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -491,6 +478,8 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
         }
         mbar_init(&tfull_bar, 1);
         mbar_init(&tempty_bar, G2_EPI_WARPS);
+        mbar_init(&mma_done, 1);
+        mbar_init(&never_bar, 1);   // completed by nothing: the fault-injection wait
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -592,6 +581,7 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                     }
                 }
             }
+            umma_drain(&mma_done);
         }
     } else {
         int e = warp - 2;
@@ -599,6 +589,8 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
         uint32_t tph = 0;
         bool ok = true;
         int row = quarter * 32 + lane;            // accumulator row: Re (< NB) or Im part of band bi*NB + row % NB
+        // fault-injection hook: a bounded wait of about 1 ms that nothing completes
+        if (p.fail_wait && !mbar_wait_ns(&never_bar, 0, &abort_flag, p.err, kDevTimeoutEpi, 1000000ULL)) ok = false;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             G2Tile tl = p.tiles[t];
             const PairDesc pr = p.pairs[tl.pair];
@@ -774,40 +766,37 @@ template void launch_block_y<float2>(const QDesc *, int, const double2 *const *,
 template void launch_block_y<double2>(const QDesc *, int, const double2 *const *, const double2 *const *,
                                       const double2 *, double2 *, long long, int, int, long long, cudaStream_t);
 
-int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *h_q,
-                    const QDesc *d_q, int nq, const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc,
-                    long long NC, int N0, int N0pad, int Dpad, int RS, bool skip_mu0, void *d_tiles_buf, size_t tiles_cap) {
-    int HS = N0pad + Dpad, MP = 2 * Dpad;
-    const int k0 = skip_mu0 ? N0pad : 0;   // K of each half starts here
-    // clusters of G1_CS CTAs share the A rows of their tiles (multicast A)
-    constexpr int CS = G1_CS;
+// Tiles of GEMM1 for one batch: per q, every 128-column block of its columns
+// with all its row tiles back to back (the Z columns are read from HBM once and
+// the Re and Im rows of Y meet in L2).  skip_mu0: K starts at N0pad.
+int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, bool skip_mu0, std::vector<unsigned char> &out) {
+    const int k0 = skip_mu0 ? N0pad : 0;
     std::vector<G1Tile> tiles;
     for (int s = 0; s < nq; ++s) {
         const QDesc &q = h_q[s];
         int klen = ((N0pad - k0 + q.D + G1_KC - 1) / G1_KC) * G1_KC;
         int mt = (2 * q.D + G1_BM - 1) / G1_BM;   // row tiles over the D real and D imaginary rows
-        // all row tiles of one column group back to back: the Z columns are read
-        // from HBM once and the Re and Im rows of Y meet in L2
-        for (long long n0 = 0; n0 < q.ncols; n0 += (long long)G1_BN * CS)
-            for (int i = 0; i < mt; ++i)
-                for (int j = 0; j < CS; ++j) {
-                    long long c0 = n0 + (long long)j * G1_BN;
-                    bool real = c0 < q.ncols;   // padding tiles repeat the group's first tile and write nothing
-                    tiles.push_back(G1Tile{s, i * G1_BM, (int)(q.colbase + (real ? c0 : n0)), klen, real ? 1 : 0, 0});
-                }
+        for (long long n0 = 0; n0 < q.ncols; n0 += G1_BN)
+            for (int i = 0; i < mt; ++i) tiles.push_back(G1Tile{s, i * G1_BM, (int)(q.colbase + n0), klen, 1, 0});
     }
-    if (tiles.empty()) return HFX_OK;
-    if (tiles.size() * sizeof(G1Tile) > tiles_cap) return set_err(ctx, HFX_ENOMEM, "gemm1 tile table too large");
+    out.assign(reinterpret_cast<const unsigned char *>(tiles.data()),
+               reinterpret_cast<const unsigned char *>(tiles.data()) + tiles.size() * sizeof(G1Tile));
+    return (int)tiles.size();
+}
+
+int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *d_q,
+                    const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc, long long NC, int N0,
+                    int N0pad, int Dpad, int RS, bool skip_mu0, const void *d_tiles, int ntiles) {
+    int HS = N0pad + Dpad, MP = 2 * Dpad;
+    if (ntiles == 0) return HFX_OK;
     if (NC > 0x7fffffffLL / 4) return set_err(ctx, HFX_EUNSUPPORTED, "batch has too many columns for 32-bit TMA coordinates");
-    int rc = cuda_check(ctx, cudaMemcpyAsync(d_tiles_buf, tiles.data(), tiles.size() * sizeof(G1Tile),
-                                             cudaMemcpyHostToDevice, ctx->stream), "gemm1 tiles");
-    if (rc) return rc;
+    int rc;
     CUtensorMap mA, mB;
-    if ((rc = make_map_2d_sw(ctx, &mA, d_Ap_all, ap_rows, RS, G1_BM / CS, G1_KC, 64))) return rc;
+    if ((rc = make_map_2d_sw(ctx, &mA, d_Ap_all, ap_rows, RS, G1_BM, G1_KC, 64))) return rc;
     if ((rc = make_map_2d_sw(ctx, &mB, d_ZS, (long long)NPL * NC, RS, G1_BN, G1_KC, 64))) return rc;
     G1Params p;
-    p.tiles = reinterpret_cast<const G1Tile *>(d_tiles_buf);
-    p.ngroups = (int)(tiles.size() / CS);
+    p.tiles = reinterpret_cast<const G1Tile *>(d_tiles);
+    p.ntiles = ntiles;
     p.qd = d_q;
     p.aexp = d_aexp;
     p.zexp = d_zexp;
@@ -820,10 +809,10 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
     p.MP = MP;
     p.N0pad = N0pad;
     p.Dpad = Dpad;
-    p.k0 = k0;
+    p.k0 = skip_mu0 ? N0pad : 0;
     p.err = ctx->d_err;
     size_t smem = (size_t)G1_STAGES * G1_STAGE + 1024;
-    auto kern = gemm1_kernel<CS>;
+    auto kern = gemm1_kernel;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     {
         // the register split of the kernel assumes this launch allocation
@@ -832,31 +821,14 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
         if (fa.numRegs < G1_REG_LAUNCH)
             return set_err(ctx, HFX_EUNSUPPORTED, "gemm1 compiled with fewer registers than its warpgroup split needs");
     }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(G1_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = ctx->stream;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(num_sms() / CS * CS);
-    int ncl = 0;
-    if ((rc = cuda_check(ctx, cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg), "gemm1 cluster occupancy"))) return rc;
-    if (ncl < 1) return set_err(ctx, HFX_EUNSUPPORTED, "gemm1: no cluster fits on the device");
-    cfg.gridDim = dim3(std::min(ncl, p.ngroups) * CS);
-    if ((rc = cuda_check(ctx, cudaLaunchKernelEx(&cfg, kern, mA, mB, p), "gemm1 launch"))) return rc;
+    const int grid = std::min<int>(num_sms(), ntiles);
+    kern<<<grid, G1_THREADS, smem, ctx->stream>>>(mA, mB, p);
     return cuda_check(ctx, cudaGetLastError(), "gemm1 launch");
 }
 
-int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16 *d_YS, const int *d_zexp,
-                    const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *h_pairs,
-                    const PairDesc *d_pairs, int npairs, const QDesc *d_q, int NB, const long long *d_praw_off,
-                    double *d_praw, void *d_tiles_buf, size_t tiles_cap) {
-    if (NB % 8 != 0 || NB < 8 || NB > 64) return set_err(ctx, HFX_EINVAL, "gemm2: band tile must be a multiple of 8 up to 64");
+// Tiles of GEMM2: every (band block i, band block j) of every pair with
+// occupied bands at k - q.
+int gemm2_tiles(const PairDesc *h_pairs, int npairs, int NB, std::vector<unsigned char> &out) {
     std::vector<G2Tile> tiles;
     for (int i = 0; i < npairs; ++i) {
         int nblk = (h_pairs[i].nb + NB - 1) / NB;
@@ -864,18 +836,26 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
         for (int bi = 0; bi < nblk; ++bi)
             for (int bj = 0; bj < nblk; ++bj) tiles.push_back(G2Tile{i, bi, bj, 0});
     }
-    if (tiles.empty()) return HFX_OK;
-    if (tiles.size() * sizeof(G2Tile) > tiles_cap) return set_err(ctx, HFX_ENOMEM, "gemm2 tile table too large");
+    out.assign(reinterpret_cast<const unsigned char *>(tiles.data()),
+               reinterpret_cast<const unsigned char *>(tiles.data()) + tiles.size() * sizeof(G2Tile));
+    return (int)tiles.size();
+}
+
+int gemm2_check_nb(int NB) { return NB % 8 == 0 && NB >= 8 && NB <= 64; }
+
+int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16 *d_YS, const int *d_zexp,
+                    const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *d_pairs, const QDesc *d_q,
+                    int NB, const long long *d_praw_off, double *d_praw, const void *d_tiles, int ntiles, int fail_wait) {
+    if (!gemm2_check_nb(NB)) return set_err(ctx, HFX_EINVAL, "gemm2: band tile must be a multiple of 8 up to 64");
+    if (ntiles == 0) return HFX_OK;
     if (NC > 0x7fffffffLL / 4) return set_err(ctx, HFX_EUNSUPPORTED, "batch has too many columns for 32-bit TMA coordinates");
-    int rc = cuda_check(ctx, cudaMemcpyAsync(d_tiles_buf, tiles.data(), tiles.size() * sizeof(G2Tile),
-                                             cudaMemcpyHostToDevice, ctx->stream), "gemm2 tiles");
-    if (rc) return rc;
+    int rc;
     CUtensorMap mZ, mY;
     if ((rc = make_map_2d(ctx, &mZ, d_ZS, (long long)NPL * NC, RS, NB))) return rc;
     if ((rc = make_map_2d(ctx, &mY, d_YS, (long long)NPL * NC, RS, NB))) return rc;
     G2Params p;
-    p.tiles = reinterpret_cast<const G2Tile *>(d_tiles_buf);
-    p.ntiles = (int)tiles.size();
+    p.tiles = reinterpret_cast<const G2Tile *>(d_tiles);
+    p.ntiles = ntiles;
     p.pairs = d_pairs;
     p.qd = d_q;
     p.praw_off = d_praw_off;
@@ -885,6 +865,7 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
     p.NC = NC;
     p.HS = HS;
     p.N0pad = N0pad;
+    p.fail_wait = fail_wait;
     p.err = ctx->d_err;
     p.stage_bytes = NPL * (G2_A_PLANE + 2 * NB * 128);
     p.nstages = std::min(G2_MAX_STAGES, (int)((226 * 1024) / p.stage_bytes));

@@ -441,10 +441,10 @@ namespace {
 constexpr int kQ0ScratchMax = 65536;   // partial sums (doubles) the array holds
 static __device__ __align__(256) double g_q0_scratch[kQ0ScratchMax];
 
-// Device address of g_q0_scratch, resolved once per device.  In host code
-// the name g_q0_scratch is only a host-side stand-in, never a device address.
-constexpr int kMaxDevices = 64;
-double *g_q0_scratch_dev[kMaxDevices] = {nullptr};
+// In host code the name g_q0_scratch is only a host-side stand-in, never a
+// device address: every call resolves the current device's address with
+// cudaGetSymbolAddress (which allocates nothing), so no cached pointer is
+// shared between host threads or outlives a device reset.
 
 __global__ void q0_final_to_kernel(const double *partial, int n, double *out, double beta, double q0, double nk,
                                    double omega) {
@@ -484,15 +484,13 @@ extern "C" int hfx_q0_bracket_noalloc(const double *lattice, const int *mesh, do
         for (int j = 0; j < 3; ++j) B[3 * i + j] = 2.0 * M_PI * inv[3 * j + i];
     size_t nslab = q0_partial_count(mesh, beta, lattice);
     if (nslab > (size_t)kQ0ScratchMax) return HFX_EUNSUPPORTED;   // k mesh x G box too large for the fixed array
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HFX_EDEVICE;
-    if (!g_q0_scratch_dev[dev]) {
-        // one-time set-up on this device (the device is current here)
-        double *ptr = nullptr;
-        if (cudaGetSymbolAddress((void **)&ptr, g_q0_scratch) != cudaSuccess || !ptr) return HFX_EDEVICE;
-        g_q0_scratch_dev[dev] = ptr;
+    // the array's address on the current device (the first call on a device
+    // also loads the library's module there)
+    double *partial = nullptr;
+    if (cudaGetSymbolAddress((void **)&partial, g_q0_scratch) != cudaSuccess || !partial) {
+        cudaGetLastError();
+        return HFX_EDEVICE;
     }
-    double *partial = g_q0_scratch_dev[dev];
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     double q0 = sqrt(-log(beta) / beta);
     int bnd[3];

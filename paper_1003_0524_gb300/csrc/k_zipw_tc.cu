@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
     extern __shared__ __align__(1024) unsigned char zt_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(zt_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
-    __shared__ uint64_t full_bar[ZT_STAGES], empty_bar[ZT_STAGES], tfull_bar, tempty_bar;
+    __shared__ uint64_t full_bar[ZT_STAGES], empty_bar[ZT_STAGES], tfull_bar, tempty_bar, mma_done;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
         }
         mbar_init(&tfull_bar, 1);
         mbar_init(&tempty_bar, ZT_EPI);
+        mbar_init(&mma_done, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                     eph ^= 1;
                 }
             }
+            umma_drain(&mma_done);
         }
     } else {
         // epilogue warp (quarter, cs): TMEM lanes of its quarter, bands
@@ -449,343 +451,319 @@ int pick_nb(int nb_max) {
 
 }  // namespace
 
-// Host tables of one batch of the interstitial GEMM (see zipw_tc_prepare_and_launch).
-struct ZipwPlan {
-    bool valid = false;
-    uint64_t sig = 0;
-    void *base = nullptr;                 // scratch the tables were uploaded to
-    ZParams p;
-    size_t o_rowk = 0, o_rowm = 0, o_line = 0, o_sst = 0, o_sz0 = 0, o_tp = 0, o_a = 0, o_aexp = 0, o_eT = 0, o_kslot = 0;
-    size_t a_elems = 0;
-    int R = 0, Rpad = 0, nzb = 0, NBt = 0, nblk = 0, nbpad = 0, nslot = 0, Kp = 0, nL = 0, gx0 = 0, gy0 = 0, By = 0, nmtile = 0;
-};
-
-// FNV-1a over everything the tables depend on
-uint64_t zipw_signature(hfx_ctx *ctx, const ZipwTcInput &in) {
-    uint64_t h = 1469598103934665603ULL;
-    auto mix = [&](const void *d, size_t n) {
-        const unsigned char *c = static_cast<const unsigned char *>(d);
-        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ULL;
+// ---------------------------------------------------------------------------
+// Host side, per build: the rows (k', m) in Morton order of k', the segment
+// grid of every row tile, the C slices and the band exponents of T.
+int zipw_tc_plan_build(hfx_ctx *ctx, const std::vector<int> &kset, int nb_max, const int tlo[3], const int tdim[3],
+                       int nb_tile, HostArena &tab, ZipwBuild &zb) {
+    zb = ZipwBuild();
+    const int nk = ctx->nk;
+    // ---- G1 lines (x, y) with their z ranges over every k' plane-wave list
+    int gmin[3] = {1 << 29, 1 << 29, 1 << 29}, gmax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
+    for (auto &k : ctx->kp)
+        for (size_t i = 0; i < k.G.size(); ++i) {
+            int x = i % 3;
+            gmin[x] = std::min(gmin[x], k.G[i]);
+            gmax[x] = std::max(gmax[x], k.G[i]);
+        }
+    if (gmin[0] > gmax[0]) return HFX_OK;
+    const int Bx = gmax[0] - gmin[0] + 1, By = gmax[1] - gmin[1] + 1;
+    std::vector<int> zlo((size_t)Bx * By, 1 << 29), zhi((size_t)Bx * By, -(1 << 29));
+    for (auto &k : ctx->kp)
+        for (size_t i = 0; i + 2 < k.G.size(); i += 3) {
+            size_t b = (size_t)(k.G[i] - gmin[0]) * By + (k.G[i + 1] - gmin[1]);
+            zlo[b] = std::min(zlo[b], k.G[i + 2]);
+            zhi[b] = std::max(zhi[b], k.G[i + 2]);
+        }
+    std::vector<int> line_of((size_t)Bx * By, -1), lx, ly, lzlo;
+    for (int x = 0; x < Bx; ++x)
+        for (int y = 0; y < By; ++y) {
+            size_t b = (size_t)x * By + y;
+            if (zlo[b] > zhi[b]) continue;
+            line_of[b] = (int)lx.size();
+            lx.push_back(gmin[0] + x);
+            ly.push_back(gmin[1] + y);
+            lzlo.push_back(zlo[b]);
+        }
+    const int nL = (int)lx.size();
+    // ---- rows (k', m): k' in Morton order of their mesh indices, so that a
+    // 128-row tile holds a compact block of the mesh (overlapping spheres)
+    const int *Mh = ctx->sys.mesh;
+    auto morton = [&](int ik) {
+        const int j[3] = {ik / (Mh[1] * Mh[2]), (ik / Mh[2]) % Mh[1], ik % Mh[2]};
+        unsigned long long code = 0;
+        for (int bit = 0; bit < 20; ++bit)
+            for (int x = 0; x < 3; ++x) code |= (unsigned long long)((j[x] >> bit) & 1) << (3 * bit + 2 - x);
+        return code;
     };
-    auto mixv = [&](const auto &v) { mix(v.data(), v.size() * sizeof(v[0])); };
-    mix(&ctx->struct_epoch, sizeof(ctx->struct_epoch));
-    mix(&ctx->nk, sizeof(int));
-    mix(&ctx->nmt, sizeof(int));
-    mix(&ctx->omega, sizeof(double));
-    mixv(in.kset);
-    mixv(in.qs);
-    mixv(in.pairs);
-    mix(&in.nb_max, sizeof(int));
-    mix(in.tlo, sizeof(in.tlo));
-    mix(in.tdim, sizeof(in.tdim));
-    return h;
+    std::vector<int> korder(nk);
+    for (int i = 0; i < nk; ++i) korder[i] = i;
+    std::stable_sort(korder.begin(), korder.end(), [&](int a, int b2) { return morton(a) < morton(b2); });
+    std::vector<int> rowk, rowm;
+    zb.rowbase.assign(nk, -1);
+    for (int kp : korder) {
+        zb.rowbase[kp] = (int)rowk.size();
+        for (int m = 0; m < ctx->kp[kp].no; ++m) { rowk.push_back(kp); rowm.push_back(m); }
+    }
+    const int R = (int)rowk.size();
+    if (R == 0) return HFX_OK;
+    const int Rpad = (R + ZT_BM - 1) / ZT_BM * ZT_BM;
+    const int nmtile = Rpad / ZT_BM;
+    std::vector<std::vector<int>> tile_k(nmtile);
+    for (int r = 0; r < R; ++r)
+        if (tile_k[r / ZT_BM].empty() || tile_k[r / ZT_BM].back() != rowk[r]) tile_k[r / ZT_BM].push_back(rowk[r]);
+    // segment grid per row tile: the lines of the tile's spheres, each cut
+    // into segments of ZT_SEGZ z values from its lowest z
+    std::vector<int> segstart((size_t)nmtile * nL, 0), segz0((size_t)nmtile * nL, 0), nseg(nmtile);
+    std::vector<std::vector<int4>> segs(nmtile);
+    std::vector<int> tzlo(nL), tzhi(nL);
+    for (int t = 0; t < nmtile; ++t) {
+        std::fill(tzlo.begin(), tzlo.end(), 1 << 29);
+        std::fill(tzhi.begin(), tzhi.end(), -(1 << 29));
+        for (int kp : tile_k[t]) {
+            const std::vector<int> &G = ctx->kp[kp].G;
+            for (size_t i = 0; i + 2 < G.size(); i += 3) {
+                int l = line_of[(size_t)(G[i] - gmin[0]) * By + (G[i + 1] - gmin[1])];
+                tzlo[l] = std::min(tzlo[l], G[i + 2]);
+                tzhi[l] = std::max(tzhi[l], G[i + 2]);
+            }
+        }
+        for (int l = 0; l < nL; ++l) {
+            if (tzlo[l] > tzhi[l]) continue;
+            segstart[(size_t)t * nL + l] = (int)segs[t].size();
+            segz0[(size_t)t * nL + l] = tzlo[l];
+            for (int z = tzlo[l]; z <= tzhi[l]; z += ZT_SEGZ) segs[t].push_back(make_int4(lx[l], ly[l], z, 0));
+        }
+        if (segs[t].empty()) segs[t].push_back(make_int4(lx[0], ly[0], lzlo[0], 0));
+        nseg[t] = (int)segs[t].size();
+    }
+    int nsegp_max = 0;
+    for (int t = 0; t < nmtile; ++t) nsegp_max = std::max(nsegp_max, (nseg[t] + 7) / 8 * 8);
+    const int Kp = nsegp_max * 8;   // K values of an A row: 8 per segment
+    const int nzb = (tdim[2] + ZT_SEGZ - 1) / ZT_SEGZ;
+    std::vector<int2> segtab((size_t)nmtile * nsegp_max);
+    std::vector<int> nchunk(nmtile);
+    for (int t = 0; t < nmtile; ++t) {
+        nchunk[t] = (nseg[t] + 7) / 8;
+        for (int s2 = 0; s2 < nsegp_max; ++s2) {
+            const int4 sg = s2 < nseg[t] ? segs[t][s2] : segs[t][0];   // padding: any valid block
+            segtab[(size_t)t * nsegp_max + s2] = make_int2(sg.x * tdim[1] + sg.y, sg.z);
+        }
+    }
+    const int NBt = zipw_tc_valid_nb(nb_tile) ? nb_tile : pick_nb(nb_max);
+    const int nblk = (nb_max + NBt - 1) / NBt;
+    // bulk-copy runs per 64-K chunk: consecutive segments of one line are
+    // consecutive z blocks of T, contiguous for a single band block
+    std::vector<int> runs((size_t)nmtile * (nsegp_max / 8), 0);
+    for (int t = 0; t < nmtile; ++t)
+        for (int c = 0; c < nsegp_max / 8; ++c) {
+            const int live = std::max(0, std::min(8, nseg[t] - 8 * c));
+            int starts = 0;
+            for (int j = 0; j < live; ++j) {
+                const int s2 = 8 * c + j;
+                const bool cont = j > 0 && nblk == 1 && segs[t][s2].x == segs[t][s2 - 1].x &&
+                                  segs[t][s2].y == segs[t][s2 - 1].y && segs[t][s2].z == segs[t][s2 - 1].z + ZT_SEGZ;
+                if (!cont) starts |= 1 << j;
+            }
+            runs[(size_t)t * (nsegp_max / 8) + c] = starts | (live << 8);
+        }
+    // extent of every segment start, for the per-batch box check
+    zb.sx0 = zb.sy0 = zb.sz0 = 1 << 29;
+    zb.sx1 = zb.sy1 = zb.sz1 = -(1 << 29);
+    for (int t = 0; t < nmtile; ++t)
+        for (const int4 &sg : segs[t]) {
+            zb.sx0 = std::min(zb.sx0, sg.x); zb.sx1 = std::max(zb.sx1, sg.x);
+            zb.sy0 = std::min(zb.sy0, sg.y); zb.sy1 = std::max(zb.sy1, sg.y);
+            zb.sz0 = std::min(zb.sz0, sg.z); zb.sz1 = std::max(zb.sz1, sg.z);
+        }
+    std::vector<int> kall(nk, -1);
+    for (int ik : kset) kall[ik] = 0;
+    zb.o_rowk = tab.put(rowk);
+    zb.o_rowm = tab.put(rowm);
+    zb.o_line = tab.put(line_of);
+    zb.o_sst = tab.put(segstart);
+    zb.o_sz0 = tab.put(segz0);
+    zb.o_seg = tab.put(segtab);
+    zb.o_nch = tab.put(nchunk);
+    zb.o_runs = tab.put(runs);
+    zb.o_kall = tab.put(kall);
+    // device scratch of the build: C slices, their row exponents, band exponents of T
+    Layout lay;
+    zb.a_elems = (size_t)NPL * Rpad * Kp;
+    zb.s_a = lay.place(zb.a_elems * 2);
+    zb.s_aexp = lay.place((size_t)Rpad * 4);
+    zb.s_eT = lay.place((size_t)nk * nb_max * 4);
+    zb.scratch_bytes = lay.off;
+    zb.R = R; zb.Rpad = Rpad; zb.nmtile = nmtile; zb.nL = nL; zb.gx0 = gmin[0]; zb.gy0 = gmin[1]; zb.By = By;
+    zb.nsegp_max = nsegp_max; zb.Kp = Kp; zb.NBt = NBt; zb.nblk = nblk; zb.nbpad = nblk * NBt; zb.nzb = nzb;
+    zb.nb_max = nb_max;
+    for (int x = 0; x < 3; ++x) { zb.tlo[x] = tlo[x]; zb.tdim[x] = tdim[x]; }
+    zb.tq_bytes_per_slot = (size_t)ZT_NCOPY * tdim[0] * tdim[1] * nzb * NPL * 2 * zb.nbpad * 8 * 2;
+    zb.ok = true;
+    return HFX_OK;
 }
 
-// Host side: segment grid, slices, shift lists, tiles and launch for one batch.
-int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
+// Host side, per batch: the shifts W = G - G0 every row tile needs for each k
+// of the batch, the aux lookup over the batch's q, and the tiles.
+int zipw_tc_plan_batch(hfx_ctx *ctx, const ZipwBuild &zb, const std::vector<int> &qs, const std::vector<PairDesc> &pairs,
+                       HostArena &tab, ZipwBatch &bt) {
+    bt = ZipwBatch();
+    if (!zb.ok) return HFX_OK;
+    const int nk = ctx->nk, nmtile = zb.nmtile;
+    // ---- aux lookup tables over the batch's q
+    int amin[3] = {1 << 29, 1 << 29, 1 << 29}, amax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
+    for (int iq : qs)
+        for (size_t i = 0; i < ctx->qp[iq].G.size(); ++i) {
+            int x = i % 3;
+            amin[x] = std::min(amin[x], ctx->qp[iq].G[i]);
+            amax[x] = std::max(amax[x], ctx->qp[iq].G[i]);
+        }
+    int ad[3];
+    for (int x = 0; x < 3; ++x) {
+        if (amin[x] > amax[x]) amin[x] = amax[x] = 0;
+        ad[x] = amax[x] - amin[x] + 1;
+    }
+    const int nq = (int)qs.size();
+    std::vector<int> gtab((size_t)nq * ad[0] * ad[1] * ad[2], -1);
+    for (int s = 0; s < nq; ++s) {
+        const std::vector<int> &G = ctx->qp[qs[s]].G;
+        for (size_t g = 0; g < G.size() / 3; ++g)
+            gtab[(((size_t)s * ad[0] + (G[3 * g] - amin[0])) * ad[1] + (G[3 * g + 1] - amin[1])) * ad[2] + (G[3 * g + 2] - amin[2])] = (int)g;
+    }
+    // ---- pair info (k, k') and the shift lists / tiles per k of the batch
+    std::vector<ZPairInfo> pinfo((size_t)nk * nk, ZPairInfo{-1, 0, 0, 0});
+    std::vector<int> bks;     // k of the batch in first-appearance order
+    std::vector<int> kslot(nk, -1);
+    for (int i = 0; i < (int)pairs.size(); ++i) {
+        const PairDesc &pr = pairs[i];
+        pinfo[(size_t)pr.ik * nk + pr.ikp] = ZPairInfo{i, pr.g0[0], pr.g0[1], pr.g0[2]};
+        if (kslot[pr.ik] < 0) { kslot[pr.ik] = (int)bks.size(); bks.push_back(pr.ik); }
+    }
+    // W = G - G0 lies in [amin, amax + 1]
+    const int wd[3] = {ad[0] + 1, ad[1] + 1, ad[2] + 1};
+    const size_t wvol = (size_t)wd[0] * wd[1] * wd[2];
+    std::vector<int4> wxyz;
+    std::vector<ZTile> tiles;
+    std::vector<unsigned char> need;
+    for (int ik : bks) {
+        need.assign(wvol * nmtile, 0);
+        for (const PairDesc &pr : pairs) {
+            if (pr.ik != ik || pr.no == 0) continue;
+            const std::vector<int> &G = ctx->qp[pr.iq].G;
+            const int t0 = zb.rowbase[pr.ikp] / ZT_BM, t1 = (zb.rowbase[pr.ikp] + pr.no - 1) / ZT_BM;
+            for (size_t g = 0; g < G.size() / 3; ++g) {
+                int w0 = G[3 * g] - pr.g0[0] - amin[0], w1 = G[3 * g + 1] - pr.g0[1] - amin[1], w2 = G[3 * g + 2] - pr.g0[2] - amin[2];
+                size_t wi = ((size_t)w0 * wd[1] + w1) * wd[2] + w2;
+                for (int t = t0; t <= t1; ++t) need[wi * nmtile + t] = 1;
+            }
+        }
+        for (size_t wi = 0; wi < wvol; ++wi) {
+            bool any = false;
+            for (int t = 0; t < nmtile; ++t) any |= need[wi * nmtile + t] != 0;
+            if (!any) continue;
+            const int widx = (int)wxyz.size();
+            const int w2 = (int)(wi % wd[2]), w1 = (int)((wi / wd[2]) % wd[1]), w0 = (int)(wi / ((size_t)wd[1] * wd[2]));
+            wxyz.push_back(make_int4(w0 + amin[0], w1 + amin[1], w2 + amin[2], 0));
+            for (int t = 0; t < nmtile; ++t)
+                if (need[wi * nmtile + t])
+                    for (int b = 0; b < zb.nblk; ++b) tiles.push_back(ZTile{ik, widx, t * ZT_BM, b});
+        }
+    }
+    if (tiles.empty()) return HFX_OK;
+    // every B segment of every tile must be one whole z block inside the sliced T box
+    for (const int4 &W : wxyz) {
+        const int Z0 = W.z + zb.sz0 - zb.tlo[2], Z1 = W.z + zb.sz1 - zb.tlo[2];
+        if (W.x + zb.sx0 - zb.tlo[0] < 0 || W.x + zb.sx1 - zb.tlo[0] >= zb.tdim[0] || W.y + zb.sy0 - zb.tlo[1] < 0 ||
+            W.y + zb.sy1 - zb.tlo[1] >= zb.tdim[1] || Z0 < 0 || Z1 / ZT_SEGZ >= zb.nzb)
+            return set_err(ctx, HFX_EUNSUPPORTED, "interstitial segment outside the step-function box");
+    }
+    if (tiles.size() > (size_t)0x7fffffff) return set_err(ctx, HFX_EUNSUPPORTED, "interstitial tile list too long");
+    bt.o_gtab = tab.put(gtab);
+    bt.o_pinfo = tab.put(pinfo);
+    bt.o_w = tab.put(wxyz);
+    bt.o_tiles = tab.put(tiles);
+    bt.o_kslot = tab.put(kslot);
+    bt.ntiles = (int)tiles.size();
+    bt.nslot = (int)bks.size();
+    for (int x = 0; x < 3; ++x) { bt.amin[x] = amin[x]; bt.ad[x] = ad[x]; }
+    bt.tq_bytes = zb.tq_bytes_per_slot * bt.nslot;
+    bt.ok = true;
+    return HFX_OK;
+}
+
+// Per build: C slices of every row (k', m) and the band exponents of T_k.
+int zipw_tc_run_build(hfx_ctx *ctx, const ZipwBuild &zb, const char *dtab, char *dscr, const double2 *const *d_ck,
+                      const int *const *d_Gk, const int *d_npw, const double2 *const *d_Tk, const int *d_nb) {
+    if (!zb.ok) return HFX_OK;
+    cudaStream_t st = ctx->stream;
+    __nv_bfloat16 *A = reinterpret_cast<__nv_bfloat16 *>(dscr + zb.s_a);
+    int *aexp = reinterpret_cast<int *>(dscr + zb.s_aexp), *eT = reinterpret_cast<int *>(dscr + zb.s_eT);
+    cudaMemsetAsync(aexp, 0, (size_t)zb.Rpad * 4, st);
+    cudaMemsetAsync(A, 0, zb.a_elems * 2, st);
+    c_slices_kernel<<<zb.R, 256, 0, st>>>(d_ck, d_Gk, d_npw, reinterpret_cast<const int *>(dtab + zb.o_rowk),
+                                          reinterpret_cast<const int *>(dtab + zb.o_rowm),
+                                          reinterpret_cast<const int *>(dtab + zb.o_line), zb.gx0, zb.gy0, zb.By, zb.nL,
+                                          reinterpret_cast<const int *>(dtab + zb.o_sst),
+                                          reinterpret_cast<const int *>(dtab + zb.o_sz0), zb.Kp, zb.Rpad,
+                                          1.0 / sqrt(ctx->omega), A, aexp);
+    t_exp_kernel<<<dim3(zb.nb_max, ctx->nk), 256, 0, st>>>(d_Tk, d_nb, zb.tdim[0], zb.tdim[1], zb.tdim[2], zb.nb_max,
+                                                           reinterpret_cast<const int *>(dtab + zb.o_kall), eT);
+    return cuda_check(ctx, cudaGetLastError(), "zipw slices");
+}
+
+int zipw_tc_valid_nb(int nb) { return nb >= 8 && nb <= 40 && nb % 8 == 0; }
+
+// Per batch: T slices of the batch's k and the GEMM.
+int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, const char *dtab, const char *dscr,
+                      __nv_bfloat16 *dTq, const PairDesc *d_pairs, const double2 *const *d_Tk, const int *d_nb,
+                      double2 *d_Z, long long RSc, cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch) {
+    if (!zb.ok || !bt.ok) return HFX_OK;
     cudaStream_t st = ctx->stream;
     int rc;
-    const int nk = ctx->nk;
-    // every table below depends only on the structure of the inputs (plane-wave
-    // and aux lists, band windows, the batch's pairs): build and upload them
-    // once and reuse them while that structure and the scratch buffer stay
-    std::shared_ptr<ZipwPlan> plan = std::static_pointer_cast<ZipwPlan>(ctx->zipw_plan);
-    if (!plan) {
-        plan = std::make_shared<ZipwPlan>();
-        ctx->zipw_plan = plan;
-    }
-    const uint64_t sig = zipw_signature(ctx, in);
-    if (!(plan->valid && plan->sig == sig && plan->base == ctx->s_zipw.p)) {
-        plan->valid = false;
-        // ---- G1 lines (x, y) with their z ranges over every k' plane-wave list
-        int gmin[3] = {1 << 29, 1 << 29, 1 << 29}, gmax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
-        for (auto &k : ctx->kp)
-            for (size_t i = 0; i < k.G.size(); ++i) {
-                int x = i % 3;
-                gmin[x] = std::min(gmin[x], k.G[i]);
-                gmax[x] = std::max(gmax[x], k.G[i]);
-            }
-        if (gmin[0] > gmax[0]) return HFX_OK;
-        const int Bx = gmax[0] - gmin[0] + 1, By = gmax[1] - gmin[1] + 1;
-        std::vector<int> zlo((size_t)Bx * By, 1 << 29), zhi((size_t)Bx * By, -(1 << 29));
-        for (auto &k : ctx->kp)
-            for (size_t i = 0; i + 2 < k.G.size(); i += 3) {
-                size_t b = (size_t)(k.G[i] - gmin[0]) * By + (k.G[i + 1] - gmin[1]);
-                zlo[b] = std::min(zlo[b], k.G[i + 2]);
-                zhi[b] = std::max(zhi[b], k.G[i + 2]);
-            }
-        std::vector<int> line_of((size_t)Bx * By, -1), lx, ly, lzlo, lzhi;
-        for (int x = 0; x < Bx; ++x)
-            for (int y = 0; y < By; ++y) {
-                size_t b = (size_t)x * By + y;
-                if (zlo[b] > zhi[b]) continue;
-                line_of[b] = (int)lx.size();
-                lx.push_back(gmin[0] + x);
-                ly.push_back(gmin[1] + y);
-                lzlo.push_back(zlo[b]);
-                lzhi.push_back(zhi[b]);
-            }
-        const int nL = (int)lx.size();
-        // ---- rows (k', m): k' in Morton order of their mesh indices, so that a
-        // 128-row tile holds a compact block of the mesh (overlapping spheres)
-        const int *Mh = ctx->sys.mesh;
-        auto morton = [&](int ik) {
-            const int j[3] = {ik / (Mh[1] * Mh[2]), (ik / Mh[2]) % Mh[1], ik % Mh[2]};
-            unsigned long long code = 0;
-            for (int bit = 0; bit < 20; ++bit)
-                for (int x = 0; x < 3; ++x) code |= (unsigned long long)((j[x] >> bit) & 1) << (3 * bit + 2 - x);
-            return code;
-        };
-        std::vector<int> korder(nk);
-        for (int i = 0; i < nk; ++i) korder[i] = i;
-        std::stable_sort(korder.begin(), korder.end(), [&](int a, int b2) { return morton(a) < morton(b2); });
-        std::vector<int> rowk, rowm, rowbase(nk, -1);
-        for (int kp : korder) {
-            rowbase[kp] = (int)rowk.size();
-            for (int m = 0; m < ctx->kp[kp].no; ++m) { rowk.push_back(kp); rowm.push_back(m); }
-        }
-        const int R = (int)rowk.size();
-        if (R == 0) return HFX_OK;
-        const int Rpad = (R + ZT_BM - 1) / ZT_BM * ZT_BM;
-        const int nmtile = Rpad / ZT_BM;
-        std::vector<std::vector<int>> tile_k(nmtile);
-        for (int r = 0; r < R; ++r)
-            if (tile_k[r / ZT_BM].empty() || tile_k[r / ZT_BM].back() != rowk[r]) tile_k[r / ZT_BM].push_back(rowk[r]);
-        // segment grid per row tile: the lines of the tile's spheres, each cut
-        // into segments of ZT_SEGZ z values from its lowest z
-        std::vector<int> segstart((size_t)nmtile * nL, 0), segz0((size_t)nmtile * nL, 0), nseg(nmtile);
-        std::vector<std::vector<int4>> segs(nmtile);
-        std::vector<int> tzlo(nL), tzhi(nL);
-        for (int t = 0; t < nmtile; ++t) {
-            std::fill(tzlo.begin(), tzlo.end(), 1 << 29);
-            std::fill(tzhi.begin(), tzhi.end(), -(1 << 29));
-            for (int kp : tile_k[t]) {
-                const std::vector<int> &G = ctx->kp[kp].G;
-                for (size_t i = 0; i + 2 < G.size(); i += 3) {
-                    int l = line_of[(size_t)(G[i] - gmin[0]) * By + (G[i + 1] - gmin[1])];
-                    tzlo[l] = std::min(tzlo[l], G[i + 2]);
-                    tzhi[l] = std::max(tzhi[l], G[i + 2]);
-                }
-            }
-            for (int l = 0; l < nL; ++l) {
-                if (tzlo[l] > tzhi[l]) continue;
-                segstart[(size_t)t * nL + l] = (int)segs[t].size();
-                segz0[(size_t)t * nL + l] = tzlo[l];
-                for (int z = tzlo[l]; z <= tzhi[l]; z += ZT_SEGZ) segs[t].push_back(make_int4(lx[l], ly[l], z, 0));
-            }
-            if (segs[t].empty()) segs[t].push_back(make_int4(lx[0], ly[0], lzlo[0], 0));
-            nseg[t] = (int)segs[t].size();
-        }
-        int nsegp_max = 0;
-        for (int t = 0; t < nmtile; ++t) nsegp_max = std::max(nsegp_max, (nseg[t] + 7) / 8 * 8);
-        const int Kp = nsegp_max * 8;   // K values of an A row: 8 per segment
-        const int nzb = (in.tdim[2] + ZT_SEGZ - 1) / ZT_SEGZ;
-        // every segment: (x td1 + y) of its line and its z0, offsets from the tile
-        // shift (W_x - tlo_x) td1 + (W_y - tlo_y) and W_z - tlo_z
-        std::vector<int2> segtab((size_t)nmtile * nsegp_max);
-        std::vector<int> nchunk(nmtile);
-        for (int t = 0; t < nmtile; ++t) {
-            nchunk[t] = (nseg[t] + 7) / 8;
-            for (int s2 = 0; s2 < nsegp_max; ++s2) {
-                const int4 sg = s2 < nseg[t] ? segs[t][s2] : segs[t][0];   // padding: any valid block
-                segtab[(size_t)t * nsegp_max + s2] = make_int2(sg.x * in.tdim[1] + sg.y, sg.z);
-            }
-        }
-        const int NBt = pick_nb(in.nb_max);
-        const int nblk = (in.nb_max + NBt - 1) / NBt;
-        // bulk-copy runs per 64-K chunk: consecutive segments of one line are
-        // consecutive z blocks of T, contiguous for a single band block
-        std::vector<int> runs((size_t)nmtile * (nsegp_max / 8), 0);
-        for (int t = 0; t < nmtile; ++t)
-            for (int c = 0; c < nsegp_max / 8; ++c) {
-                const int live = std::max(0, std::min(8, nseg[t] - 8 * c));
-                int starts = 0;
-                for (int j = 0; j < live; ++j) {
-                    const int s2 = 8 * c + j;
-                    const bool cont = j > 0 && nblk == 1 && segs[t][s2].x == segs[t][s2 - 1].x &&
-                                      segs[t][s2].y == segs[t][s2 - 1].y && segs[t][s2].z == segs[t][s2 - 1].z + ZT_SEGZ;
-                    if (!cont) starts |= 1 << j;
-                }
-                runs[(size_t)t * (nsegp_max / 8) + c] = starts | (live << 8);
-            }
-        // ---- aux lookup tables over the batch's q
-        int amin[3] = {1 << 29, 1 << 29, 1 << 29}, amax[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
-        for (int iq : in.qs)
-            for (size_t i = 0; i < ctx->qp[iq].G.size(); ++i) {
-                int x = i % 3;
-                amin[x] = std::min(amin[x], ctx->qp[iq].G[i]);
-                amax[x] = std::max(amax[x], ctx->qp[iq].G[i]);
-            }
-        int ad[3];
-        for (int x = 0; x < 3; ++x) {
-            if (amin[x] > amax[x]) amin[x] = amax[x] = 0;
-            ad[x] = amax[x] - amin[x] + 1;
-        }
-        const int nq = (int)in.qs.size();
-        std::vector<int> gtab((size_t)nq * ad[0] * ad[1] * ad[2], -1);
-        for (int s = 0; s < nq; ++s) {
-            const std::vector<int> &G = ctx->qp[in.qs[s]].G;
-            for (size_t g = 0; g < G.size() / 3; ++g)
-                gtab[(((size_t)s * ad[0] + (G[3 * g] - amin[0])) * ad[1] + (G[3 * g + 1] - amin[1])) * ad[2] + (G[3 * g + 2] - amin[2])] = (int)g;
-        }
-        // ---- pair info (k, k') and the shift lists / tiles per k
-        std::vector<ZPairInfo> pinfo((size_t)nk * nk, ZPairInfo{-1, 0, 0, 0});
-        for (int i = 0; i < (int)in.pairs.size(); ++i) {
-            const PairDesc &pr = in.pairs[i];
-            pinfo[(size_t)pr.ik * nk + pr.ikp] = ZPairInfo{i, pr.g0[0], pr.g0[1], pr.g0[2]};
-        }
-        // W = G - G0 lies in [amin, amax + 1]
-        const int wd[3] = {ad[0] + 1, ad[1] + 1, ad[2] + 1};
-        const size_t wvol = (size_t)wd[0] * wd[1] * wd[2];
-        std::vector<int4> wxyz;
-        std::vector<ZTile> tiles;
-        std::vector<unsigned char> need;
-        std::vector<int> kslot(nk, -1);
-        int nslot = 0;
-        for (int ik : in.kset) {
-            kslot[ik] = nslot++;
-            need.assign(wvol * nmtile, 0);
-            for (const PairDesc &pr : in.pairs) {
-                if (pr.ik != ik || pr.no == 0) continue;
-                const std::vector<int> &G = ctx->qp[pr.iq].G;
-                const int t0 = rowbase[pr.ikp] / ZT_BM, t1 = (rowbase[pr.ikp] + pr.no - 1) / ZT_BM;
-                for (size_t g = 0; g < G.size() / 3; ++g) {
-                    int w0 = G[3 * g] - pr.g0[0] - amin[0], w1 = G[3 * g + 1] - pr.g0[1] - amin[1], w2 = G[3 * g + 2] - pr.g0[2] - amin[2];
-                    size_t wi = ((size_t)w0 * wd[1] + w1) * wd[2] + w2;
-                    for (int t = t0; t <= t1; ++t) need[wi * nmtile + t] = 1;
-                }
-            }
-            for (size_t wi = 0; wi < wvol; ++wi) {
-                bool any = false;
-                for (int t = 0; t < nmtile; ++t) any |= need[wi * nmtile + t] != 0;
-                if (!any) continue;
-                const int widx = (int)wxyz.size();
-                const int w2 = (int)(wi % wd[2]), w1 = (int)((wi / wd[2]) % wd[1]), w0 = (int)(wi / ((size_t)wd[1] * wd[2]));
-                wxyz.push_back(make_int4(w0 + amin[0], w1 + amin[1], w2 + amin[2], 0));
-                for (int t = 0; t < nmtile; ++t)
-                    if (need[wi * nmtile + t])
-                        for (int b = 0; b < nblk; ++b) tiles.push_back(ZTile{ik, widx, t * ZT_BM, b});
-            }
-        }
-        if (tiles.empty()) return HFX_OK;
-        // tiles stay k-major: T of one k and the C slices (4 planes x 512 rows x
-        // Kp values) stay in L2 while the CTAs sweep that k's shifts
-        {
-            // every B segment of every tile must be one whole z block inside the sliced T box
-            int sx0 = 1 << 29, sx1 = -(1 << 29), sy0 = 1 << 29, sy1 = -(1 << 29), sz0 = 1 << 29, sz1 = -(1 << 29);
-            for (int t = 0; t < nmtile; ++t)
-                for (const int4 &sg : segs[t]) {
-                    sx0 = std::min(sx0, sg.x); sx1 = std::max(sx1, sg.x);
-                    sy0 = std::min(sy0, sg.y); sy1 = std::max(sy1, sg.y);
-                    sz0 = std::min(sz0, sg.z); sz1 = std::max(sz1, sg.z);
-                }
-            for (const int4 &W : wxyz) {
-                const int Z0 = W.z + sz0 - in.tlo[2], Z1 = W.z + sz1 - in.tlo[2];
-                if (W.x + sx0 - in.tlo[0] < 0 || W.x + sx1 - in.tlo[0] >= in.tdim[0] || W.y + sy0 - in.tlo[1] < 0 ||
-                    W.y + sy1 - in.tlo[1] >= in.tdim[1] || Z0 < 0 || Z1 / ZT_SEGZ >= nzb)
-                    return set_err(ctx, HFX_EUNSUPPORTED, "interstitial segment outside the step-function box");
-            }
-        }
-        // ---- device buffers (scratch s_zipw)
-        const int nbpad = nblk * NBt;
-        const size_t tp_elems = (size_t)ZT_NCOPY * nslot * in.tdim[0] * in.tdim[1] * nzb * NPL * 2 * nbpad * 8;
-        const size_t a_elems = (size_t)NPL * Rpad * Kp;
-        size_t off = 0;
-        auto place = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
-        const size_t o_tp = place(tp_elems * 2), o_a = place(a_elems * 2), o_aexp = place((size_t)Rpad * 4),
-                     o_eT = place((size_t)nk * in.nb_max * 4), o_rowk = place((size_t)R * 4), o_rowm = place((size_t)R * 4),
-                     o_line = place(line_of.size() * 4), o_sst = place(segstart.size() * 4), o_sz0 = place(segz0.size() * 4),
-                     o_seg = place(segtab.size() * sizeof(int2)), o_gtab = place(gtab.size() * 4),
-                     o_pinfo = place(pinfo.size() * sizeof(ZPairInfo)), o_w = place(wxyz.size() * sizeof(int4)),
-                     o_tiles = place(tiles.size() * sizeof(ZTile)), o_kslot = place((size_t)nk * 4),
-                     o_nch = place(nchunk.size() * 4), o_runs = place(runs.size() * 4);
-        if ((rc = scratch_reserve(ctx, ctx->s_zipw, off))) return rc;
-        char *b = reinterpret_cast<char *>(ctx->s_zipw.p);
-        auto up = [&](size_t o, const void *src, size_t bytes) {
-            return cuda_check(ctx, cudaMemcpyAsync(b + o, src, bytes, cudaMemcpyHostToDevice, st), "zipw tables");
-        };
-        if ((rc = up(o_rowk, rowk.data(), R * 4)) || (rc = up(o_rowm, rowm.data(), R * 4)) ||
-            (rc = up(o_line, line_of.data(), line_of.size() * 4)) || (rc = up(o_sst, segstart.data(), segstart.size() * 4)) ||
-            (rc = up(o_sz0, segz0.data(), segz0.size() * 4)) || (rc = up(o_seg, segtab.data(), segtab.size() * sizeof(int2))) ||
-            (rc = up(o_gtab, gtab.data(), gtab.size() * 4)) ||
-            (rc = up(o_pinfo, pinfo.data(), pinfo.size() * sizeof(ZPairInfo))) ||
-            (rc = up(o_w, wxyz.data(), wxyz.size() * sizeof(int4))) ||
-            (rc = up(o_tiles, tiles.data(), tiles.size() * sizeof(ZTile))) || (rc = up(o_kslot, kslot.data(), nk * 4)) ||
-            (rc = up(o_nch, nchunk.data(), nchunk.size() * 4)) || (rc = up(o_runs, runs.data(), runs.size() * 4)))
-            return rc;
-        ZParams &p = plan->p;
-        p.tiles = reinterpret_cast<ZTile *>(b + o_tiles);
-        p.ntiles = (int)tiles.size();
-        p.wxyz = reinterpret_cast<int4 *>(b + o_w);
-        p.pinfo = reinterpret_cast<ZPairInfo *>(b + o_pinfo);
-        p.pairs = in.d_pairs;
-        p.gtab = reinterpret_cast<int *>(b + o_gtab);
-        p.ax0 = amin[0]; p.ay0 = amin[1]; p.az0 = amin[2];
-        p.ad0 = ad[0]; p.ad1 = ad[1]; p.ad2 = ad[2];
-        p.rowk = reinterpret_cast<int *>(b + o_rowk);
-        p.rowm = reinterpret_cast<int *>(b + o_rowm);
-        p.aexp = reinterpret_cast<int *>(b + o_aexp);
-        p.eT = reinterpret_cast<int *>(b + o_eT);
-        p.kslot = reinterpret_cast<int *>(b + o_kslot);
-        p.segoff = reinterpret_cast<int2 *>(b + o_seg);
-        p.nsegp_max = nsegp_max;
-        p.Tq = reinterpret_cast<__nv_bfloat16 *>(b + o_tp);
-        p.td0 = in.tdim[0];
-        p.td1 = in.tdim[1];
-        p.nzb = nzb;
-        p.nblk = nblk;
-        p.nslot = nslot;
-        p.nchunk = reinterpret_cast<int *>(b + o_nch);
-        p.runs = reinterpret_cast<int *>(b + o_runs);
-        p.Z = in.d_Z;
-        p.RSc = in.RSc;
-        p.nmt = ctx->nmt;
-        p.nk = nk;
-        p.R = R;
-        p.Rpad = Rpad;
-        p.nbmax = in.nb_max;
-        p.tlo0 = in.tlo[0]; p.tlo1 = in.tlo[1]; p.tlo2 = in.tlo[2];
-        p.rs = 1.0 / sqrt(ctx->omega);
-        p.err = ctx->d_err;
-            plan->o_rowk = o_rowk; plan->o_rowm = o_rowm; plan->o_line = o_line; plan->o_sst = o_sst; plan->o_sz0 = o_sz0;
-            plan->o_tp = o_tp; plan->o_a = o_a; plan->o_aexp = o_aexp; plan->o_eT = o_eT; plan->o_kslot = o_kslot;
-            plan->a_elems = a_elems;
-            plan->R = R; plan->Rpad = Rpad; plan->nzb = nzb; plan->NBt = NBt; plan->nblk = nblk; plan->nbpad = nbpad;
-            plan->nslot = nslot; plan->Kp = Kp; plan->nL = nL; plan->gx0 = gmin[0]; plan->gy0 = gmin[1]; plan->By = By;
-        plan->nmtile = nmtile;
-            plan->sig = sig;
-            plan->base = ctx->s_zipw.p;
-            plan->valid = true;
-    }
-    const ZipwPlan &P = *plan;
-    char *b = reinterpret_cast<char *>(ctx->s_zipw.p);
-    __nv_bfloat16 *Tp = reinterpret_cast<__nv_bfloat16 *>(b + P.o_tp), *A = reinterpret_cast<__nv_bfloat16 *>(b + P.o_a);
-    int *aexp = reinterpret_cast<int *>(b + P.o_aexp), *eT = reinterpret_cast<int *>(b + P.o_eT);
-    cudaMemsetAsync(aexp, 0, (size_t)P.Rpad * 4, st);
-    cudaMemsetAsync(A, 0, P.a_elems * 2, st);
-    c_slices_kernel<<<P.R, 256, 0, st>>>(in.d_ck, in.d_Gk, in.d_npw, reinterpret_cast<int *>(b + P.o_rowk),
-                                         reinterpret_cast<int *>(b + P.o_rowm), reinterpret_cast<int *>(b + P.o_line), P.gx0,
-                                         P.gy0, P.By, P.nL, reinterpret_cast<int *>(b + P.o_sst),
-                                         reinterpret_cast<int *>(b + P.o_sz0),
-                                         P.Kp, P.Rpad, P.p.rs, A, aexp);
-    t_exp_kernel<<<dim3(in.nb_max, nk), 256, 0, st>>>(in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], in.nb_max,
-                                                      reinterpret_cast<int *>(b + P.o_kslot), eT);
+    const int *kslot = reinterpret_cast<const int *>(dtab + bt.o_kslot);
     {
-        const long long nthreads = (long long)in.tdim[0] * in.tdim[1] * P.nzb * P.nbpad;
-        t_slices_kernel<<<dim3((unsigned)((nthreads + 255) / 256), nk), 256, 0, st>>>(
-            in.d_Tk, in.d_nb, in.tdim[0], in.tdim[1], in.tdim[2], P.nzb, P.NBt, P.nblk, in.nb_max, P.nslot,
-            reinterpret_cast<int *>(b + P.o_kslot), eT, Tp);
+        const long long nthreads = (long long)zb.tdim[0] * zb.tdim[1] * zb.nzb * zb.nbpad;
+        t_slices_kernel<<<dim3((unsigned)((nthreads + 255) / 256), ctx->nk), 256, 0, st>>>(
+            d_Tk, d_nb, zb.tdim[0], zb.tdim[1], zb.tdim[2], zb.nzb, zb.NBt, zb.nblk, zb.nb_max, bt.nslot, kslot,
+            reinterpret_cast<const int *>(dscr + zb.s_eT), dTq);
     }
-    if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw slices"))) return rc;
-    // ---- tensor maps and launch
+    if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw T slices"))) return rc;
     CUtensorMap mA;
-    if ((rc = make_map_2d(ctx, &mA, A, (long long)NPL * P.Rpad, P.Kp, ZT_BM))) return rc;
-    ZParams p = P.p;   // per-call pointers: the batch's pairs and projections, the error word
-    p.pairs = in.d_pairs;
-    p.Z = in.d_Z;
-    p.RSc = in.RSc;
+    if ((rc = make_map_2d(ctx, &mA, dscr + zb.s_a, (long long)NPL * zb.Rpad, zb.Kp, ZT_BM))) return rc;
+    ZParams p;
+    p.tiles = reinterpret_cast<const ZTile *>(dtab + bt.o_tiles);
+    p.ntiles = bt.ntiles;
+    p.wxyz = reinterpret_cast<const int4 *>(dtab + bt.o_w);
+    p.pinfo = reinterpret_cast<const ZPairInfo *>(dtab + bt.o_pinfo);
+    p.pairs = d_pairs;
+    p.gtab = reinterpret_cast<const int *>(dtab + bt.o_gtab);
+    p.ax0 = bt.amin[0]; p.ay0 = bt.amin[1]; p.az0 = bt.amin[2];
+    p.ad0 = bt.ad[0]; p.ad1 = bt.ad[1]; p.ad2 = bt.ad[2];
+    p.rowk = reinterpret_cast<const int *>(dtab + zb.o_rowk);
+    p.rowm = reinterpret_cast<const int *>(dtab + zb.o_rowm);
+    p.aexp = reinterpret_cast<const int *>(dscr + zb.s_aexp);
+    p.eT = reinterpret_cast<const int *>(dscr + zb.s_eT);
+    p.kslot = kslot;
+    p.segoff = reinterpret_cast<const int2 *>(dtab + zb.o_seg);
+    p.nsegp_max = zb.nsegp_max;
+    p.nchunk = reinterpret_cast<const int *>(dtab + zb.o_nch);
+    p.runs = reinterpret_cast<const int *>(dtab + zb.o_runs);
+    p.Tq = dTq;
+    p.td0 = zb.tdim[0];
+    p.td1 = zb.tdim[1];
+    p.nzb = zb.nzb;
+    p.nblk = zb.nblk;
+    p.nslot = bt.nslot;
+    p.Z = d_Z;
+    p.RSc = RSc;
+    p.nmt = ctx->nmt;
+    p.nk = ctx->nk;
+    p.R = zb.R;
+    p.Rpad = zb.Rpad;
+    p.nbmax = zb.nb_max;
+    p.tlo0 = zb.tlo[0]; p.tlo1 = zb.tlo[1]; p.tlo2 = zb.tlo[2];
+    p.rs = 1.0 / sqrt(ctx->omega);
     p.err = ctx->d_err;
-    const int NBt = P.NBt;
     const int grid = std::min<int>(num_sms(), p.ntiles);
     // the whole opt-in shared memory: the pipeline stages plus a guard region
     // past the last stage that no descriptor of the B operand can reach beyond
@@ -798,17 +776,18 @@ int zipw_tc_prepare_and_launch(hfx_ctx *ctx, const ZipwTcInput &in) {
         size_t smem = std::max<size_t>((size_t)ZT_STAGES * (NPL * ZT_A_PLANE + 8 * NPL * 2 * nb * 16) + 1024,
                                        (size_t)smem_max - fa.sharedSizeBytes);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (in.ev_gemm0) cudaEventRecord(in.ev_gemm0, st);
+        if (ev0) record_event(ev0, st);
         kern<<<grid, 64 + 32 * ZT_EPI, smem, st>>>(mA, p);
-        if (in.ev_gemm1) cudaEventRecord(in.ev_gemm1, st);
+        if (ev1) record_event(ev1, st);
     };
-    switch (NBt) {
+    switch (zb.NBt) {
     case 8: go(zipw_tc_kernel<8>, 8); break;
     case 16: go(zipw_tc_kernel<16>, 16); break;
     case 24: go(zipw_tc_kernel<24>, 24); break;
     case 32: go(zipw_tc_kernel<32>, 32); break;
     default: go(zipw_tc_kernel<40>, 40); break;
     }
+    if (nlaunch) *nlaunch += 2;
     return cuda_check(ctx, cudaGetLastError(), "zipw tensor-core kernel");
 }
 

@@ -56,6 +56,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
         }
     }
 }
+// Bounded wait on a barrier that nothing completes, for the fault-injection
+// hook of the tests: gives up after ns nanoseconds like mbar_wait does.
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err,
+                                             int code, unsigned long long ns) {
+    unsigned long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > ns) {
+            *abort_flag = 1;
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
 // Best-effort bounded wait used only while draining after an abort.
 __device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
     unsigned long long t0 = gtimer();
@@ -70,36 +85,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
             "r"(dst),
         "l"((uint64_t)map), "r"(saddr(bar)), "r"(x), "r"(y)
         : "memory");
-}
-
-// ------------------------------------------------------------- clusters
-// TMA multicast and tcgen05.commit multicast reach the CTAs of this CTA's
-// cluster only (the GPU's own memory; nothing leaves the device).
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// 2-D tile load written to the same shared-memory offset of every CTA in mask,
-// completing bytes on the mbarrier at the same offset in each of them
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%3, "
-        "%4}], [%2], %5;" ::"r"(dst),
-        "l"((uint64_t)map), "r"(saddr(bar)), "r"(x), "r"(y), "h"(mask)
-        : "memory");
-}
-// arrive once on the mbarrier at this offset in every CTA of mask when the
-// tcgen05 operations issued so far have completed
-__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                     saddr(bar)),
-                 "h"(mask)
-                 : "memory");
 }
 
 // 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16)
@@ -130,6 +115,15 @@ __device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, ui
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
                  : "memory");
+}
+
+// The MMA thread's last step: wait (bounded) until every tcgen05.mma it issued
+// has completed, so that TMEM is never freed under an MMA still in flight
+// (after an abort nothing else waits for them).  bar: an mbarrier of count 1
+// used for nothing else.
+__device__ __forceinline__ void umma_drain(uint64_t *bar) {
+    umma_commit(bar);
+    mbar_drain(bar, 0);
 }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {

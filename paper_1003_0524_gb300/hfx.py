@@ -28,12 +28,13 @@ HFX_EUNSUPPORTED = -9
 HFX_PREC_FP64 = 0
 HFX_PREC_SLICED = 1
 HFX_SPARSE_AUTO, HFX_SPARSE_ON, HFX_SPARSE_OFF = 0, 1, 2
+HFX_LAYOUT_DENSE, HFX_LAYOUT_TRANSFORMED = 0, 1
 
 EXPORTS = (
     "hfx_default_options", "hfx_create", "hfx_set_radial", "hfx_set_kpoint", "hfx_set_coulomb",
     "hfx_set_products", "hfx_get_products", "hfx_build_all", "hfx_build_exchange", "hfx_get_exchange",
     "hfx_exchange_device_ptr", "hfx_get_energy", "hfx_get_q0_bracket", "hfx_destroy", "hfx_strerror",
-    "hfx_last_error", "hfx_version", "hfx_q0_bracket_noalloc",
+    "hfx_last_error", "hfx_version", "hfx_q0_bracket_noalloc", "hfx_get_transform",
 )
 
 
@@ -67,6 +68,10 @@ class hfx_options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("device", ctypes.c_int),
         ("work_bytes", ctypes.c_size_t),
+        ("use_graph", ctypes.c_int),
+        ("tile_nb_zhy", ctypes.c_int),
+        ("tile_nb_zipw", ctypes.c_int),
+        ("test_fail_wait", ctypes.c_int),
     ]
 
 
@@ -87,6 +92,9 @@ class hfx_stats(ctypes.Structure):
         ("flops_apply", ctypes.c_double),
         ("flops_zhy", ctypes.c_double),
         ("flops_zipw", ctypes.c_double),
+        ("graph_replayed", ctypes.c_int),
+        ("tile_nb_zhy", ctypes.c_int),
+        ("tile_nb_zipw", ctypes.c_int),
     ]
 
 
@@ -120,7 +128,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.hfx_set_kpoint.restype = ip
     L.hfx_set_kpoint.argtypes = [vp, ip, ip, ip, ip, vp, vp, vp]
     L.hfx_set_coulomb.restype = ip
-    L.hfx_set_coulomb.argtypes = [vp, ip, ip, vp, vp]
+    L.hfx_set_coulomb.argtypes = [vp, ip, ip, vp, vp, ip, ip]
+    L.hfx_get_transform.restype = ip
+    L.hfx_get_transform.argtypes = [vp, ip, ip, vp]
     L.hfx_set_products.restype = ip
     L.hfx_set_products.argtypes = [vp, ip, ip, vp]
     L.hfx_get_products.restype = ip
@@ -204,11 +214,20 @@ def hfx_set_kpoint(ctx, ik: int, n_bands: int, n_occ: int, G, c, A):
                                       c.ctypes.data, A.ctypes.data))
 
 
-def hfx_set_coulomb(ctx, iq: int, G_aux, v):
+def hfx_set_coulomb(ctx, iq: int, G_aux, v, ld: Optional[int] = None, layout: int = HFX_LAYOUT_DENSE):
+    """v: (N_aux, N_aux) complex, or a (N_aux, ld) array whose first N_aux
+    columns hold the matrix (row stride ld)."""
     G = _c(G_aux, np.int32).reshape(-1, 3)
     v = _c(v, np.complex128)
+    ld = int(v.shape[1]) if ld is None else int(ld)
     _check(ctx, load().hfx_set_coulomb(ctx, int(iq), int(G.shape[0]), G.ctypes.data if G.size else None,
-                                       v.ctypes.data))
+                                       v.ctypes.data, ld, int(layout)))
+
+
+def hfx_get_transform(ctx, atom: int, L: int, P: int) -> np.ndarray:
+    out = np.zeros((P, P), np.float64)
+    _check(ctx, load().hfx_get_transform(ctx, int(atom), int(L), out.ctypes.data))
+    return out
 
 
 def hfx_set_products(ctx, ik: int, iq: int, Z):
@@ -287,7 +306,8 @@ class Context:
     """One exchange-matrix context bound to a system from ``synthetic``."""
 
     def __init__(self, sysm, precision: str = "sliced", sparse: str = "auto", q0_term: bool = True,
-                 beta: float = 0.005, stream: Optional[int] = None, device: int = 0, work_bytes: int = 0):
+                 beta: float = 0.005, stream: Optional[int] = None, device: int = 0, work_bytes: int = 0,
+                 use_graph: bool = True, tile_nb_zhy: int = 0, tile_nb_zipw: int = 0, test_fail_wait: bool = False):
         opt = hfx_default_options()
         opt.precision = {"fp64": HFX_PREC_FP64, "sliced": HFX_PREC_SLICED}[precision]
         opt.sparse = {"auto": HFX_SPARSE_AUTO, "on": HFX_SPARSE_ON, "off": HFX_SPARSE_OFF}[sparse]
@@ -296,6 +316,10 @@ class Context:
         opt.stream = stream
         opt.device = int(device)
         opt.work_bytes = int(work_bytes)
+        opt.use_graph = int(bool(use_graph))
+        opt.tile_nb_zhy = int(tile_nb_zhy)
+        opt.tile_nb_zipw = int(tile_nb_zipw)
+        opt.test_fail_wait = int(bool(test_fail_wait))
         self.sys = sysm
         self.ctx = hfx_create(sysm.lattice, sysm.pos_frac, sysm.rmt, sysm.lmax, sysm.Lmax, sysm.P, sysm.mesh, opt)
 

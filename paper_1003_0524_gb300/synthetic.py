@@ -356,14 +356,14 @@ def make_system(cfg: int | dict, *, seed: Optional[int] = None, mesh=None, nb=No
                     vt[base + 1:base + P, base + 1:base + P] = bc
                     vt[base + 1:base + P, base] = cc
                     vt[base, base + 1:base + P] = cc.conj()
-        # back to the original basis: v = Q^T v_t Q, Q block-diagonal per (a,L,M)
-        Q = np.eye(n_aux)
-        for a in range(n_at):
-            for lm in range(nlm_aux):
-                L = int(math.isqrt(lm))
-                base = (a * nlm_aux + lm) * P
-                Q[base:base + P, base:base + P] = frames[a][L]
-        vq = Q.T @ vt @ Q
+        # back to the original basis: v = Q^T v_t Q with Q block-diagonal, one
+        # frame per (a,L,M) block of the MT rows and the identity on the IPW
+        # rows; applied block by block (rows, then columns)
+        Fb = np.stack([frames[a][int(math.isqrt(lm))] for a in range(n_at) for lm in range(nlm_aux)])
+        nblk = Fb.shape[0]
+        vq = vt.copy()
+        vq[:n_mt] = np.einsum("bji,bjc->bic", Fb, vq[:n_mt].reshape(nblk, P, n_aux)).reshape(n_mt, n_aux)
+        vq[:, :n_mt] = np.einsum("rbj,bji->rbi", vq[:, :n_mt].reshape(n_aux, nblk, P), Fb).reshape(n_aux, n_mt)
         v.append(0.5 * (vq + vq.conj().T))
 
     return System(name=str(spec["name"]), lattice=lattice, pos_frac=pos, rmt=rmt, lmax=lmax,

@@ -68,6 +68,16 @@ SMALL = {
     # mesh with narrow band windows, so that the oracle stays fast
     "cfg3_shape": lambda: S.make_system(3, mesh=(1, 1, 2), nb=12, no=4),
     "cfg4_shape": lambda: S.make_system(4, mesh=(1, 1, 2), nb=10, no=4),
+    # the same cells with 72 bands: two Z^H Y band blocks, L <= 5 and the
+    # dense block D ~ 2660 of config 4, D ~ 1225 of config 3
+    "cfg3_nb72": lambda: S.make_system(3, mesh=(1, 1, 2), nb=72, no=8),
+    "cfg4_nb72": lambda: S.make_system(4, mesh=(1, 1, 2), nb=72, no=8),
+    # the literal MT coefficient distribution A ~ CN(0, 1) (a_scale 1): the MT
+    # rows of Z (bilinear in A) then dwarf the interstitial rows of the same
+    # column by ~240x.  v is scaled down so that max|V| stays ~ 1 Ha (with the
+    # usual scale 24 max|V| is ~ 2.8e3 Ha on this case)
+    "cfg1_ascale1": lambda: S.make_system(dict(S.CONFIGS[1], a_scale=1.0, scale=1.5e-3),
+                                          mesh=(2, 2, 1), nb=8, no=4),
 }
 
 
@@ -94,6 +104,9 @@ def test_split_matches_oracle(name):
     assert err <= TOL_SPLIT_ABS, err
     for k in V:
         assert np.abs(V[k] - V[k].conj().T).max() <= 2 * TOL_SPLIT_ABS
+    # E_x = (1/2)(1/N_k) sum_k sum_{n < n_occ} Re V_nn, so |dE_x| is at most
+    # (1/2) max_k n_occ(k) times the bar on |dV|
+    assert abs(ex - ex_ref) <= 0.5 * int(max(s.n_occ)) * TOL_SPLIT_ABS, ex - ex_ref
 
 
 # In the sliced build every projection is a slice product: each operand line
@@ -236,3 +249,99 @@ def test_full_size_workload_sampled_k():
     for k in V:
         assert np.abs(V[k] - V[k].conj().T).max() <= 2 * TOL_SPLIT_ABS
     assert st["n_pairs"] == 64 * 64
+
+
+def test_many_batches_split_every_q():
+    """A work budget far below the working set: the pairs are cut k-major into
+    at least three batches, so the k points of every q fall into several
+    batches (the path that configurations too large for one batch take)."""
+    s = S.make_system(1, mesh=(2, 2, 2), nb=12, no=4)
+    ref = oracle_v("cfg1_k2_nb12", s, range(s.n_k))
+    for prec, tol in (("fp64", TOL_FP64_REL * vmax(ref)), ("sliced", TOL_SPLIT_ABS)):
+        V, ex, st = gpu_v(s, prec, work_bytes=24 << 20)
+        print(f"{prec}: {st['n_batches']} batches, max|dV| = {max_err(V, ref):.3e}")
+        assert st["n_batches"] >= 3
+        assert st["n_pairs"] == s.n_k * s.n_k
+        assert max_err(V, ref) <= tol
+        ex_ref = O.exchange_energy(s, ref)
+        assert abs(ex - ex_ref) <= 0.5 * int(max(s.n_occ)) * tol
+
+
+def test_graph_replay_is_identical():
+    """The first build runs its launches directly, the second captures them as
+    one CUDA graph and the third replays it: all three give the same bits, and
+    so does a context that never captures."""
+    s = S.make_system(1, mesh=(2, 2, 2), nb=10, no=4)
+    with hfx.Context(s, precision="sliced") as c:
+        c.load_system()
+        runs = []
+        for _ in range(3):
+            st = c.build_all()
+            runs.append(({ik: c.exchange(ik) for ik in range(s.n_k)}, st))
+        assert runs[0][1]["graph_replayed"] == 0 and runs[2][1]["graph_replayed"] == 1
+        assert runs[2][1]["n_launches"] == runs[0][1]["n_launches"]
+        for V, _ in runs[1:]:
+            for k in V:
+                assert np.array_equal(V[k], runs[0][0][k])
+    V2, _, st2 = gpu_v(s, "sliced", use_graph=False)
+    for k in V2:
+        assert np.array_equal(V2[k], runs[0][0][k])
+
+
+def _transformed(c, s, v):
+    """T v T^T with the context's own multipole transforms (Sec. III.C)."""
+    nlm = (s.Lmax + 1) ** 2
+    Q = np.eye(v.shape[0])
+    for a in range(s.n_atoms):
+        for L in range(s.Lmax + 1):
+            T = hfx.hfx_get_transform(c.ctx, a, L, s.P)
+            for M in range(2 * L + 1):
+                b = (a * nlm + L * L + M) * s.P
+                Q[b:b + s.P, b:b + s.P] = T
+    return Q @ v @ Q.T
+
+
+@pytest.mark.parametrize("precision", ["fp64", "sliced"])
+def test_coulomb_given_transformed_matches_dense(precision):
+    """hfx_set_coulomb with the layout TRANSFORMED (v_t = T v T^T, Fig. 1),
+    passed with a row stride larger than N_aux, gives the V^x of the dense
+    layout: 1e-12 relative in FP64, 1e-8 Ha in the sliced build."""
+    s = S.make_system(1, mesh=(2, 2, 1), nb=8, no=3)
+    Vd, _, _ = gpu_v(s, precision)
+    with hfx.Context(s, precision=precision) as c:
+        c.load_system(coulomb=False)
+        for a in range(s.n_atoms):
+            for L in range(s.Lmax + 1):
+                T = hfx.hfx_get_transform(c.ctx, a, L, s.P)
+                assert np.abs(T @ T.T - np.eye(s.P)).max() <= 1e-14
+                mu = s.mu[a, L * s.P:(L + 1) * s.P]
+                assert np.abs(T[0] - mu / np.linalg.norm(mu)).max() <= 1e-15
+        for iq in range(s.n_k):
+            vt = _transformed(c, s, s.v[iq])
+            n = vt.shape[0]
+            padded = np.zeros((n, n + 5), np.complex128)
+            padded[:, :n] = vt
+            hfx.hfx_set_coulomb(c.ctx, iq, s.Gaux[iq], padded, ld=n + 5, layout=hfx.HFX_LAYOUT_TRANSFORMED)
+        st = c.build_all()
+        assert st["sparse_used"] == 1
+        Vt = {ik: c.exchange(ik) for ik in range(s.n_k)}
+    tol = 1e-12 * vmax(Vd) if precision == "fp64" else TOL_SPLIT_ABS
+    assert max_err(Vt, Vd) <= tol
+
+
+def test_expired_device_wait_is_reported_and_recovered():
+    """Failure detection without a GPU fault: the test hook makes one bounded
+    wait of the Z^H Y kernel wait on a barrier that nothing completes.  The
+    wait expires after about 1 ms, the kernel drains its copies and MMAs,
+    frees its TMEM and returns; the build reports HFX_ETIMEOUT.  The next
+    build on the same context is correct."""
+    s = S.make_system(0, nb=6, no=3)
+    ref = oracle_v("cfg0_nb6", s, range(s.n_k))
+    with hfx.Context(s, precision="sliced", test_fail_wait=True) as c:
+        c.load_system()
+        with pytest.raises(hfx.HfxError) as e:
+            c.build_all()
+        assert e.value.code == hfx.HFX_ETIMEOUT
+        c.build_all()
+        V = {ik: c.exchange(ik) for ik in range(s.n_k)}
+    assert max_err(V, ref) <= TOL_SPLIT_ABS
