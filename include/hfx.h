@@ -150,6 +150,10 @@ typedef struct {
     int graph_replayed;       /* 1 if the build was the replay of a captured CUDA graph */
     int tile_nb_zhy;          /* band block of the Z^H Y tiles used */
     int tile_nb_zipw;         /* band block of the interstitial tiles used (0: FP64 build) */
+    double flops_apply_exec;  /* flops of the dense-block apply as executed: the sliced
+                                 build applies the upper triangle U of v_t (half
+                                 diagonal) and adds P' + P'^H, 8 D (D+1)/2 per column;
+                                 the FP64 build applies all of v_t, 8 D^2 */
 } hfx_stats;
 
 /* ------------------------------------------------------------ entry points */

@@ -210,7 +210,8 @@ void launch_transform_v(const double2 *d_v, double2 *d_VD, double2 *d_VB, const 
                         int Lmax, int P, int nipw, int sparse, unsigned long long *d_offmax,
                         unsigned long long *d_absmax, cudaStream_t st);
 // Fixed-point slices (four BF16 planes, per-row exponents) of the real
-// embedding [[Vr,-Vi],[Vi,Vr]] of VD.
+// embedding [[Ur,-Ui],[Ui,Ur]] of U, the dense-block rows of the upper triangle
+// of v_t with half its diagonal.
 void launch_build_ap(const double2 *d_VD, __nv_bfloat16 *d_Ap, int *d_aexp, int D, int naux, int N0, int N0pad,
                      int Dpad, int RS, cudaStream_t st);
 // q->0 bracket of Eq. (div final) into *d_out (FP64); d_partial holds
@@ -260,21 +261,21 @@ void launch_block64(const QDesc *d_q, int nq, const double2 *const *d_VB, const 
 template <typename V>
 void launch_slice_cols(const V *d_Z, long long RSc, const QDesc *d_q, int nq, long long NC, long long maxcols, int N0,
                        int N0pad, int Dpad, int RS, __nv_bfloat16 *d_XS, int *d_exp, cudaStream_t st);
-// The channel blocks of Y (rows [0, N0)).  With d_VD non-null (the double-FP32
-// kernel, block_y_couples(P, N0)) it also adds to each channel's mu != 0 row
-// N0 + ch its couplings to the channel's mu = 0 functions, v_t[N0+ch, mu=0 of ch]
-// Z[mu=0 of ch]: the only nonzeros of the dense-block rows in the mu = 0 columns,
-// which gemm1 then skips (launch it after gemm1).
+// The channel blocks of Y' = U Z (rows [0, N0)), U the upper triangle of v_t
+// with half its diagonal.  (With d_VD non-null, the double-FP32 kernel would
+// also add the dense rows' couplings to the mu = 0 functions, the lower
+// triangle; the Hermitian split passes null.)
 template <typename V>
 void launch_block_y(const QDesc *d_q, int nq, const double2 *const *d_VB, const double2 *const *d_VD, const V *d_Z,
                     double2 *d_Y, long long RSc, int P, int N0, long long maxcols, cudaStream_t st);
 bool block_y_couples(int P, int N0);
-// GEMM1 tiles of one batch (host) and its launch; skip_mu0 leaves out the mu = 0
-// columns of v_t's dense-block rows (added by launch_block_y).
-int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, bool skip_mu0, std::vector<unsigned char> &out);
+// GEMM1 tiles of one batch (host) and its launch: Y' = U Z for the dense-block
+// rows, U the upper triangle of v_t with half its diagonal (the slices of
+// launch_build_ap), K of every row tile from its first row on.
+int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, std::vector<unsigned char> &out);
 int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *d_q,
                     const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc, long long NC, int N0,
-                    int N0pad, int Dpad, int RS, bool skip_mu0, const void *d_tiles, int ntiles);
+                    int N0pad, int Dpad, int RS, const void *d_tiles, int ntiles);
 int gemm2_tiles(const PairDesc *h_pairs, int npairs, int NB, std::vector<unsigned char> &out);
 int gemm2_check_nb(int NB);
 int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16 *d_YS, const int *d_zexp,

@@ -116,7 +116,6 @@ struct BatchPlan {
     size_t o_pairs = 0, o_qd = 0, o_kpair = 0, o_praw = 0, o_klist = 0, o_kstart = 0, o_klp = 0, o_vb = 0, o_vd = 0;
     size_t o_zg1 = 0, o_zg2 = 0, o_g1t = 0, o_g2t = 0;
     int n_g1t = 0, n_g2t = 0, maxM1 = 0, maxN1 = 0, mx2 = 0;
-    bool couple = false;
     ZipwBatch zipw;
     ZmtBatch zmt;
     std::vector<std::pair<int, const double2 *>> overrides;   // (pair, caller's Z)
@@ -146,7 +145,7 @@ struct BuildPlan {
     int runs = 0;                     // builds executed with this plan
     int nlaunch = 0;
     cudaEvent_t e_start = nullptr, e_fin0 = nullptr, e_end = nullptr;
-    double flops = 0, fl_apply = 0, fl_zhy = 0, fl_zipw = 0;
+    double flops = 0, fl_apply = 0, fl_apply_exec = 0, fl_zhy = 0, fl_zipw = 0;
     int npairs_total = 0;
     int device = 0;
 
@@ -383,6 +382,7 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
             pl.flops += 8.0 * m * n * (nnz + (double)qd.naux * n) + 8.0 * m * n * ctx->nlmp * nmt +
                         8.0 * m * n * qd.nipw * hnpw[pr.ikp];
             pl.fl_apply += 8.0 * m * n * (double)qd.D * qd.D;
+            pl.fl_apply_exec += tc ? 8.0 * m * n * 0.5 * (double)qd.D * (qd.D + 1) : 8.0 * m * n * (double)qd.D * qd.D;
             pl.fl_zhy += 8.0 * m * n * (double)qd.naux * n;
             pl.fl_zipw += 8.0 * m * n * (double)qd.nipw * hnpw[pr.ikp];
         }
@@ -475,9 +475,8 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
         }
         if (tc) {
             if ((rc = zmt_tc_plan_batch(ctx, pl.zmt, bt.pairs, RSc, tab, bt.zmt))) return rc;
-            bt.couple = sparse && std::is_same<V, double2>::value && block_y_couples(P, N0);
             std::vector<unsigned char> t1, t2;
-            bt.n_g1t = gemm1_tiles(bt.qd.data(), nq, pl.N0pad, bt.couple, t1);
+            bt.n_g1t = gemm1_tiles(bt.qd.data(), nq, pl.N0pad, t1);
             bt.n_g2t = gemm2_tiles(bt.pairs.data(), npairs, NB, t2);
             bt.o_g1t = tab.put(t1);
             bt.o_g2t = tab.put(t2);
@@ -661,16 +660,15 @@ int plan_run(hfx_ctx *ctx, BuildPlan &pl, int keep, int fail_wait) {
             launch_slice_cols<V>(Zc, RSc, d_qd, nq, bt.ncols, bt.maxcols, N0, pl.N0pad, pl.Dpad, pl.RS, ZS, zexp, ctx->stream);
             if ((rc = cuda_check(ctx, cudaGetLastError(), "slice kernels"))) return rc;
             rec(ctx, bt.ev[6]);
-            // the mu = 0 columns of the dense-block rows hold only each channel's
-            // mu != 0 -> mu = 0 couplings: gemm1 leaves them out and the channel
-            // block kernel, run after it, adds them
+            // Y' = U Z with U the upper triangle of v_t (half diagonal): the dense
+            // rows on the tensor cores, the mu = 0 rows in the channel-block kernel;
+            // the q reduction adds P' + P'^H for P' = Z^H Y'
             if ((rc = launch_gemm1_tc(ctx, reinterpret_cast<const __nv_bfloat16 *>(ctx->s_ap.p), (long long)nk * 4 * pl.MP,
                                       reinterpret_cast<const int *>(ctx->s_aexp.p), d_qd, ZS, zexp, Yd, RSc, bt.ncols, N0,
-                                      pl.N0pad, pl.Dpad, pl.RS, bt.couple, tab + bt.o_g1t, bt.n_g1t)))
+                                      pl.N0pad, pl.Dpad, pl.RS, tab + bt.o_g1t, bt.n_g1t)))
                 return rc;
             rec(ctx, bt.ev[7]);
-            launch_block_y<V>(d_qd, nq, reinterpret_cast<const double2 *const *>(tab + bt.o_vb),
-                              bt.couple ? reinterpret_cast<const double2 *const *>(tab + bt.o_vd) : nullptr, Zc, Yd, RSc, P,
+            launch_block_y<V>(d_qd, nq, reinterpret_cast<const double2 *const *>(tab + bt.o_vb), nullptr, Zc, Yd, RSc, P,
                               N0, bt.maxcols, ctx->stream);
             launch_slice_cols<double2>(Yd, RSc, d_qd, nq, bt.ncols, bt.maxcols, N0, pl.N0pad, pl.Dpad, pl.RS, YS, yexp,
                                        ctx->stream);
@@ -749,6 +747,7 @@ void fill_stats(hfx_ctx *ctx, BuildPlan &pl, hfx_stats *st, bool graph) {
     st->sparse_used = ctx->sparse_used ? 1 : 0;
     st->n_launches = pl.nlaunch;
     st->flops_apply = pl.fl_apply;
+    st->flops_apply_exec = pl.fl_apply_exec;
     st->flops_zhy = pl.fl_zhy;
     st->flops_zipw = pl.fl_zipw;
     st->graph_replayed = graph ? 1 : 0;

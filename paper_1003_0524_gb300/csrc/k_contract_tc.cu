@@ -100,7 +100,16 @@ __global__ void __launch_bounds__(256, 4) slice_cols_kernel(const V *__restrict_
     }
 }
 
-// Y rows of the mu=0 functions (on-site blocks of Fig. 1), FP64.
+// Weight of v_B[ch, i, s] in U, the upper triangle of v_t with half its
+// diagonal, in the order [mu=0 | mu!=0 | IPW]: s = 0 is the coupling of mu = 0
+// function i to the channel's mu != 0 function (a dense-block column, above the
+// diagonal); s >= 1 is mu = 0 function s - 1 of the same channel.
+__device__ __forceinline__ double upper_weight(int i, int s) {
+    return s == 0 ? 1.0 : (s - 1 > i ? 1.0 : (s - 1 == i ? 0.5 : 0.0));
+}
+
+// Y rows of the mu=0 functions (on-site blocks of Fig. 1), FP64, with the
+// upper part U of the blocks.
 template <typename V>
 __global__ void block_y_kernel(const QDesc *__restrict__ qd, const double2 *const *__restrict__ VB,
                                const V *__restrict__ Z, double2 *__restrict__ Y, long long RSc, int P, int N0) {
@@ -118,7 +127,8 @@ __global__ void block_y_kernel(const QDesc *__restrict__ qd, const double2 *cons
         double2 acc = cmul(row[0], make_double2((double)z0.x, (double)z0.y));
         for (int s = 1; s < P; ++s) {
             V zs = z[ch * (P - 1) + s - 1];
-            acc = cfma(row[s], make_double2((double)zs.x, (double)zs.y), acc);
+            const double w = upper_weight(i, s);
+            acc = cfma(make_double2(w * row[s].x, w * row[s].y), make_double2((double)zs.x, (double)zs.y), acc);
         }
         Y[col * RSc + u] = acc;
     }
@@ -140,12 +150,14 @@ __device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
     lo = nl ? __uint_as_float(__float_as_uint(r * __uint_as_float((uint32_t)(e - 948) << 23)) | sg) : 0.0f;
 }
 
-// Y rows of the mu = 0 functions (on-site blocks of Fig. 1): for channel ch,
-// Y[ch (P-1) + i] = v_B[ch, i, 0] Z[N0 + ch] + sum_{s >= 1} v_B[ch, i, s] Z[ch (P-1) + s - 1].
-// One thread per (column, channel) computes its P - 1 rows in double-FP32
-// arithmetic (about 2^-44 relative; the rows are sliced to 2^-32 of the column
-// maximum next), so the kernel runs on the FP32 units rather than GB300's
-// narrow FP64 pipe.  The blocks of q are split into shared memory once.
+// Y rows of the mu = 0 functions (on-site blocks of Fig. 1) with the upper
+// part U of v_t: for channel ch,
+// Y[ch (P-1) + i] = v_B[ch, i, 0] Z[N0 + ch] + sum_{s >= 1} w(i, s) v_B[ch, i, s] Z[ch (P-1) + s - 1],
+// w = upper_weight.  One thread per (column, channel) computes its P - 1 rows
+// in double-FP32 arithmetic (about 2^-44 relative; the rows are sliced to
+// 2^-32 of the column maximum next), so the kernel runs on the FP32 units
+// rather than GB300's narrow FP64 pipe.  The blocks of q are split into shared
+// memory once.
 template <int P>
 __global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *const *__restrict__ VB,
                                   const double2 *const *__restrict__ VD, const double2 *__restrict__ Z,
@@ -155,10 +167,11 @@ __global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *c
     const double2 *vb = VB[blockIdx.y];
     const int nch = N0 / (P - 1);
     for (int i = threadIdx.x; i < N0 * P; i += blockDim.x) {
+        const double w = upper_weight((i / P) % (P - 1), i % P);
         const double2 v = vb[i];
         float4 f;
-        split_f64(v.x, f.x, f.y);
-        split_f64(v.y, f.z, f.w);
+        split_f64(w * v.x, f.x, f.y);
+        split_f64(w * v.y, f.z, f.w);
         vbs[i] = f;
     }
     float4 *vcs = vbs + N0 * P;   // v_t[N0 + ch, ch (P-1) + i]: row ch of the dense block
@@ -224,7 +237,7 @@ __global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *c
 // stage, three stages; the four class accumulators fill TMEM (single buffer:
 // the MMA warp waits for the epilogue to read a K group before the next).
 // Each CTA loads the A and B tiles of its own output tile.
-struct G1Tile { int qslot, mrow, ncol0, klen, out, pad; };
+struct G1Tile { int qslot, mrow, ncol0, klen, iq, kbeg; };   // K of each half: [kbeg, kbeg + klen); iq: the q of A
 
 struct G1Params {
     const G1Tile *tiles;
@@ -236,7 +249,6 @@ struct G1Params {
     long long RSc;
     long long NC;          // columns of the batch (plane stride in rows of ZS)
     int RS, HS, MP, N0pad, Dpad, N0;
-    int k0;                // first K column of each half (N0pad: the mu = 0 columns left out)
     int *err;
 };
 
@@ -287,14 +299,17 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
             int s = 0;
             uint32_t ph = 0;
             int issued = 0;
+            G1Tile nx = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x] : G1Tile{};
             for (int t = blockIdx.x; t < p.ntiles && !abort_flag; t += gridDim.x) {
-                G1Tile tl = p.tiles[t];
-                int qi = p.qd[tl.qslot].iq;
+                const G1Tile tl = nx;
+                // the next tile's descriptor, loaded now: its latency overlaps this tile's copies
+                if (t + (int)gridDim.x < p.ntiles) nx = p.tiles[t + gridDim.x];
+                const int qi = tl.iq;
                 int nk = tl.klen / G1_KC;
                 bool stop = false;
                 for (int kc = 0; kc < 2 * nk; ++kc) {
                     if (!mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma)) { stop = true; break; }
-                    int x = p.k0 + ((kc < nk) ? kc * G1_KC : p.HS + (kc - nk) * G1_KC);
+                    int x = tl.kbeg + ((kc < nk) ? kc * G1_KC : p.HS + (kc - nk) * G1_KC);
                     unsigned char *st = stages + (size_t)s * G1_STAGE;
                     mbar_expect_tx(&full_bar[s], G1_STAGE);
 #pragma unroll
@@ -319,9 +334,11 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
             // the ten slice products
             constexpr uint32_t id1 = idesc_bf16(G1_BM, G1_BN), id2 = idesc_bf16(G1_BM, 2 * G1_BN);
             bool ok = true;
+            int nklen = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x].klen : 0;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-                G1Tile tl = p.tiles[t];
-                int nchunk = 2 * (tl.klen / G1_KC);
+                const int klen = nklen;
+                if (t + (int)gridDim.x < p.ntiles) nklen = p.tiles[t + gridDim.x].klen;   // prefetch
+                int nchunk = 2 * (klen / G1_KC);
                 for (int g0 = 0; g0 < nchunk && ok; g0 += G1_GROUP) {
                     if (!mbar_wait(&tempty_bar, eph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                     tc_fence_after();
@@ -366,13 +383,17 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
             int nchunk = 2 * (tl.klen / G1_KC);
             int ngroups = (nchunk + G1_GROUP - 1) / G1_GROUP;
             // output scales: the row exponent, and the exponents of the 64 columns of
-            // this half, fetched together before the stores (lane l holds columns
-            // l and 32 + l; the store loop shuffles them)
+            // this half (lane l holds columns l and 32 + l; the store loop shuffles
+            // them), fetched at tile start so that their latency overlaps the first
+            // K group instead of following the last one
             const int r = tl.mrow + quarter * 32 + lane;     // row of A' in this q: [0, D) real, [D, 2D) imaginary
             const bool im = r >= q.D;
             const int rr = im ? r - q.D : r;
-            const bool live = rr < q.D && tl.out;
+            const bool live = rr < q.D;
             const long long c0 = tl.ncol0 + half * 64, cend = q.colbase + q.ncols;
+            const int ea = live ? p.aexp[(size_t)q.iq * p.MP + r] - 16 : 0;
+            const int zx0 = c0 + lane < cend ? p.zexp[c0 + lane] : 0;
+            const int zx1 = c0 + 32 + lane < cend ? p.zexp[c0 + 32 + lane] : 0;
             uint64_t hi[32], lo[32];   // packed pairs of columns
 #pragma unroll
             for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
@@ -401,9 +422,6 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                 eph ^= 1;
             }
             if (!ok) break;
-            const int ea = live ? p.aexp[(size_t)q.iq * p.MP + r] - 16 : 0;
-            const int zx0 = c0 + lane < cend ? p.zexp[c0 + lane] : 0;
-            const int zx1 = c0 + 32 + lane < cend ? p.zexp[c0 + 32 + lane] : 0;
             double *dst = reinterpret_cast<double *>(p.Y + c0 * p.RSc + p.N0 + (live ? rr : 0)) + (im ? 1 : 0);
             const long long cstride = 2 * p.RSc;
 #pragma unroll
@@ -441,13 +459,15 @@ struct G2Params {
     int *err;
 };
 
-constexpr int G2_A_PLANE = 128 * 64 * 2;    // 16 KB: rows [0,NB) Re, [NB,2NB) Im, rest zero
-constexpr int G2_GROUP = 4;                 // chunks per exact K group (256)
 constexpr int G2_EPI_WARPS = 8;
 constexpr int G2_MAX_STAGES = 4;
 
-// number of 64-row K chunks of a pair: mu=0 rows plus the dense rows of its q
-__device__ __forceinline__ int g2_chunks(const QDesc &q, int N0pad) { return (N0pad + q.D + 63) / 64; }
+// K chunk of the Z^H Y tiles: 64 (128-byte swizzle) for band blocks up to 40,
+// 32 (64-byte swizzle) above, so that at least three pipeline stages fit
+__host__ __device__ constexpr int g2_kc(int NB) { return NB >= 48 ? 32 : 64; }
+
+// number of K chunks of a pair: mu=0 rows plus the dense rows of its q
+template <int KC> __device__ __forceinline__ int g2_chunks(const QDesc &q, int N0pad) { return (N0pad + q.D + KC - 1) / KC; }
 
 // warp 0: TMA; warp 1: MMA; warps 2..9: epilogue (lane quarter = w%4,
 // column half = (w-2)/4 of the 2NB accumulator columns).  Four class
@@ -456,8 +476,11 @@ template <int NB>
 __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const __grid_constant__ CUtensorMap tmZ,
                                                                           const __grid_constant__ CUtensorMap tmY,
                                                                           G2Params p) {
+    constexpr int KC = g2_kc(NB);                  // K values per chunk
+    constexpr int G2_A_PLANE = 128 * KC * 2;       // rows [0,NB) Re, [NB,2NB) Im, rest zero
+    constexpr int G2_GROUP = 256 / KC;             // chunks per exact K group (256)
     constexpr int W = 2 * NB, CW = W / 2;   // accumulator columns; per thread
-    constexpr int B_PLANE = W * 128;
+    constexpr int B_PLANE = W * KC * 2;
     extern __shared__ __align__(1024) unsigned char g2_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(g2_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
@@ -489,7 +512,7 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
     __syncthreads();
     tc_fence_after();
     uint32_t tmem = tmem_slot;
-    constexpr uint32_t box_bytes = 64u * NB * 2u;
+    constexpr uint32_t box_bytes = (uint32_t)KC * NB * 2u;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -500,7 +523,7 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                 G2Tile tl = p.tiles[t];
                 const PairDesc pr = p.pairs[tl.pair];
                 const QDesc q = p.qd[pr.qslot];
-                int nc = g2_chunks(q, p.N0pad);
+                int nc = g2_chunks<KC>(q, p.N0pad);
                 bool stop = false;
                 for (int m = 0; m < pr.no && !stop; ++m) {
                     long long ya = pr.col0 + (long long)m * pr.nb + tl.bi * NB;
@@ -513,10 +536,10 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                             unsigned char *a = st + pl * G2_A_PLANE;
                             unsigned char *b = st + NPL * G2_A_PLANE + pl * B_PLANE;
                             int ra = (int)(pl * p.NC + ya), rb = (int)(pl * p.NC + yb);
-                            tma_load_2d(saddr(a), &tmZ, &full_bar[s], c * 64, ra);
-                            tma_load_2d(saddr(a + NB * 128), &tmZ, &full_bar[s], p.HS + c * 64, ra);
-                            tma_load_2d(saddr(b), &tmY, &full_bar[s], c * 64, rb);
-                            tma_load_2d(saddr(b + NB * 128), &tmY, &full_bar[s], p.HS + c * 64, rb);
+                            tma_load_2d(saddr(a), &tmZ, &full_bar[s], c * KC, ra);
+                            tma_load_2d(saddr(a + NB * KC * 2), &tmZ, &full_bar[s], p.HS + c * KC, ra);
+                            tma_load_2d(saddr(b), &tmY, &full_bar[s], c * KC, rb);
+                            tma_load_2d(saddr(b + NB * KC * 2), &tmY, &full_bar[s], p.HS + c * KC, rb);
                         }
                         ++issued;
                         if (++s == NS) { s = 0; ph ^= 1; }
@@ -544,7 +567,7 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                 G2Tile tl = p.tiles[t];
                 const PairDesc pr = p.pairs[tl.pair];
                 const QDesc q = p.qd[pr.qslot];
-                int nc = g2_chunks(q, p.N0pad);
+                int nc = g2_chunks<KC>(q, p.N0pad);
                 for (int m = 0; m < pr.no && ok; ++m) {
                     for (int g0 = 0; g0 < nc && ok; g0 += G2_GROUP) {
                         if (!mbar_wait(&tempty_bar, tph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
@@ -555,11 +578,13 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                             unsigned char *st = stages + (size_t)s * SB;
                             uint32_t a0 = saddr(st), b0 = saddr(st + NPL * G2_A_PLANE);
 #pragma unroll
-                            for (int ks = 0; ks < 4; ++ks) {
-                                const uint64_t d0 = desc_sw128(a0) + 2 * ks, d1 = desc_sw128(a0 + G2_A_PLANE) + 2 * ks;
-                                const uint64_t d2 = desc_sw128(a0 + 2 * G2_A_PLANE) + 2 * ks;
-                                const uint64_t d3 = desc_sw128(a0 + 3 * G2_A_PLANE) + 2 * ks;
-                                const uint64_t e0 = desc_sw128(b0) + 2 * ks, e2 = desc_sw128(b0 + 2 * B_PLANE) + 2 * ks;
+                            for (int ks = 0; ks < KC / 16; ++ks) {
+                                // K-major operands, 128- or 64-byte swizzle (one swizzled row per chunk)
+                                auto dsc = [](uint32_t a) { return KC == 64 ? desc_sw128(a) : desc_sw64(a); };
+                                const uint64_t d0 = dsc(a0) + 2 * ks, d1 = dsc(a0 + G2_A_PLANE) + 2 * ks;
+                                const uint64_t d2 = dsc(a0 + 2 * G2_A_PLANE) + 2 * ks;
+                                const uint64_t d3 = dsc(a0 + 3 * G2_A_PLANE) + 2 * ks;
+                                const uint64_t e0 = dsc(b0) + 2 * ks, e2 = dsc(b0 + 2 * B_PLANE) + 2 * ks;
                                 const uint32_t acc = (c == g0 && ks == 0) ? 0u : 1u;   // the two a = 0 MMAs set all classes
                                 umma_bf16(tmem, d0, e0, id2, acc);                  // classes 0, 1
                                 umma_bf16(tmem + 2 * W, d0, e2, id2, acc);          // classes 2, 3
@@ -595,7 +620,7 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
             G2Tile tl = p.tiles[t];
             const PairDesc pr = p.pairs[tl.pair];
             const QDesc q = p.qd[pr.qslot];
-            int nc = g2_chunks(q, p.N0pad);
+            int nc = g2_chunks<KC>(q, p.N0pad);
             uint64_t hi[CW / 2], lo[CW / 2];   // packed pairs of columns
 #pragma unroll
             for (int j = 0; j < CW / 2; ++j) { hi[j] = 0; lo[j] = 0; }
@@ -766,18 +791,33 @@ template void launch_block_y<float2>(const QDesc *, int, const double2 *const *,
 template void launch_block_y<double2>(const QDesc *, int, const double2 *const *, const double2 *const *,
                                       const double2 *, double2 *, long long, int, int, long long, cudaStream_t);
 
-// Tiles of GEMM1 for one batch: per q, every 128-column block of its columns
-// with all its row tiles back to back (the Z columns are read from HBM once and
-// the Re and Im rows of Y meet in L2).  skip_mu0: K starts at N0pad.
-int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, bool skip_mu0, std::vector<unsigned char> &out) {
-    const int k0 = skip_mu0 ? N0pad : 0;
+// Tiles of GEMM1 for one batch.  The A operand is the upper triangle U of the
+// dense block, so a row tile's K range (in each half) starts at its first row:
+// [N0pad + r_min, N0pad + D), rounded to the K chunk.  Order, per q: groups of
+// G1_COLGROUP 128-column blocks; inside a group, every row tile for each block
+// of the group in turn.  The tiles running at once then share a few A row tiles
+// and a few Z column blocks, both of which stay in L2 (the A slices of one q
+// are up to ~140 MB on the largest workloads, more than L2), and the Re and Im
+// rows of one Y column meet in L2.
+constexpr int G1_COLGROUP = 8;
+int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, std::vector<unsigned char> &out) {
     std::vector<G1Tile> tiles;
     for (int s = 0; s < nq; ++s) {
         const QDesc &q = h_q[s];
-        int klen = ((N0pad - k0 + q.D + G1_KC - 1) / G1_KC) * G1_KC;
         int mt = (2 * q.D + G1_BM - 1) / G1_BM;   // row tiles over the D real and D imaginary rows
-        for (long long n0 = 0; n0 < q.ncols; n0 += G1_BN)
-            for (int i = 0; i < mt; ++i) tiles.push_back(G1Tile{s, i * G1_BM, (int)(q.colbase + n0), klen, 1, 0});
+        std::vector<int> kbeg(mt), klen(mt);
+        for (int i = 0; i < mt; ++i) {
+            const int r0 = i * G1_BM, r1 = std::min(2 * q.D, r0 + G1_BM);   // rows [r0, r1)
+            const int rmin = (r0 < q.D && r1 > q.D) ? 0 : (r0 < q.D ? r0 : r0 - q.D);
+            kbeg[i] = N0pad + rmin / G1_KC * G1_KC;
+            klen[i] = (N0pad + q.D - kbeg[i] + G1_KC - 1) / G1_KC * G1_KC;
+        }
+        for (long long g0 = 0; g0 < q.ncols; g0 += (long long)G1_BN * G1_COLGROUP)
+            for (int i = 0; i < mt; ++i)
+                for (int j = 0; j < G1_COLGROUP; ++j) {
+                    const long long n0 = g0 + (long long)j * G1_BN;
+                    if (n0 < q.ncols) tiles.push_back(G1Tile{s, i * G1_BM, (int)(q.colbase + n0), klen[i], q.iq, kbeg[i]});
+                }
     }
     out.assign(reinterpret_cast<const unsigned char *>(tiles.data()),
                reinterpret_cast<const unsigned char *>(tiles.data()) + tiles.size() * sizeof(G1Tile));
@@ -786,7 +826,7 @@ int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, bool skip_mu0, std::vector<
 
 int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *d_q,
                     const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc, long long NC, int N0,
-                    int N0pad, int Dpad, int RS, bool skip_mu0, const void *d_tiles, int ntiles) {
+                    int N0pad, int Dpad, int RS, const void *d_tiles, int ntiles) {
     int HS = N0pad + Dpad, MP = 2 * Dpad;
     if (ntiles == 0) return HFX_OK;
     if (NC > 0x7fffffffLL / 4) return set_err(ctx, HFX_EUNSUPPORTED, "batch has too many columns for 32-bit TMA coordinates");
@@ -809,7 +849,6 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
     p.MP = MP;
     p.N0pad = N0pad;
     p.Dpad = Dpad;
-    p.k0 = skip_mu0 ? N0pad : 0;
     p.err = ctx->d_err;
     size_t smem = (size_t)G1_STAGES * G1_STAGE + 1024;
     auto kern = gemm1_kernel;
@@ -851,8 +890,9 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
     if (NC > 0x7fffffffLL / 4) return set_err(ctx, HFX_EUNSUPPORTED, "batch has too many columns for 32-bit TMA coordinates");
     int rc;
     CUtensorMap mZ, mY;
-    if ((rc = make_map_2d(ctx, &mZ, d_ZS, (long long)NPL * NC, RS, NB))) return rc;
-    if ((rc = make_map_2d(ctx, &mY, d_YS, (long long)NPL * NC, RS, NB))) return rc;
+    const int KC = g2_kc(NB);
+    if ((rc = make_map_2d_sw(ctx, &mZ, d_ZS, (long long)NPL * NC, RS, NB, KC, 2 * KC))) return rc;
+    if ((rc = make_map_2d_sw(ctx, &mY, d_YS, (long long)NPL * NC, RS, NB, KC, 2 * KC))) return rc;
     G2Params p;
     p.tiles = reinterpret_cast<const G2Tile *>(d_tiles);
     p.ntiles = ntiles;
@@ -867,7 +907,7 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
     p.N0pad = N0pad;
     p.fail_wait = fail_wait;
     p.err = ctx->d_err;
-    p.stage_bytes = NPL * (G2_A_PLANE + 2 * NB * 128);
+    p.stage_bytes = NPL * (128 * KC * 2 + 2 * NB * KC * 2);
     p.nstages = std::min(G2_MAX_STAGES, (int)((226 * 1024) / p.stage_bytes));
     if (p.nstages < 1) return set_err(ctx, HFX_EUNSUPPORTED, "gemm2 stage does not fit in shared memory");
     size_t smem = (size_t)p.nstages * p.stage_bytes + 1024;

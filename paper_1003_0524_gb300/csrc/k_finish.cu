@@ -6,7 +6,8 @@ namespace hfx {
 
 namespace {
 
-// Vacc[k] += sum_{pairs of k in this batch, ascending q} P_pair.
+// Vacc[k] += sum_{pairs of k in this batch, ascending q} P_pair, where the
+// tensor-core tiles (raw_format 1) hold P' = Z^H U Z and P_pair = P' + P'^H.
 __global__ void reduce_pairs_kernel(const PairDesc *__restrict__ pairs, const int *__restrict__ kstart,
                                     const int *__restrict__ klist_pairs, const int *__restrict__ klist,
                                     const double *__restrict__ praw, const long long *__restrict__ praw_off, int NB,
@@ -28,14 +29,18 @@ __global__ void reduce_pairs_kernel(const PairDesc *__restrict__ pairs, const in
                 acc.x += v.x;
                 acc.y += v.y;
             } else {
+                // real-embedded tiles of P' = Z^H U Z; the pair's term is P' + P'^H
                 int nblk = (nb + NB - 1) / NB;
                 int bi = n / NB, a = n % NB, bj = n2 / NB, b = n2 % NB;
                 int W = 2 * NB;
                 const double *t0 = P + ((size_t)bi * nblk + bj) * W * W;
+                const double *t1 = P + ((size_t)bj * nblk + bi) * W * W;
                 double pr = t0[(size_t)a * W + b] + t0[(size_t)(NB + a) * W + NB + b];
                 double pim = t0[(size_t)a * W + NB + b] - t0[(size_t)(NB + a) * W + b];
-                acc.x += pr;
-                acc.y += pim;
+                double qr = t1[(size_t)b * W + a] + t1[(size_t)(NB + b) * W + NB + a];
+                double qim = t1[(size_t)b * W + NB + a] - t1[(size_t)(NB + b) * W + a];
+                acc.x += pr + qr;
+                acc.y += pim - qim;
             }
         }
         V[e] = acc;

@@ -263,19 +263,22 @@ __global__ void transform_v_kernel(const double2 *v, double2 *VD, double2 *VB, c
     }
 }
 
-// Element (r, c) of the real embedding [[Vr, -Vi], [Vi, Vr]] of the
-// dense-block rows of v_t: rows [Re D (Dpad) | Im D (Dpad)], columns
-// [Re (N0pad + Dpad) | Im (N0pad + Dpad)] (zero in the padding).
+// Element (r, c) of the real embedding [[Ur, -Ui], [Ui, Ur]] of the
+// dense-block rows of U, the upper triangle of v_t with half its diagonal
+// (v_t = U + U^H for Hermitian v_t, so Z^H v_t Z = P' + P'^H with P' = Z^H U Z):
+// rows [Re D (Dpad) | Im D (Dpad)], columns [Re (N0pad + Dpad) | Im (N0pad +
+// Dpad)] (zero in the padding).  In the order [mu=0 | dense], the mu = 0
+// columns of the dense-block rows lie below the diagonal and are zero in U.
 __device__ __forceinline__ double ap_elem(const double2 *VD, int r, int c, int D, int naux, int N0, int N0pad,
                                          int Dpad) {
     int HS = N0pad + Dpad;
     int rim = r >= D, rr = rim ? r - D : r;   // real rows [0, D), imaginary rows [D, 2D)
     int cim = c >= HS, u = cim ? c - HS : c;
-    int j = -1;
-    if (u < N0pad) j = (u < N0) ? u : -1;
-    else j = (u - N0pad < naux - N0) ? N0 + (u - N0pad) : -1;
-    if (rr >= D || j < 0) return 0.0;
-    double2 val = VD[(size_t)rr * naux + j];
+    if (rr >= D || u < N0pad) return 0.0;
+    const int d = u - N0pad;                  // dense column index
+    if (d >= naux - N0 || d < rr) return 0.0;
+    double2 val = VD[(size_t)rr * naux + N0 + d];
+    if (d == rr) { val.x *= 0.5; val.y *= 0.5; }
     if (!rim && !cim) return val.x;
     if (!rim && cim) return -val.y;
     if (rim && !cim) return val.y;

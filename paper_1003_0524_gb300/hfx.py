@@ -95,6 +95,7 @@ class hfx_stats(ctypes.Structure):
         ("graph_replayed", ctypes.c_int),
         ("tile_nb_zhy", ctypes.c_int),
         ("tile_nb_zipw", ctypes.c_int),
+        ("flops_apply_exec", ctypes.c_double),
     ]
 
 
@@ -250,10 +251,13 @@ def hfx_build_all(ctx, keep_products: bool = False) -> dict:
     return {f: getattr(st, f) for f, _ in hfx_stats._fields_}
 
 
-def hfx_build_exchange(ctx, ik: int, n_bands: int) -> np.ndarray:
+def hfx_build_exchange(ctx, ik: int, n_bands: int, stats: bool = False):
+    """V^x(k) of one k (its N_k pairs); with stats=True also the build statistics."""
     out = np.zeros((n_bands, n_bands), np.complex128)
     st = hfx_stats()
     _check(ctx, load().hfx_build_exchange(ctx, int(ik), out.ctypes.data, ctypes.byref(st)))
+    if stats:
+        return out, {f: getattr(st, f) for f, _ in hfx_stats._fields_}
     return out
 
 
@@ -307,7 +311,17 @@ class Context:
 
     def __init__(self, sysm, precision: str = "sliced", sparse: str = "auto", q0_term: bool = True,
                  beta: float = 0.005, stream: Optional[int] = None, device: int = 0, work_bytes: int = 0,
-                 use_graph: bool = True, tile_nb_zhy: int = 0, tile_nb_zipw: int = 0, test_fail_wait: bool = False):
+                 use_graph: bool = True, tile_nb_zhy: int = 0, tile_nb_zipw: int = 0, test_fail_wait: bool = False,
+                 tuning: bool = False):
+        """tuning: take the tile shapes of this size class from the autotuner's
+        file (paper_1003_0524_gb300/tuning.json) when it has them."""
+        self.tuned = None
+        if tuning and not tile_nb_zhy and not tile_nb_zipw:
+            from .autotune import lookup
+            self.tuned = lookup(sysm)
+            if self.tuned:
+                tile_nb_zhy = int(self.tuned["tile_nb_zhy"])
+                tile_nb_zipw = int(self.tuned["tile_nb_zipw"])
         opt = hfx_default_options()
         opt.precision = {"fp64": HFX_PREC_FP64, "sliced": HFX_PREC_SLICED}[precision]
         opt.sparse = {"auto": HFX_SPARSE_AUTO, "on": HFX_SPARSE_ON, "off": HFX_SPARSE_OFF}[sparse]
@@ -345,8 +359,8 @@ class Context:
     def exchange(self, ik: int) -> np.ndarray:
         return hfx_get_exchange(self.ctx, ik, int(self.sys.n_bands[ik]))
 
-    def build_exchange(self, ik: int) -> np.ndarray:
-        return hfx_build_exchange(self.ctx, ik, int(self.sys.n_bands[ik]))
+    def build_exchange(self, ik: int, stats: bool = False):
+        return hfx_build_exchange(self.ctx, ik, int(self.sys.n_bands[ik]), stats)
 
     def energy(self) -> float:
         return hfx_get_energy(self.ctx)
