@@ -678,6 +678,49 @@ int ora_vx_part(const OraSys *s, int ik, int nsel, const int *sel, int nq, const
     return vx_core(s, ik, 0, 0, sel, nsel, nq, qlist, Vout);
 }
 
+/* ------------------------------------------------ LAPW representation */
+
+/* Eq. (APW trafo), Sec. III.A: the exchange matrix in the LAPW basis of k,
+ *   V_GG' = sum_{n,n'} (S c)[G][n] V[n][n'] (c^H S)[n'][G'],
+ * (S c)[G][n] = sum_G'' S[G][G''] c[n][G''] = < chi_G | phi_n >,
+ * (c^H S)[n'][G'] = sum_G'' conj(c[n'][G'']) S[G''][G'] = < phi_n' | chi_G' >,
+ * with S[G][G'] = < chi_G | chi_G' > the overlap matrix of the basis functions
+ * of k and c[n][G] the coefficients of phi_n in them.  Inputs row-major and
+ * complex: S npw x npw, c nb x npw, V nb x nb; output npw x npw.  Plain loops:
+ * the two brackets first, then the double sum over n, n' per element. */
+int ora_lapw_trafo(int npw, int nb, const double *Sd, const double *cd, const double *Vd, double *out) {
+    const cplx *S = (const cplx *)Sd, *c = (const cplx *)cd, *V = (const cplx *)Vd;
+    cplx *L = (cplx *)malloc(sizeof(cplx) * ((size_t)npw * nb + 1));   /* (S c)[G][n] */
+    cplx *R = (cplx *)malloc(sizeof(cplx) * ((size_t)nb * npw + 1));   /* (c^H S)[n][G'] */
+#pragma omp parallel for schedule(static)
+    for (int G = 0; G < npw; ++G)
+        for (int n = 0; n < nb; ++n) {
+            cplx acc = {0.0, 0.0};
+            for (int G2 = 0; G2 < npw; ++G2) acc = cadd(acc, cmul(S[(size_t)G * npw + G2], c[(size_t)n * npw + G2]));
+            L[(size_t)G * nb + n] = acc;
+        }
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < nb; ++n)
+        for (int G = 0; G < npw; ++G) {
+            cplx acc = {0.0, 0.0};
+            for (int G2 = 0; G2 < npw; ++G2) acc = cadd(acc, cconjmul(c[(size_t)n * npw + G2], S[(size_t)G2 * npw + G]));
+            R[(size_t)n * npw + G] = acc;
+        }
+    cplx *O = (cplx *)out;
+#pragma omp parallel for schedule(static)
+    for (int G = 0; G < npw; ++G)
+        for (int G2 = 0; G2 < npw; ++G2) {
+            cplx acc = {0.0, 0.0};
+            for (int n = 0; n < nb; ++n)
+                for (int n2 = 0; n2 < nb; ++n2)
+                    acc = cadd(acc, cmul(cmul(L[(size_t)G * nb + n], V[(size_t)n * nb + n2]), R[(size_t)n2 * npw + G2]));
+            O[(size_t)G * npw + G2] = acc;
+        }
+    free(L);
+    free(R);
+    return 0;
+}
+
 int ora_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

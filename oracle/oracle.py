@@ -96,6 +96,8 @@ def lib():
             L.ora_vx_sub.argtypes = [vp, ip, ip, vp, ip, vp]
             L.ora_vx_part.restype = ip
             L.ora_vx_part.argtypes = [vp, ip, ip, vp, ip, vp, vp]
+            L.ora_lapw_trafo.restype = ip
+            L.ora_lapw_trafo.argtypes = [ip, ip, vp, vp, vp, vp]
             L.ora_num_threads.restype = ip
             L.ora_num_threads.argtypes = []
             _lib = L
@@ -240,6 +242,19 @@ def transform_T(mu) -> np.ndarray:
     T = np.zeros((P, P), np.float64)
     lib().ora_transform_T(P, _ptr(mu), _ptr(T))
     return T
+
+
+def lapw_trafo(S, c, V) -> np.ndarray:
+    """Eq. (APW trafo): V_GG' = (S c) V (c^H S) with S (npw x npw), c (nb x npw)
+    the coefficients of the bands in the basis of k, V (nb x nb)."""
+    S = np.ascontiguousarray(S, dtype=np.complex128)
+    c = np.ascontiguousarray(c, dtype=np.complex128)
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    nb, npw = c.shape
+    assert S.shape == (npw, npw) and V.shape == (nb, nb)
+    out = np.zeros((npw, npw), np.complex128)
+    lib().ora_lapw_trafo(npw, nb, _ptr(S), _ptr(c), _ptr(V), _ptr(out))
+    return out
 
 
 def num_threads() -> int:

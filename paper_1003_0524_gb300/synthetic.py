@@ -222,6 +222,18 @@ def _frame_with_first_row(rng: np.random.Generator, mu: np.ndarray) -> np.ndarra
     return q.T.copy()
 
 
+def overlap(sysm, ik: int, seed: Optional[int] = None) -> np.ndarray:
+    """A seeded Hermitian positive-definite overlap matrix S_GG'(k) of the
+    basis functions of k (npw x npw, in the order of sysm.Gk[ik]): the unit
+    matrix plus a random positive semi-definite part of norm ~0.1, standing in
+    for the LAPW overlap (interstitial step-function plus muffin-tin terms)."""
+    npw = int(sysm.Gk[ik].shape[0])
+    rng = np.random.Generator(np.random.PCG64((sysm.seed if seed is None else seed) * 1000 + 7 + ik))
+    w = _cn(rng, (npw, npw))
+    s = np.eye(npw) + 0.1 * (w @ w.conj().T) / npw
+    return 0.5 * (s + s.conj().T)
+
+
 def sphere_gap(lattice, pos_frac, rmt) -> float:
     """Smallest |R_i - R_j - T| - S_i - S_j over atom pairs and lattice shifts
     (negative means overlapping muffin-tin spheres)."""

@@ -407,3 +407,50 @@ def test_exchange_energy_identity():
     dbl *= -0.5 / s.n_k ** 2
     assert ex == pytest.approx(dbl, rel=1e-13)
     assert ex < 0
+
+
+# ---------------------------------------------------------------- LAPW representation (Eq. APW trafo)
+
+def _hpd(rng, n):
+    w = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2)
+    s = np.eye(n) + 0.3 * (w @ w.conj().T) / n
+    return 0.5 * (s + s.conj().T)
+
+
+def _s_orthonormal(rng, S, nb):
+    """Coefficients c (rows: bands) with c* S c^T = 1, i.e. <phi_n|phi_n'> = delta."""
+    ev, U = np.linalg.eigh(S)
+    s_inv_half = (U / np.sqrt(ev)) @ U.conj().T
+    z = rng.standard_normal((S.shape[0], nb)) + 1j * rng.standard_normal((S.shape[0], nb))
+    q, _ = np.linalg.qr(z)
+    return (s_inv_half @ q).T
+
+
+def test_lapw_trafo_round_trip_recovers_band_matrix():
+    """With a square S-orthonormal coefficient matrix the transform is the
+    change of basis c^{-H} V c^{-1}; projecting back with the coefficients,
+    c* V_GG' c^T, must give V again (Eq. APW trafo, Sec. III.A)."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    n = 9
+    S = _hpd(rng, n)
+    c = _s_orthonormal(rng, S, n)
+    assert np.abs(c.conj() @ S @ c.T - np.eye(n)).max() < 1e-12
+    V = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    V = V + V.conj().T
+    Vgg = O.lapw_trafo(S, c, V)
+    assert np.abs(c.conj() @ Vgg @ c.T - V).max() < 1e-11 * np.abs(V).max()
+    assert np.abs(Vgg - Vgg.conj().T).max() < 1e-12 * np.abs(Vgg).max()
+
+
+def test_lapw_trafo_of_unit_band_matrix_is_a_projector():
+    """For fewer bands than basis functions and V = 1, S^{-1} V_GG' is the
+    S-orthogonal projector onto the span of the bands: idempotent, with trace
+    equal to the number of bands."""
+    rng = np.random.Generator(np.random.PCG64(12))
+    npw, nb = 14, 5
+    S = _hpd(rng, npw)
+    c = _s_orthonormal(rng, S, nb)
+    Vgg = O.lapw_trafo(S, c, np.eye(nb))
+    Pm = np.linalg.solve(S, Vgg)
+    assert np.abs(Pm @ Pm - Pm).max() < 1e-12
+    assert abs(np.trace(Pm) - nb) < 1e-12
