@@ -271,6 +271,24 @@ HFX_API int hfx_get_q0_bracket(hfx_ctx *ctx, double *b);
 HFX_API int hfx_q0_bracket_noalloc(const double *lattice, const int *mesh, double beta, double *bracket_dev,
                                    void *stream);
 
+/* Overlap matrix S_GG'(k) = <chi_G|chi_G'> of the LAPW basis functions of k
+ * (Eq. APW Hamiltonian, Sec. III.A), npw x npw complex, Hermitian (checked,
+ * HFX_ENOTHERM), rows in the order of the plane-wave list given to
+ * hfx_set_kpoint, row stride ld >= npw.  Requires hfx_set_kpoint(k). */
+HFX_API int hfx_set_overlap(hfx_ctx *ctx, int ik, const double *S, int ld);
+
+/* The exchange matrix in the LAPW basis of every k (Eq. APW trafo):
+ *   V_GG'(k) = sum_{n,n'} (S c)[G][n] V^x_nn'(k) (c^H S)[n'][G'],
+ * with c the coefficients of hfx_set_kpoint and V^x of the last hfx_build_all,
+ * in FP64 on the device (three batched complex GEMMs over all k).  Requires a
+ * complete build and hfx_set_overlap for every k (HFX_EMISSING).  st->ms_total
+ * and st->useful_flops describe the transform. */
+HFX_API int hfx_lapw_transform_all(hfx_ctx *ctx, hfx_stats *st);
+
+/* Copy V_GG'(k) of the last hfx_lapw_transform_all into Vgg (npw x npw
+ * complex, row stride ld >= npw). */
+HFX_API int hfx_get_lapw_exchange(hfx_ctx *ctx, int ik, double *Vgg, int ld);
+
 /* Release every host and device resource of the context (NULL is a no-op). */
 HFX_API void hfx_destroy(hfx_ctx *ctx);
 

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhfx.so")
-SOURCES = ["hfx_api.cu", "hfx_plan.cu", "k_setup.cu", "k_stage1.cu", "k_contract64.cu", "k_contract_tc.cu", "k_zipw_tc.cu",
+SOURCES = ["hfx_api.cu", "hfx_plan.cu", "hfx_lapw.cu", "k_setup.cu", "k_stage1.cu", "k_contract64.cu", "k_contract_tc.cu", "k_zipw_tc.cu",
            "k_cgemm_tc.cu", "k_finish.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

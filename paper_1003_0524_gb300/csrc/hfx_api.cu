@@ -370,6 +370,9 @@ void hfx_destroy(hfx_ctx *ctx) {
     for (auto &z : ctx->zover) dfree(z.second);
     for (auto &z : ctx->zkeep) dfree(z.second);
     for (auto *v : ctx->d_V) dfree(v);
+    for (auto *v : ctx->d_S) dfree(v);
+    dfree(ctx->s_lapw.p);
+    dfree(ctx->s_lapw_tab.p);
     dfree(ctx->d_R); dfree(ctx->d_mu); dfree(ctx->d_T); dfree(ctx->d_Tid); dfree(ctx->d_gaunt); dfree(ctx->d_posf);
     dfree(ctx->d_err); dfree(ctx->d_Ex);
     Scratch *all[] = {&ctx->s_theta, &ctx->s_thpsi, &ctx->s_B,    &ctx->s_zc,   &ctx->s_zs,   &ctx->s_ys,

@@ -178,6 +178,13 @@ struct hfx_ctx {
     uint64_t struct_epoch = 0;
     // the cached build plan (device tables, scratch layout, captured graph)
     std::shared_ptr<hfx::BuildPlan> plan;
+
+    // the LAPW representation (Eq. APW trafo): overlaps per k, results of the last transform
+    std::vector<double2 *> d_S;
+    std::vector<int> S_npw;
+    hfx::Scratch s_lapw, s_lapw_tab;
+    std::vector<size_t> lapw_off;
+    bool lapw_valid = false;
 };
 
 namespace hfx {

@@ -770,6 +770,7 @@ int build_with_plan(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_st
         ctx->plan = pl;
     }
     BuildPlan &pl = *ctx->plan;
+    ctx->lapw_valid = false;
     const int fail = ctx->opt.test_fail_wait;
     ctx->opt.test_fail_wait = 0;
     const bool want_graph = ctx->opt.use_graph && !keep && !fail && !pl.graph_failed;

@@ -35,6 +35,7 @@ EXPORTS = (
     "hfx_set_products", "hfx_get_products", "hfx_build_all", "hfx_build_exchange", "hfx_get_exchange",
     "hfx_exchange_device_ptr", "hfx_get_energy", "hfx_get_q0_bracket", "hfx_destroy", "hfx_strerror",
     "hfx_last_error", "hfx_version", "hfx_q0_bracket_noalloc", "hfx_get_transform",
+    "hfx_set_overlap", "hfx_lapw_transform_all", "hfx_get_lapw_exchange",
 )
 
 
@@ -132,6 +133,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.hfx_set_coulomb.argtypes = [vp, ip, ip, vp, vp, ip, ip]
     L.hfx_get_transform.restype = ip
     L.hfx_get_transform.argtypes = [vp, ip, ip, vp]
+    L.hfx_set_overlap.restype = ip
+    L.hfx_set_overlap.argtypes = [vp, ip, vp, ip]
+    L.hfx_lapw_transform_all.restype = ip
+    L.hfx_lapw_transform_all.argtypes = [vp, P(hfx_stats)]
+    L.hfx_get_lapw_exchange.restype = ip
+    L.hfx_get_lapw_exchange.argtypes = [vp, ip, vp, ip]
     L.hfx_set_products.restype = ip
     L.hfx_set_products.argtypes = [vp, ip, ip, vp]
     L.hfx_get_products.restype = ip
@@ -293,6 +300,23 @@ def hfx_q0_bracket_noalloc(lattice, mesh, beta: float, bracket_dev_ptr: int, str
     code = load().hfx_q0_bracket_noalloc(lat.ctypes.data, m.ctypes.data, float(beta), int(bracket_dev_ptr), stream)
     if code != HFX_OK:
         raise HfxError(code, load().hfx_strerror(code).decode())
+
+
+def hfx_set_overlap(ctx, ik: int, S, ld: Optional[int] = None):
+    S = _c(S, np.complex128)
+    _check(ctx, load().hfx_set_overlap(ctx, int(ik), S.ctypes.data, int(S.shape[1]) if ld is None else int(ld)))
+
+
+def hfx_lapw_transform_all(ctx) -> dict:
+    st = hfx_stats()
+    _check(ctx, load().hfx_lapw_transform_all(ctx, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in hfx_stats._fields_}
+
+
+def hfx_get_lapw_exchange(ctx, ik: int, npw: int) -> np.ndarray:
+    out = np.zeros((npw, npw), np.complex128)
+    _check(ctx, load().hfx_get_lapw_exchange(ctx, int(ik), out.ctypes.data, int(npw)))
+    return out
 
 
 def hfx_destroy(ctx):

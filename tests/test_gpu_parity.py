@@ -357,3 +357,40 @@ def test_tile_shapes_match_oracle(nb_zhy, nb_zipw):
     V, _, st = gpu_v(s, "sliced", tile_nb_zhy=nb_zhy, tile_nb_zipw=nb_zipw)
     assert st["tile_nb_zhy"] == nb_zhy and st["tile_nb_zipw"] == nb_zipw
     assert max_err(V, ref) <= TOL_SPLIT_ABS
+
+
+@pytest.mark.parametrize("precision", ["fp64", "sliced"])
+def test_lapw_representation_matches_oracle(precision):
+    """Eq. (APW trafo) on the GPU, V_GG'(k) = (S c) V^x (c^H S) for every k: against
+    the oracle's transform of the same V^x (the transform alone, FP64, 1e-12
+    relative), and against the oracle's transform of the oracle's V^x (end to
+    end: the V^x bar carried through the two brackets)."""
+    s = S.make_system(1, mesh=(2, 2, 1), nb=10, no=4)
+    ref = oracle_v("cfg1_221_nb10", s, range(s.n_k))
+    Sk = [S.overlap(s, ik) for ik in range(s.n_k)]
+    with hfx.Context(s, precision=precision) as c:
+        c.load_system()
+        with pytest.raises(hfx.HfxError) as e:
+            hfx.hfx_lapw_transform_all(c.ctx)
+        assert e.value.code == hfx.HFX_EMISSING
+        c.build_all()
+        V = {ik: c.exchange(ik) for ik in range(s.n_k)}
+        bad = Sk[0].copy()
+        bad[0, 1] += 0.5
+        with pytest.raises(hfx.HfxError) as e:
+            hfx.hfx_set_overlap(c.ctx, 0, bad)
+        assert e.value.code == hfx.HFX_ENOTHERM
+        for ik in range(s.n_k):
+            hfx.hfx_set_overlap(c.ctx, ik, Sk[ik])
+        st = hfx.hfx_lapw_transform_all(c.ctx)
+        assert st["n_launches"] == 3
+        Vg = {ik: hfx.hfx_get_lapw_exchange(c.ctx, ik, s.Gk[ik].shape[0]) for ik in range(s.n_k)}
+    for ik in range(s.n_k):
+        own = O.lapw_trafo(Sk[ik], s.c[ik], V[ik])
+        assert np.abs(Vg[ik] - own).max() <= 1e-12 * np.abs(own).max()
+        full = O.lapw_trafo(Sk[ik], s.c[ik], ref[ik])
+        L = np.abs(Sk[ik] @ s.c[ik].T)            # |<chi_G|phi_n>|
+        bound = float((L.sum(axis=1)[:, None] * L.sum(axis=1)[None, :]).max())
+        tol = (TOL_FP64_REL * vmax(ref) if precision == "fp64" else TOL_SPLIT_ABS) * bound
+        assert np.abs(Vg[ik] - full).max() <= tol
+        assert np.abs(Vg[ik] - Vg[ik].conj().T).max() <= 1e-12 * np.abs(Vg[ik]).max() + tol
