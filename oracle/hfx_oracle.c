@@ -35,6 +35,7 @@ typedef struct { double re, im; } cplx;
 
 static inline cplx cmul(cplx a, cplx b) { cplx r = {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; return r; }
 static inline cplx cconjmul(cplx a, cplx b) { /* conj(a) * b */ cplx r = {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re}; return r; }
+static inline cplx cconj(cplx a) { cplx r = {a.re, -a.im}; return r; }
 static inline cplx cadd(cplx a, cplx b) { cplx r = {a.re + b.re, a.im + b.im}; return r; }
 static inline cplx cscale(cplx a, double s) { cplx r = {a.re * s, a.im * s}; return r; }
 
@@ -718,6 +719,57 @@ int ora_lapw_trafo(int npw, int nb, const double *Sd, const double *cd, const do
         }
     free(L);
     free(R);
+    return 0;
+}
+
+/* ------------------------------------------------ k.p term at q = 0 */
+
+/* Appendix A: terms of the BZ integrand of Eq. (divergent part) beyond 1/q^2 at
+ * q = 0, from first-order k.p perturbation theory, Eq. (first order kp
+ * expansion): with the momentum matrix elements p[a][m][n] = <phi_m|d_a|phi_n>
+ * (a = x, y, z) and the band energies eps[n],
+ *   D[a][m][n] = <phi_m | d/dq_a Phi_n> = -i p[a][m][n] / (eps[n] - eps[m])  (m != n),
+ * and D = 0 for m = n and for |eps[n] - eps[m]| < deg_tol (a degenerate pair,
+ * on which first-order theory does not fix the mixing).  The spherical
+ * average of the second-order term is
+ *   Abar[n1][n2] = (4 pi / 3) sum_a [ sum_{n < nocc} D[a][n1][n] conj(D[a][n2][n])
+ *                    - (n1, n2 < nocc) sum_m conj(D[a][m][n1]) D[a][m][n2] ],
+ * and it enters the q = 0 point of the discretised BZ integral (weight
+ * 4 pi / (N_k Omega) per point, 1 / (4 pi) of it for the angular average):
+ *   out[n1][n2] = -Abar[n1][n2] / (N_k Omega),
+ * the term added to V^x(k).  Inputs complex row-major; nk_omega = N_k Omega. */
+int ora_kp_term(int nb, int nocc, const double *eps, const double *pd, double nk_omega, double deg_tol, double *out) {
+    const cplx *p = (const cplx *)pd;
+    cplx *D = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)nb * nb + 1);
+    for (int a = 0; a < 3; ++a)
+        for (int m = 0; m < nb; ++m)
+            for (int n = 0; n < nb; ++n) {
+                cplx d = {0.0, 0.0};
+                double de = eps[n] - eps[m];
+                if (m != n && fabs(de) >= deg_tol) {
+                    cplx pm = p[((size_t)a * nb + m) * nb + n];
+                    d.re = pm.im / de;     /* -i (x + i y) / de = (y - i x) / de */
+                    d.im = -pm.re / de;
+                }
+                D[((size_t)a * nb + m) * nb + n] = d;
+            }
+    cplx *O = (cplx *)out;
+    for (int n1 = 0; n1 < nb; ++n1)
+        for (int n2 = 0; n2 < nb; ++n2) {
+            cplx acc = {0.0, 0.0};
+            for (int a = 0; a < 3; ++a) {
+                const cplx *Da = D + (size_t)a * nb * nb;
+                for (int n = 0; n < nocc; ++n) acc = cadd(acc, cmul(Da[(size_t)n1 * nb + n], cconj(Da[(size_t)n2 * nb + n])));
+                if (n1 < nocc && n2 < nocc)
+                    for (int m = 0; m < nb; ++m) {
+                        cplx t = cconjmul(Da[(size_t)m * nb + n1], Da[(size_t)m * nb + n2]);
+                        acc.re -= t.re;
+                        acc.im -= t.im;
+                    }
+            }
+            O[(size_t)n1 * nb + n2] = cscale(acc, -(4.0 * M_PI / 3.0) / nk_omega);
+        }
+    free(D);
     return 0;
 }
 

@@ -98,6 +98,8 @@ def lib():
             L.ora_vx_part.argtypes = [vp, ip, ip, vp, ip, vp, vp]
             L.ora_lapw_trafo.restype = ip
             L.ora_lapw_trafo.argtypes = [ip, ip, vp, vp, vp, vp]
+            L.ora_kp_term.restype = ip
+            L.ora_kp_term.argtypes = [ip, ip, vp, vp, dp, dp, vp]
             L.ora_num_threads.restype = ip
             L.ora_num_threads.argtypes = []
             _lib = L
@@ -254,6 +256,18 @@ def lapw_trafo(S, c, V) -> np.ndarray:
     assert S.shape == (npw, npw) and V.shape == (nb, nb)
     out = np.zeros((npw, npw), np.complex128)
     lib().ora_lapw_trafo(npw, nb, _ptr(S), _ptr(c), _ptr(V), _ptr(out))
+    return out
+
+
+def kp_term(eps, p, nocc: int, nk_omega: float, deg_tol: float = 1e-6) -> np.ndarray:
+    """Appendix A: the k.p term at q = 0 added to V^x(k), -Abar / (N_k Omega),
+    from the band energies eps (nb) and momentum elements p (3, nb, nb)."""
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.complex128)
+    nb = eps.size
+    assert p.shape == (3, nb, nb)
+    out = np.zeros((nb, nb), np.complex128)
+    lib().ora_kp_term(nb, int(nocc), _ptr(eps), _ptr(p), float(nk_omega), float(deg_tol), _ptr(out))
     return out
 
 

@@ -234,6 +234,21 @@ def overlap(sysm, ik: int, seed: Optional[int] = None) -> np.ndarray:
     return 0.5 * (s + s.conj().T)
 
 
+def momentum(sysm, ik: int, seed: Optional[int] = None):
+    """Seeded band energies (ascending, occupied below a gap of 0.2 Ha) and
+    anti-Hermitian momentum matrix elements p[a][m][n] = <phi_m|d_a|phi_n>
+    (a = x, y, z; entries ~0.3 bohr^-1) of the bands of k, standing in for the
+    inputs of the k.p term at q = 0."""
+    nb, no = int(sysm.n_bands[ik]), int(sysm.n_occ[ik])
+    rng = np.random.Generator(np.random.PCG64((sysm.seed if seed is None else seed) * 1000 + 500 + ik))
+    occ = np.sort(rng.uniform(-1.0, 0.0, no))
+    emp = np.sort(rng.uniform(0.2, 2.0, nb - no))
+    eps = np.concatenate([occ, emp])
+    w = 0.3 * _cn(rng, (3, nb, nb))
+    p = 0.5 * (w - np.conj(np.swapaxes(w, 1, 2)))
+    return eps, p
+
+
 def sphere_gap(lattice, pos_frac, rmt) -> float:
     """Smallest |R_i - R_j - T| - S_i - S_j over atom pairs and lattice shifts
     (negative means overlapping muffin-tin spheres)."""

@@ -454,3 +454,59 @@ def test_lapw_trafo_of_unit_band_matrix_is_a_projector():
     Pm = np.linalg.solve(S, Vgg)
     assert np.abs(Pm @ Pm - Pm).max() < 1e-12
     assert abs(np.trace(Pm) - nb) < 1e-12
+
+
+# ---------------------------------------------------------------- k.p term at q = 0 (Appendix A)
+
+def _antiherm(rng, nb):
+    w = rng.standard_normal((3, nb, nb)) + 1j * rng.standard_normal((3, nb, nb))
+    return 0.5 * (w - np.conj(np.swapaxes(w, 1, 2)))
+
+
+def test_kp_term_two_band_closed_form():
+    """Two bands, the lower occupied, p_x = [[0, x], [-x*, 0]] (and y, z alike):
+    D_10 = -i p_10 / (e_0 - e_1), so Abar_00 = -(4 pi/3) s and Abar_11 = +(4 pi/3) s with
+    s = sum_a |x_a|^2 / (e_1 - e_0)^2, and Abar_01 = 0; the term added to V^x is
+    -Abar / (N_k Omega)."""
+    x = np.array([0.3 + 0.1j, -0.2j, 0.05])
+    p = np.zeros((3, 2, 2), np.complex128)
+    p[:, 0, 1] = x
+    p[:, 1, 0] = -np.conj(x)
+    e = np.array([-0.5, 0.7])
+    nko = 123.0
+    t = O.kp_term(e, p, 1, nko)
+    s = float(np.sum(np.abs(x) ** 2)) / (e[1] - e[0]) ** 2
+    c = 4.0 * np.pi / 3.0 * s / nko
+    assert abs(t[0, 0] - c) < 1e-15 and abs(t[1, 1] + c) < 1e-15
+    assert abs(t[0, 1]) < 1e-18 and abs(t[1, 0]) < 1e-18
+
+
+def test_kp_term_vanishes_with_every_band_occupied_and_is_hermitian():
+    """D is anti-Hermitian (p is), so D D^H = D^H D: with every band of the
+    window occupied the two sums of the occupied-occupied case cancel.  With
+    some bands empty the term is Hermitian and its empty-empty block is
+    negative semi-definite (minus a Gram matrix)."""
+    rng = np.random.Generator(np.random.PCG64(21))
+    nb = 7
+    e = np.sort(rng.uniform(-1, 1, nb))
+    p = _antiherm(rng, nb)
+    assert np.abs(O.kp_term(e, p, nb, 10.0)).max() < 1e-13
+    t = O.kp_term(e, p, 3, 10.0)
+    assert np.abs(t - t.conj().T).max() < 1e-14
+    assert np.linalg.eigvalsh(t[3:, 3:]).max() < 1e-14
+    assert np.abs(O.kp_term(e, 2 * p, 3, 10.0) - 4 * t).max() < 1e-13   # quadratic in p
+    assert np.abs(O.kp_term(e + 0.37, p, 3, 10.0) - t).max() < 1e-13   # only energy differences
+
+
+def test_kp_term_skips_degenerate_pairs():
+    """First-order k.p does not fix the mixing inside a degenerate pair: such
+    pairs contribute nothing (no division by a zero energy difference)."""
+    rng = np.random.Generator(np.random.PCG64(22))
+    e = np.array([-1.0, -0.5, 0.4, 0.4, 1.0])
+    p = _antiherm(rng, 5)
+    t = O.kp_term(e, p, 2, 10.0)
+    assert np.all(np.isfinite(t))
+    p2 = p.copy()
+    p2[:, 2, 3] = 0.0
+    p2[:, 3, 2] = 0.0
+    assert np.abs(O.kp_term(e, p2, 2, 10.0) - t).max() < 1e-15
