@@ -112,6 +112,10 @@ typedef struct {
                                  (0: least padded work) */
     int tile_nb_zipw;         /* band block of the interstitial tiles: 8..40, multiple
                                  of 8 (0: fewest padded bands) */
+    int kp_term;              /* nonzero: add the k.p term at q = 0 of Appendix A to V^x
+                                 (needs hfx_set_momentum for every k) */
+    double kp_deg_tol;        /* energy difference (Ha) below which two bands count as
+                                 degenerate and their k.p mixing is left out */
     int test_fail_wait;       /* fault-injection hook for tests: nonzero makes the next
                                  build's Z^H Y kernel wait on a barrier that nothing
                                  completes; the bounded wait expires after about 1 ms,
@@ -270,6 +274,20 @@ HFX_API int hfx_get_q0_bracket(hfx_ctx *ctx, double *b);
  * HFX_EUNSUPPORTED, HFX_EDEVICE (no device or launch failure). */
 HFX_API int hfx_q0_bracket_noalloc(const double *lattice, const int *mesh, double beta, double *bracket_dev,
                                    void *stream);
+
+/* Inputs of the k.p term at q = 0 (Appendix A, Eq. first order kp expansion)
+ * for the bands of k:
+ *   eps  [n_bands] band energies (Ha)
+ *   p    [3][n_bands][n_bands] complex momentum matrix elements
+ *        <phi_m| d/dr_a |phi_n> (a = x, y, z), anti-Hermitian in (m, n) (checked
+ *        against herm_tol, HFX_EINVAL).
+ * With opt.kp_term the build adds to V^x(k) the term -Abar/(N_k Omega): Abar is
+ * the spherical average of the second-order terms of the integrand of
+ * Eq. (divergent part), from D_mn = -i p_mn / (eps_n - eps_m) (pairs closer than
+ * kp_deg_tol left out), for occupied (n1, n2)
+ *   (4 pi/3) sum_a [sum_{n occ} D_n1n conj(D_n2n) - sum_m conj(D_mn1) D_mn2],
+ * otherwise (4 pi/3) sum_a sum_{n occ} D_n1n conj(D_n2n).  Requires hfx_set_kpoint(k). */
+HFX_API int hfx_set_momentum(hfx_ctx *ctx, int ik, const double *eps, const double *p);
 
 /* Overlap matrix S_GG'(k) = <chi_G|chi_G'> of the LAPW basis functions of k
  * (Eq. APW Hamiltonian, Sec. III.A), npw x npw complex, Hermitian (checked,

@@ -87,6 +87,8 @@ void hfx_default_options(hfx_options *opt) {
     opt->device = 0;
     opt->work_bytes = 0;
     opt->use_graph = 1;
+    opt->kp_term = 0;
+    opt->kp_deg_tol = 1e-6;
     opt->tile_nb_zhy = 0;
     opt->tile_nb_zipw = 0;
     opt->test_fail_wait = 0;
@@ -131,6 +133,7 @@ int hfx_create(const hfx_system *sys, const hfx_options *opt_in, hfx_ctx **out) 
     if (opt.sparse < 0 || opt.sparse > 2 || !(opt.beta > 0.0 && opt.beta < 1.0)) return HFX_EINVAL;
     if ((opt.tile_nb_zhy && !gemm2_check_nb(opt.tile_nb_zhy)) || (opt.tile_nb_zipw && !zipw_tc_valid_nb(opt.tile_nb_zipw)))
         return HFX_EINVAL;
+    if (!(opt.kp_deg_tol >= 0.0) || !std::isfinite(opt.kp_deg_tol)) return HFX_EINVAL;
 
     hfx_ctx *ctx = new (std::nothrow) hfx_ctx();
     if (!ctx) return HFX_ENOMEM;
@@ -272,6 +275,7 @@ int hfx_set_kpoint(hfx_ctx *ctx, int ik, int n_bands, int n_occ, int npw, const 
     bool gchanged = !k.set || k.G.size() != (size_t)3 * npw || std::memcmp(k.G.data(), G, sizeof(int) * 3 * npw) != 0;
     if (gchanged || k.nb != n_bands || k.no != n_occ || k.npw != npw) ++ctx->struct_epoch;
     if (gchanged) k.G.assign(G, G + 3 * npw);
+    if (k.nb != n_bands) k.kp_set = false;   // the k.p inputs belong to the old band window
     k.nb = n_bands;
     k.no = n_occ;
     k.npw = npw;
@@ -331,6 +335,40 @@ int hfx_set_coulomb(hfx_ctx *ctx, int iq, int n_ipw, const int *G_aux, const dou
     return HFX_OK;
 }
 
+int hfx_set_momentum(hfx_ctx *ctx, int ik, const double *eps, const double *p) {
+    if (!ctx) return HFX_EINVAL;
+    if (ik < 0 || ik >= ctx->nk || !eps || !p) return set_err(ctx, HFX_EINVAL, "set_momentum: bad k or pointer");
+    KPoint &k = ctx->kp[ik];
+    if (!k.set) return set_err(ctx, HFX_EMISSING, "set_momentum: set_kpoint(k) comes first");
+    const int nb = k.nb;
+    const size_t np = (size_t)3 * nb * nb;
+    if (!finite_all(eps, nb) || !finite_all(p, 2 * np)) return set_err(ctx, HFX_ENONFINITE, "set_momentum: non-finite value");
+    double mx = 0.0, dev = 0.0;
+    for (size_t i = 0; i < 2 * np; ++i) mx = std::max(mx, std::fabs(p[i]));
+    for (int a = 0; a < 3; ++a)
+        for (int m = 0; m < nb; ++m)
+            for (int n = 0; n <= m; ++n) {
+                const double *x = p + 2 * (((size_t)a * nb + m) * nb + n), *y = p + 2 * (((size_t)a * nb + n) * nb + m);
+                dev = std::max(dev, std::fabs(x[0] + y[0]) + std::fabs(x[1] - y[1]));
+            }
+    if (dev > ctx->opt.herm_tol * std::max(mx, 1e-300))
+        return set_err(ctx, HFX_EINVAL, "set_momentum: momentum elements are not anti-Hermitian");
+    int rc = HFX_OK;
+    if (k.kp_nb != nb) {
+        dfree(k.d_eps); dfree(k.d_p); dfree(k.d_kp);
+        k.d_eps = nullptr; k.d_p = nullptr; k.d_kp = nullptr;
+        k.kp_nb = 0;
+        if ((rc = dalloc(ctx, &k.d_eps, nb)) || (rc = dalloc(ctx, &k.d_p, np)) || (rc = dalloc(ctx, &k.d_kp, (size_t)nb * nb)))
+            return rc;
+        k.kp_nb = nb;
+    }
+    if ((rc = h2d(ctx, k.d_eps, eps, nb)) || (rc = h2d(ctx, k.d_p, reinterpret_cast<const double2 *>(p), np)) || (rc = sync(ctx)))
+        return rc;
+    k.kp_set = true;
+    ctx->built = false;
+    return HFX_OK;
+}
+
 int hfx_set_products(hfx_ctx *ctx, int ik, int iq, const double *Z) {
     if (!ctx) return HFX_EINVAL;
     if (ik < 0 || ik >= ctx->nk || iq < 0 || iq >= ctx->nk) return set_err(ctx, HFX_EINVAL, "set_products: index out of range");
@@ -365,7 +403,7 @@ void hfx_destroy(hfx_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     plan_release(ctx);
-    for (auto &k : ctx->kp) { dfree(k.d_G); dfree(k.d_c); dfree(k.d_A); }
+    for (auto &k : ctx->kp) { dfree(k.d_G); dfree(k.d_c); dfree(k.d_A); dfree(k.d_eps); dfree(k.d_p); dfree(k.d_kp); }
     for (auto &q : ctx->qp) { dfree(q.d_G); dfree(q.d_v); dfree(q.d_VD); dfree(q.d_VB); }
     for (auto &z : ctx->zover) dfree(z.second);
     for (auto &z : ctx->zkeep) dfree(z.second);

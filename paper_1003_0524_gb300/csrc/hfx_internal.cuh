@@ -80,6 +80,12 @@ struct KPoint {
     double2 *d_c = nullptr;      // [nb][npw]
     double2 *d_A = nullptr;      // [nb][n_atoms][N_lmp]
     std::vector<int> G;          // host copy (for boxes)
+    // inputs of the k.p term at q = 0 (Appendix A) and its result
+    double *d_eps = nullptr;     // [nb]
+    double2 *d_p = nullptr;      // [3][nb][nb]
+    double2 *d_kp = nullptr;     // [nb][nb]  term added to V^x
+    int kp_nb = 0;               // band count the buffers were made for
+    bool kp_set = false;
 };
 
 struct QPoint {
@@ -359,7 +365,12 @@ int zmt_tc_run_batch(hfx_ctx *ctx, const ZmtPlan &zs, const ZmtBatch &zb, const 
 void launch_reduce_pairs(const PairDesc *d_pairs, const int *d_kstart, const int *d_klist_pairs, int nk_in_batch,
                          const int *d_klist, const double *d_praw, const long long *d_praw_off, int NB, int raw_format,
                          double2 *const *d_vacc, const int *d_nb_k, int nb_max, cudaStream_t st);
+// V = -(1/N_k) Vacc - q->0 term (+ the k.p term d_kp[k] if d_kp is non-null), and E_x.
 void launch_finish(double2 *const *d_vacc, double2 *const *d_V, const int *d_nb_k, const int *d_no_k, int nk,
-                   int nb_max, double inv_nk, double q0b, int q0_on, double *d_Ex, cudaStream_t st);
+                   int nb_max, double inv_nk, double q0b, int q0_on, double2 *const *d_kp, double *d_Ex,
+                   cudaStream_t st);
+// The k.p term at q = 0 (Appendix A) of every k: -Abar / (N_k Omega) into d_kp[k].
+void launch_kp_term(const double *const *d_eps, const double2 *const *d_p, double2 *const *d_kp, const int *d_nb_k,
+                    const int *d_no_k, int nk, int nb_max, double nk_omega, double deg_tol, cudaStream_t st);
 
 }  // namespace hfx

@@ -131,6 +131,8 @@ struct BuildPlan {
     int N0 = 0, sparse = 0, nb_max = 0, no_max = 0, npw_max = 0, maxD = 0, N0pad = 0, Dpad = 0, HS = 0, RS = 0, MP = 0;
     int NB = 8;
     size_t o_A = 0, o_c = 0, o_G = 0, o_Ga = 0, o_npw = 0, o_nb = 0, o_no = 0, o_B = 0, o_T = 0, o_vacc = 0, o_V = 0;
+    bool kp = false;                  // the k.p term at q = 0 is added
+    size_t o_eps = 0, o_p = 0, o_kp = 0;
     size_t vtot = 0;
     TpPlan tp;
     ZmtPlan zmt;
@@ -196,6 +198,8 @@ uint64_t plan_signature(hfx_ctx *ctx, const std::vector<int> &kset) {
     for (auto &q : ctx->qp) { h.val(q.d_G); h.val(q.d_VD); h.val(q.d_VB); h.val(q.nipw); }
     h.val(ctx->d_T); h.val(ctx->d_R); h.val(ctx->d_gaunt); h.val(ctx->d_posf); h.val(ctx->d_err); h.val(ctx->d_Ex);
     h.val(ctx->s_ap.p); h.val(ctx->s_aexp.p);
+    h.val(ctx->opt.kp_term); h.val(ctx->opt.kp_deg_tol);
+    for (auto &k : ctx->kp) { h.val(k.d_eps); h.val(k.d_p); h.val(k.d_kp); }
     for (auto &z : ctx->zover) { h.val(z.first); h.val(z.second); }
     return h.h;
 }
@@ -278,6 +282,19 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
     pl.o_A = tab.put(hA); pl.o_c = tab.put(hc); pl.o_G = tab.put(hG); pl.o_Ga = tab.put(hGa);
     pl.o_npw = tab.put(hnpw); pl.o_nb = tab.put(hnb); pl.o_no = tab.put(hno);
     pl.o_B = tab.put(hB); pl.o_T = tab.put(hT); pl.o_vacc = tab.put(hvacc); pl.o_V = tab.put(hV);
+    if (ctx->opt.kp_term) {
+        std::vector<const double *> he(nk);
+        std::vector<const double2 *> hp(nk);
+        std::vector<double2 *> hk(nk);
+        for (int i = 0; i < nk; ++i) {
+            const KPoint &k = ctx->kp[i];
+            if (!k.kp_set || k.kp_nb != k.nb)
+                return set_err(ctx, HFX_EMISSING, "kp_term: set_momentum missing for k " + std::to_string(i));
+            he[i] = k.d_eps; hp[i] = k.d_p; hk[i] = k.d_kp;
+        }
+        pl.kp = true;
+        pl.o_eps = tab.put(he); pl.o_p = tab.put(hp); pl.o_kp = tab.put(hk);
+    }
 
     // ---- per-build products on the tensor cores (plans; their scratch is reserved below)
     if (tc) {
@@ -702,9 +719,17 @@ int plan_run(hfx_ctx *ctx, BuildPlan &pl, int keep, int fail_wait) {
         rec(ctx, bt.ev[10]);
     }
     rec(ctx, pl.e_fin0);
+    if (pl.kp) {
+        launch_kp_term(reinterpret_cast<const double *const *>(tab + pl.o_eps), reinterpret_cast<const double2 *const *>(tab + pl.o_p),
+                       reinterpret_cast<double2 *const *>(tab + pl.o_kp), reinterpret_cast<const int *>(tab + pl.o_nb),
+                       reinterpret_cast<const int *>(tab + pl.o_no), nk, pl.nb_max, nk * ctx->omega, ctx->opt.kp_deg_tol,
+                       ctx->stream);
+        ++nl;
+    }
     launch_finish(reinterpret_cast<double2 *const *>(tab + pl.o_vacc), reinterpret_cast<double2 *const *>(tab + pl.o_V),
                   reinterpret_cast<const int *>(tab + pl.o_nb), reinterpret_cast<const int *>(tab + pl.o_no), nk, pl.nb_max,
-                  1.0 / nk, ctx->q0_bracket, ctx->opt.q0_term ? 1 : 0, ctx->d_Ex, ctx->stream);
+                  1.0 / nk, ctx->q0_bracket, ctx->opt.q0_term ? 1 : 0,
+                  pl.kp ? reinterpret_cast<double2 *const *>(tab + pl.o_kp) : nullptr, ctx->d_Ex, ctx->stream);
     nl += 2;
     rec(ctx, pl.e_end);
     pl.nlaunch = nl;

@@ -51,17 +51,56 @@ __global__ void reduce_pairs_kernel(const PairDesc *__restrict__ pairs, const in
 // V = -(1/N_k) Vacc - delta_nn' f_nk b, and E_x = (1/2)(1/N_k) sum_k sum_{n<no} Re V_nn.
 __global__ void finish_kernel(double2 *const *__restrict__ vacc, double2 *const *__restrict__ Vout,
                               const int *__restrict__ nb_k, const int *__restrict__ no_k, int nk, double inv_nk,
-                              double q0b, int q0_on) {
+                              double q0b, int q0_on, double2 *const *__restrict__ kp) {
     int ik = blockIdx.y;
     int nb = nb_k[ik], no = no_k[ik];
     const double2 *A = vacc[ik];
+    const double2 *K = kp ? kp[ik] : nullptr;
     double2 *V = Vout[ik];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nb * nb; e += gridDim.x * blockDim.x) {
         int n = e / nb, n2 = e % nb;
         double2 a = A[e];
         double2 v = make_double2(-inv_nk * a.x, -inv_nk * a.y);
         if (q0_on && n == n2 && n < no) v.x -= q0b;
+        if (K) { v.x += K[e].x; v.y += K[e].y; }
         V[e] = v;
+    }
+}
+
+// D[a][m][n] = <phi_m | d/dq_a Phi_n> = -i p[a][m][n] / (eps[n] - eps[m]), zero for
+// m = n and for degenerate pairs (first-order k.p, Appendix A).
+__device__ __forceinline__ double2 kp_d(const double2 *p, const double *eps, int nb, int a, int m, int n, double tol) {
+    const double de = eps[n] - eps[m];
+    if (m == n || fabs(de) < tol) return make_double2(0.0, 0.0);
+    const double2 x = p[((size_t)a * nb + m) * nb + n];
+    return make_double2(x.y / de, -x.x / de);
+}
+
+// One thread per (k, n1, n2): the spherical average Abar of the second-order
+// terms of the integrand at q = 0 and the term -Abar / (N_k Omega) it adds to V^x.
+__global__ void kp_term_kernel(const double *const *__restrict__ eps_k, const double2 *const *__restrict__ p_k,
+                               double2 *const *__restrict__ kp_k, const int *__restrict__ nb_k,
+                               const int *__restrict__ no_k, double nk_omega, double tol) {
+    const int ik = blockIdx.y;
+    const int nb = nb_k[ik], no = no_k[ik];
+    const double *eps = eps_k[ik];
+    const double2 *p = p_k[ik];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nb * nb; e += gridDim.x * blockDim.x) {
+        const int n1 = e / nb, n2 = e % nb;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int a = 0; a < 3; ++a) {
+            for (int n = 0; n < no; ++n)
+                acc = cfma_conj(kp_d(p, eps, nb, a, n2, n, tol), kp_d(p, eps, nb, a, n1, n, tol), acc);
+            if (n1 < no && n2 < no)
+                for (int m = 0; m < nb; ++m) {
+                    const double2 t = cfma_conj(kp_d(p, eps, nb, a, m, n1, tol), kp_d(p, eps, nb, a, m, n2, tol),
+                                                make_double2(0.0, 0.0));
+                    acc.x -= t.x;
+                    acc.y -= t.y;
+                }
+        }
+        const double f = -(4.0 * 3.14159265358979323846 / 3.0) / nk_omega;
+        kp_k[ik][e] = make_double2(f * acc.x, f * acc.y);
     }
 }
 
@@ -97,12 +136,21 @@ void launch_reduce_pairs(const PairDesc *d_pairs, const int *d_kstart, const int
 }
 
 void launch_finish(double2 *const *d_vacc, double2 *const *d_V, const int *d_nb_k, const int *d_no_k, int nk,
-                   int nb_max, double inv_nk, double q0b, int q0_on, double *d_Ex, cudaStream_t st) {
+                   int nb_max, double inv_nk, double q0b, int q0_on, double2 *const *d_kp, double *d_Ex,
+                   cudaStream_t st) {
     int nx = (nb_max * nb_max + 255) / 256;
     if (nx > 64) nx = 64;
     dim3 grid((unsigned)nx, (unsigned)nk);
-    finish_kernel<<<grid, 256, 0, st>>>(d_vacc, d_V, d_nb_k, d_no_k, nk, inv_nk, q0b, q0_on);
+    finish_kernel<<<grid, 256, 0, st>>>(d_vacc, d_V, d_nb_k, d_no_k, nk, inv_nk, q0b, q0_on, d_kp);
     energy_kernel<<<1, 256, 0, st>>>(d_V, d_nb_k, d_no_k, nk, inv_nk, d_Ex);
+}
+
+void launch_kp_term(const double *const *d_eps, const double2 *const *d_p, double2 *const *d_kp, const int *d_nb_k,
+                    const int *d_no_k, int nk, int nb_max, double nk_omega, double deg_tol, cudaStream_t st) {
+    int nx = (nb_max * nb_max + 127) / 128;
+    if (nx > 1024) nx = 1024;
+    dim3 grid((unsigned)nx, (unsigned)nk);
+    kp_term_kernel<<<grid, 128, 0, st>>>(d_eps, d_p, d_kp, d_nb_k, d_no_k, nk_omega, deg_tol);
 }
 
 }  // namespace hfx

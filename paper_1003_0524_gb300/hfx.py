@@ -35,7 +35,7 @@ EXPORTS = (
     "hfx_set_products", "hfx_get_products", "hfx_build_all", "hfx_build_exchange", "hfx_get_exchange",
     "hfx_exchange_device_ptr", "hfx_get_energy", "hfx_get_q0_bracket", "hfx_destroy", "hfx_strerror",
     "hfx_last_error", "hfx_version", "hfx_q0_bracket_noalloc", "hfx_get_transform",
-    "hfx_set_overlap", "hfx_lapw_transform_all", "hfx_get_lapw_exchange",
+    "hfx_set_overlap", "hfx_lapw_transform_all", "hfx_get_lapw_exchange", "hfx_set_momentum",
 )
 
 
@@ -72,6 +72,8 @@ class hfx_options(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("tile_nb_zhy", ctypes.c_int),
         ("tile_nb_zipw", ctypes.c_int),
+        ("kp_term", ctypes.c_int),
+        ("kp_deg_tol", ctypes.c_double),
         ("test_fail_wait", ctypes.c_int),
     ]
 
@@ -133,6 +135,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.hfx_set_coulomb.argtypes = [vp, ip, ip, vp, vp, ip, ip]
     L.hfx_get_transform.restype = ip
     L.hfx_get_transform.argtypes = [vp, ip, ip, vp]
+    L.hfx_set_momentum.restype = ip
+    L.hfx_set_momentum.argtypes = [vp, ip, vp, vp]
     L.hfx_set_overlap.restype = ip
     L.hfx_set_overlap.argtypes = [vp, ip, vp, ip]
     L.hfx_lapw_transform_all.restype = ip
@@ -302,6 +306,12 @@ def hfx_q0_bracket_noalloc(lattice, mesh, beta: float, bracket_dev_ptr: int, str
         raise HfxError(code, load().hfx_strerror(code).decode())
 
 
+def hfx_set_momentum(ctx, ik: int, eps, p):
+    eps = _c(eps, np.float64)
+    p = _c(p, np.complex128)
+    _check(ctx, load().hfx_set_momentum(ctx, int(ik), eps.ctypes.data, p.ctypes.data))
+
+
 def hfx_set_overlap(ctx, ik: int, S, ld: Optional[int] = None):
     S = _c(S, np.complex128)
     _check(ctx, load().hfx_set_overlap(ctx, int(ik), S.ctypes.data, int(S.shape[1]) if ld is None else int(ld)))
@@ -336,7 +346,7 @@ class Context:
     def __init__(self, sysm, precision: str = "sliced", sparse: str = "auto", q0_term: bool = True,
                  beta: float = 0.005, stream: Optional[int] = None, device: int = 0, work_bytes: int = 0,
                  use_graph: bool = True, tile_nb_zhy: int = 0, tile_nb_zipw: int = 0, test_fail_wait: bool = False,
-                 tuning: bool = False):
+                 tuning: bool = False, kp_term: bool = False):
         """tuning: take the tile shapes of this size class from the autotuner's
         file (paper_1003_0524_gb300/tuning.json) when it has them."""
         self.tuned = None
@@ -358,6 +368,7 @@ class Context:
         opt.tile_nb_zhy = int(tile_nb_zhy)
         opt.tile_nb_zipw = int(tile_nb_zipw)
         opt.test_fail_wait = int(bool(test_fail_wait))
+        opt.kp_term = int(bool(kp_term))
         self.sys = sysm
         self.ctx = hfx_create(sysm.lattice, sysm.pos_frac, sysm.rmt, sysm.lmax, sysm.Lmax, sysm.P, sysm.mesh, opt)
 

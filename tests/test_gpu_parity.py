@@ -394,3 +394,32 @@ def test_lapw_representation_matches_oracle(precision):
         tol = (TOL_FP64_REL * vmax(ref) if precision == "fp64" else TOL_SPLIT_ABS) * bound
         assert np.abs(Vg[ik] - full).max() <= tol
         assert np.abs(Vg[ik] - Vg[ik].conj().T).max() <= 1e-12 * np.abs(Vg[ik]).max() + tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "sliced"])
+def test_kp_term_matches_oracle(precision):
+    """The k.p term at q = 0 (Appendix A) added in the build: V^x equals the
+    oracle's V^x plus the oracle's term -Abar/(N_k Omega) of every k, at each
+    build's bar; E_x follows from the diagonal.  Without hfx_set_momentum the
+    build reports HFX_EMISSING."""
+    s = S.make_system(1, mesh=(2, 2, 1), nb=10, no=4)
+    ref = oracle_v("cfg1_221_nb10", s, range(s.n_k))
+    o = O.Oracle(s)
+    nko = s.n_k * o.omega()
+    mom = [S.momentum(s, ik) for ik in range(s.n_k)]
+    ref_kp = {ik: ref[ik] + O.kp_term(mom[ik][0], mom[ik][1], int(s.n_occ[ik]), nko) for ik in range(s.n_k)}
+    with hfx.Context(s, precision=precision, kp_term=True) as c:
+        c.load_system()
+        with pytest.raises(hfx.HfxError) as e:
+            c.build_all()
+        assert e.value.code == hfx.HFX_EMISSING
+        for ik in range(s.n_k):
+            hfx.hfx_set_momentum(c.ctx, ik, *mom[ik])
+        c.build_all()
+        V = {ik: c.exchange(ik) for ik in range(s.n_k)}
+        ex = c.energy()
+    tol = TOL_FP64_REL * vmax(ref_kp) if precision == "fp64" else TOL_SPLIT_ABS
+    assert max_err(V, ref_kp) <= tol
+    assert max(np.abs(ref_kp[k] - ref[k]).max() for k in ref) > 100 * tol   # the term is visible
+    ex_ref = O.exchange_energy(s, ref_kp)
+    assert abs(ex - ex_ref) <= 0.5 * int(max(s.n_occ)) * tol
