@@ -110,8 +110,8 @@ typedef struct {
                                  the same inputs structure replay it on `stream` */
     int tile_nb_zhy;          /* band block of the Z^H Y tiles: 8..64, multiple of 8
                                  (0: least padded work) */
-    int tile_nb_zipw;         /* band block of the interstitial tiles: 8..40, multiple
-                                 of 8 (0: fewest padded bands) */
+    int tile_nb_zipw;         /* band block of the interstitial tiles: 8..64, multiple
+                                 of 8 (0: fewest padded bands up to 40) */
     int kp_term;              /* nonzero: add the k.p term at q = 0 of Appendix A to V^x
                                  (needs hfx_set_momentum for every k) */
     double kp_deg_tol;        /* energy difference (Ha) below which two bands count as

@@ -3,7 +3,7 @@
 The tensor-core kernels take two tile parameters that the library otherwise
 picks by a closed formula: the band block of the Z^H Y tiles (tile_nb_zhy, a
 multiple of 8 up to 64) and the band block of the interstitial tiles
-(tile_nb_zipw, a multiple of 8 up to 40).  Their best values depend on the
+(tile_nb_zipw, a multiple of 8 up to 64).  Their best values depend on the
 band window, the occupied count and the aux size, not on the number of k
 points: every (k, q) pair of a size class runs the same tile shapes.  The
 tuner therefore times the candidates on a part of the workload that still
@@ -29,7 +29,7 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNING_FILE = os.path.join(HERE, "tuning.json")
 NB_ZHY = (8, 16, 24, 32, 40, 48, 56, 64)
-NB_ZIPW = (8, 16, 24, 32, 40)
+NB_ZIPW = (8, 16, 24, 32, 40, 48, 56, 64)
 
 
 def size_class(sysm) -> dict:

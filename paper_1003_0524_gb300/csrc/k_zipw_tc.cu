@@ -32,9 +32,11 @@ using namespace tc;
 namespace {
 
 constexpr int ZT_BM = 128;
-constexpr int ZT_A_PLANE = 128 * 64 * 2;   // 16 KB: 128 rows x 64 K
-constexpr int ZT_GROUP = 4;                // 64-K chunks per exact group (256)
-constexpr int ZT_STAGES = 2;
+// K chunk: KSEG segments of 8 K values.  Band blocks up to 40 take 8 segments
+// (64 K, 128-byte swizzle, two stages); larger ones 4 (32 K, 64-byte swizzle,
+// three stages), so that the stages of a 64-band tile still fit
+__host__ __device__ constexpr int zt_kseg(int NB) { return NB > 40 ? 4 : 8; }
+__host__ __device__ constexpr int zt_stages(int KSEG) { return KSEG == 8 ? 2 : 3; }
 constexpr int ZT_EPI = 8;
 constexpr int ZT_SEGZ = 4;                 // z values per segment (8 K values: real and imaginary parts)
 constexpr int ZT_NCOPY = ZT_SEGZ;          // z-shifted copies of the sliced T box
@@ -202,9 +204,14 @@ template <int NB>
 __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                       ZParams p) {
     constexpr int N = 2 * NB;                            // real and imaginary output columns
+    constexpr int KSEG = zt_kseg(NB);                    // segments per K chunk
+    constexpr int KC = 8 * KSEG;                         // K values per chunk
+    constexpr int ZT_A_PLANE = 128 * KC * 2;             // 128 rows x KC K
+    constexpr int ZT_GROUP = 256 / KC;                   // chunks per exact group (256)
+    constexpr int ZT_STAGES = zt_stages(KSEG);
     constexpr int SEGB = N * 16;                         // one segment of one plane: N rows x 8 K
     constexpr int SEG4 = NPL * SEGB;                     // one segment, all planes (one bulk copy)
-    constexpr int STAGE = NPL * ZT_A_PLANE + 8 * SEG4;   // eight segments per 64-K chunk
+    constexpr int STAGE = NPL * ZT_A_PLANE + KSEG * SEG4;   // KSEG segments per chunk
     extern __shared__ __align__(1024) unsigned char zt_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(zt_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
     // B segments of every stage start as zeros: padding segments are never loaded
     for (int s = 0; s < ZT_STAGES; ++s) {
         uint4 *bz = reinterpret_cast<uint4 *>(stages + (size_t)s * STAGE + NPL * ZT_A_PLANE);
-        for (int i = threadIdx.x; i < 8 * SEG4 / 16; i += blockDim.x) bz[i] = make_uint4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < KSEG * SEG4 / 16; i += blockDim.x) bz[i] = make_uint4(0, 0, 0, 0);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
@@ -251,7 +258,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             const int gt = tl.mrow / ZT_BM, nch = p.nchunk[gt];
             const int slot = p.kslot[tl.k];
             const int2 *so = p.segoff + (size_t)gt * p.nsegp_max;
-            const int *runs = p.runs + (size_t)gt * (p.nsegp_max / 8);
+            const int *runs = p.runs + (size_t)gt * (p.nsegp_max / KSEG);
             // a segment starts at X = W_x + x - tlo_x, Y likewise, and T z index
             // Zs = W_z - tlo_z + z0: copy Zs mod 4, z block Zs / 4 -- inside the
             // box by construction
@@ -269,11 +276,11 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                 if (!ok) { stop = true; break; }
                 unsigned char *st = stages + (size_t)s * STAGE;
                 if (lane < NPL)
-                    tma_load_2d(saddr(st + lane * ZT_A_PLANE), &tmA, &full_bar[s], c * 64, lane * p.Rpad + tl.mrow);
+                    tma_load_2d(saddr(st + lane * ZT_A_PLANE), &tmA, &full_bar[s], c * KC, lane * p.Rpad + tl.mrow);
                 if (lane < live && ((starts >> lane) & 1)) {
                     const int rest = starts >> (lane + 1);
                     const int len = rest ? __ffs(rest) : live - lane;   // segments up to the next run
-                    const int2 sg = so[c * 8 + lane];
+                    const int2 sg = so[c * KSEG + lane];
                     const int Zs = bz + sg.y;
                     const int cp = Zs & (ZT_NCOPY - 1);
                     const long long cell =
@@ -297,8 +304,10 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             // A slice a times the B slices b = 0 .. 3 - a, stacked in N (the B planes
             // are contiguous), lands in the class columns (a + b) N: five MMAs per
             // K step cover the ten slice products
-            constexpr uint32_t id1 = idesc_bf16(ZT_BM, N), id2 = idesc_bf16(ZT_BM, 2 * N), id3 = idesc_bf16(ZT_BM, 3 * N);
-            static_assert(3 * N <= 256 && (N % 16) == 0, "stacked B planes exceed the MMA width");
+            constexpr bool three = 3 * N <= 256;           // a1 x (b0, b1, b2) in one MMA
+            constexpr uint32_t id1 = idesc_bf16(ZT_BM, N), id2 = idesc_bf16(ZT_BM, 2 * N),
+                               id3 = idesc_bf16(ZT_BM, three ? 3 * N : N);
+            static_assert(2 * N <= 256 && (N % 16) == 0, "stacked B planes exceed the MMA width");
             bool ok = true;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
                 const ZTile tm0 = p.tiles[t];
@@ -313,18 +322,24 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                         const uint32_t a0 = saddr(st), b0 = saddr(st + NPL * ZT_A_PLANE);
                         const bool first = c == g0;
 #pragma unroll
-                        for (int ks = 0; ks < 4; ++ks) {
+                        for (int ks = 0; ks < KSEG / 2; ++ks) {
                             // K step ks: segments 2 ks and 2 ks + 1 (B planes from plane b on)
-                            const uint64_t d0 = desc_sw128(a0) + 2 * ks;
-                            const uint64_t d1 = desc_sw128(a0 + ZT_A_PLANE) + 2 * ks;
-                            const uint64_t d2 = desc_sw128(a0 + 2 * ZT_A_PLANE) + 2 * ks;
-                            const uint64_t d3 = desc_sw128(a0 + 3 * ZT_A_PLANE) + 2 * ks;
+                            auto dsc = [](uint32_t a) { return KSEG == 8 ? desc_sw128(a) : desc_sw64(a); };
+                            const uint64_t d0 = dsc(a0) + 2 * ks;
+                            const uint64_t d1 = dsc(a0 + ZT_A_PLANE) + 2 * ks;
+                            const uint64_t d2 = dsc(a0 + 2 * ZT_A_PLANE) + 2 * ks;
+                            const uint64_t d3 = dsc(a0 + 3 * ZT_A_PLANE) + 2 * ks;
                             const uint64_t e0 = desc_ns(b0 + 2 * ks * SEG4, SEG4, 128);
                             const uint64_t e2 = desc_ns(b0 + 2 * ks * SEG4 + 2 * SEGB, SEG4, 128);
                             const uint32_t acc = (first && ks == 0) ? 0u : 1u;   // the two a = 0 MMAs set all classes
                             umma_bf16(tmem, d0, e0, id2, acc);                 // classes 0, 1
                             umma_bf16(tmem + 2 * N, d0, e2, id2, acc);         // classes 2, 3
-                            umma_bf16(tmem + N, d1, e0, id3, 1u);              // classes 1, 2, 3
+                            if (three) {
+                                umma_bf16(tmem + N, d1, e0, id3, 1u);          // classes 1, 2, 3
+                            } else {
+                                umma_bf16(tmem + N, d1, e0, id2, 1u);          // classes 1, 2
+                                umma_bf16(tmem + 3 * N, d1, e2, id1, 1u);      // class 3
+                            }
                             umma_bf16(tmem + 2 * N, d2, e0, id2, 1u);          // classes 2, 3
                             umma_bf16(tmem + 3 * N, d3, e0, id1, 1u);          // class 3
                         }
@@ -349,7 +364,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             const ZTile tl = p.tiles[t];
             const int4 W = p.wxyz[tl.w];
-            const int ngroups = (p.nchunk[tl.mrow / ZT_BM] + ZT_GROUP - 1) / ZT_GROUP;
+            const int ngroups = (p.nchunk[tl.mrow / ZT_BM] + ZT_GROUP - 1) / ZT_GROUP;   // same grouping as the MMA warp
             // everything the output of this row needs, fetched now so that the
             // dependent loads overlap the first K group instead of following it:
             // the output row g, the first column and the live bands, the scales
@@ -541,31 +556,32 @@ int zipw_tc_plan_build(hfx_ctx *ctx, const std::vector<int> &kset, int nb_max, c
     for (int t = 0; t < nmtile; ++t) nsegp_max = std::max(nsegp_max, (nseg[t] + 7) / 8 * 8);
     const int Kp = nsegp_max * 8;   // K values of an A row: 8 per segment
     const int nzb = (tdim[2] + ZT_SEGZ - 1) / ZT_SEGZ;
+    const int NBt = zipw_tc_valid_nb(nb_tile) ? nb_tile : pick_nb(nb_max);
+    const int nblk = (nb_max + NBt - 1) / NBt;
+    const int KSEG = zt_kseg(NBt);   // segments per K chunk of the kernel instance
     std::vector<int2> segtab((size_t)nmtile * nsegp_max);
     std::vector<int> nchunk(nmtile);
     for (int t = 0; t < nmtile; ++t) {
-        nchunk[t] = (nseg[t] + 7) / 8;
+        nchunk[t] = (nseg[t] + KSEG - 1) / KSEG;
         for (int s2 = 0; s2 < nsegp_max; ++s2) {
             const int4 sg = s2 < nseg[t] ? segs[t][s2] : segs[t][0];   // padding: any valid block
             segtab[(size_t)t * nsegp_max + s2] = make_int2(sg.x * tdim[1] + sg.y, sg.z);
         }
     }
-    const int NBt = zipw_tc_valid_nb(nb_tile) ? nb_tile : pick_nb(nb_max);
-    const int nblk = (nb_max + NBt - 1) / NBt;
-    // bulk-copy runs per 64-K chunk: consecutive segments of one line are
+    // bulk-copy runs per K chunk: consecutive segments of one line are
     // consecutive z blocks of T, contiguous for a single band block
-    std::vector<int> runs((size_t)nmtile * (nsegp_max / 8), 0);
+    std::vector<int> runs((size_t)nmtile * (nsegp_max / KSEG), 0);
     for (int t = 0; t < nmtile; ++t)
-        for (int c = 0; c < nsegp_max / 8; ++c) {
-            const int live = std::max(0, std::min(8, nseg[t] - 8 * c));
+        for (int c = 0; c < nsegp_max / KSEG; ++c) {
+            const int live = std::max(0, std::min(KSEG, nseg[t] - KSEG * c));
             int starts = 0;
             for (int j = 0; j < live; ++j) {
-                const int s2 = 8 * c + j;
+                const int s2 = KSEG * c + j;
                 const bool cont = j > 0 && nblk == 1 && segs[t][s2].x == segs[t][s2 - 1].x &&
                                   segs[t][s2].y == segs[t][s2 - 1].y && segs[t][s2].z == segs[t][s2 - 1].z + ZT_SEGZ;
                 if (!cont) starts |= 1 << j;
             }
-            runs[(size_t)t * (nsegp_max / 8) + c] = starts | (live << 8);
+            runs[(size_t)t * (nsegp_max / KSEG) + c] = starts | (live << 8);
         }
     // extent of every segment start, for the per-batch box check
     zb.sx0 = zb.sy0 = zb.sz0 = 1 << 29;
@@ -711,7 +727,7 @@ int zipw_tc_run_build(hfx_ctx *ctx, const ZipwBuild &zb, const char *dtab, char 
     return cuda_check(ctx, cudaGetLastError(), "zipw slices");
 }
 
-int zipw_tc_valid_nb(int nb) { return nb >= 8 && nb <= 40 && nb % 8 == 0; }
+int zipw_tc_valid_nb(int nb) { return nb >= 8 && nb <= 64 && nb % 8 == 0; }
 
 // Per batch: T slices of the batch's k and the GEMM.
 int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, const char *dtab, const char *dscr,
@@ -729,7 +745,8 @@ int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, co
     }
     if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw T slices"))) return rc;
     CUtensorMap mA;
-    if ((rc = make_map_2d(ctx, &mA, dscr + zb.s_a, (long long)NPL * zb.Rpad, zb.Kp, ZT_BM))) return rc;
+    const int KSEG = zt_kseg(zb.NBt), KC = 8 * KSEG;
+    if ((rc = make_map_2d_sw(ctx, &mA, dscr + zb.s_a, (long long)NPL * zb.Rpad, zb.Kp, ZT_BM, KC, 2 * KC))) return rc;
     ZParams p;
     p.tiles = reinterpret_cast<const ZTile *>(dtab + bt.o_tiles);
     p.ntiles = bt.ntiles;
@@ -773,8 +790,8 @@ int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, co
     auto go = [&](auto kern, int nb) {
         cudaFuncAttributes fa;
         cudaFuncGetAttributes(&fa, kern);
-        size_t smem = std::max<size_t>((size_t)ZT_STAGES * (NPL * ZT_A_PLANE + 8 * NPL * 2 * nb * 16) + 1024,
-                                       (size_t)smem_max - fa.sharedSizeBytes);
+        const size_t stage = (size_t)NPL * 128 * KC * 2 + (size_t)KSEG * NPL * 2 * nb * 16;
+        size_t smem = std::max<size_t>((size_t)zt_stages(KSEG) * stage + 1024, (size_t)smem_max - fa.sharedSizeBytes);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ev0) record_event(ev0, st);
         kern<<<grid, 64 + 32 * ZT_EPI, smem, st>>>(mA, p);
@@ -785,7 +802,10 @@ int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, co
     case 16: go(zipw_tc_kernel<16>, 16); break;
     case 24: go(zipw_tc_kernel<24>, 24); break;
     case 32: go(zipw_tc_kernel<32>, 32); break;
-    default: go(zipw_tc_kernel<40>, 40); break;
+    case 40: go(zipw_tc_kernel<40>, 40); break;
+    case 48: go(zipw_tc_kernel<48>, 48); break;
+    case 56: go(zipw_tc_kernel<56>, 56); break;
+    default: go(zipw_tc_kernel<64>, 64); break;
     }
     if (nlaunch) *nlaunch += 2;
     return cuda_check(ctx, cudaGetLastError(), "zipw tensor-core kernel");

@@ -347,11 +347,13 @@ def test_expired_device_wait_is_reported_and_recovered():
     assert max_err(V, ref) <= TOL_SPLIT_ABS
 
 
-@pytest.mark.parametrize("nb_zhy,nb_zipw", [(8, 8), (24, 16), (48, 24), (56, 32), (64, 40)])
+@pytest.mark.parametrize("nb_zhy,nb_zipw", [(8, 8), (24, 16), (48, 24), (56, 32), (64, 40), (40, 48), (16, 56),
+                                            (64, 64)])
 def test_tile_shapes_match_oracle(nb_zhy, nb_zipw):
-    """Every band block the autotuner may choose for the Z^H Y tiles (K chunks
-    of 64 up to 40 bands, of 32 above) and for the interstitial tiles gives the
-    oracle's V^x within the bar, on 72 bands (several blocks, a ragged last one)."""
+    """Every band block the autotuner may choose for the Z^H Y tiles and for the
+    interstitial tiles (both with K chunks of 64 up to 40 bands and of 32 above)
+    gives the oracle's V^x within the bar, on 72 bands (several blocks, a ragged
+    last one)."""
     s = SMALL["cfg1_nb72"]()
     ref = oracle_v("cfg1_nb72", s, range(s.n_k))
     V, _, st = gpu_v(s, "sliced", tile_nb_zhy=nb_zhy, tile_nb_zipw=nb_zipw)
