@@ -773,6 +773,72 @@ int ora_kp_term(int nb, int nocc, const double *eps, const double *pd, double nk
     return 0;
 }
 
+/* ------------------------------------------------- inversion symmetry */
+
+/* Sec. III.D: the partner of every atom under r -> -r, i.e. the atom a' whose
+ * fractional position is -R_a up to integers, with the same sphere radius;
+ * -1 where there is none.  Returns the number of atoms without a partner. */
+int ora_inv_partner(const OraSys *s, int *partner) {
+    int missing = 0;
+    for (int a = 0; a < s->n_atoms; ++a) {
+        partner[a] = -1;
+        for (int b = 0; b < s->n_atoms && partner[a] < 0; ++b) {
+            int ok = fabs(s->rmt[a] - s->rmt[b]) < 1e-12;
+            for (int x = 0; x < 3 && ok; ++x) {
+                double d = s->pos_frac[3 * a + x] + s->pos_frac[3 * b + x];
+                ok = fabs(d - floor(d + 0.5)) < 1e-8;
+            }
+            if (ok) partner[a] = b;
+        }
+        if (partner[a] < 0) ++missing;
+    }
+    return missing;
+}
+
+/* Sec. III.D, Eqs. (sym MT functions) and the M = 0 rule after them: the
+ * symmetrized MT functions M' as columns of S over the original Bloch MT
+ * functions, M'_J = sum_I S[I][J] M_I (row-major, N_aux x N_aux complex, the
+ * identity on the interstitial plane waves).  With a' the partner of a and
+ * s = (-1)^(L+M):
+ *   M'_(a,L,M,P)    = [M_(a,L,M,P) + s M_(a',L,-M,P)] / sqrt 2
+ *   M'_(a',L,-M,P)  = i [M_(a,L,M,P) - s M_(a',L,-M,P)] / sqrt 2
+ * for every M when a < a' (the reading of which atom of a pair plays "a"),
+ * and for M < 0 when a' = a; for a' = a and M = 0 the function is kept for
+ * even L and multiplied by i for odd L.  Returns -1 if an atom has no partner. */
+int ora_sym_matrix(const OraSys *s, int n_aux, double *Sout) {
+    int *partner = (int *)malloc(sizeof(int) * (s->n_atoms > 0 ? s->n_atoms : 1));
+    if (ora_inv_partner(s, partner)) { free(partner); return -1; }
+    cplx *S = (cplx *)Sout;
+    memset(S, 0, sizeof(cplx) * (size_t)n_aux * n_aux);
+    const int P = s->P, nlm = (s->Lmax + 1) * (s->Lmax + 1), nmt = n_mt(s);
+    const double h = 1.0 / sqrt(2.0);
+    for (int I = nmt; I < n_aux; ++I) S[(size_t)I * n_aux + I].re = 1.0;
+    for (int a = 0; a < s->n_atoms; ++a) {
+        const int b = partner[a];
+        for (int L = 0; L <= s->Lmax; ++L)
+            for (int M = -L; M <= L; ++M) {
+                const double sg = ((L + M) % 2 == 0) ? 1.0 : -1.0;
+                for (int p = 0; p < P; ++p) {
+                    const int A = (a * nlm + lm_idx(L, M)) * P + p;       /* M_(a,L,M,P) */
+                    const int B = (b * nlm + lm_idx(L, -M)) * P + p;      /* M_(a',L,-M,P) */
+                    if (a == b && M == 0) {
+                        if (L % 2 == 0) S[(size_t)A * n_aux + A].re = 1.0;
+                        else S[(size_t)A * n_aux + A].im = 1.0;
+                        continue;
+                    }
+                    if (!(a < b || (a == b && M < 0))) continue;       /* handled with its pair */
+                    /* column A: the first function of the pair, column B: the second */
+                    S[(size_t)A * n_aux + A].re = h;
+                    S[(size_t)B * n_aux + A].re = sg * h;
+                    S[(size_t)A * n_aux + B].im = h;
+                    S[(size_t)B * n_aux + B].im = -sg * h;
+                }
+            }
+    }
+    free(partner);
+    return 0;
+}
+
 int ora_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

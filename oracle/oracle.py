@@ -5,7 +5,10 @@ and by the CPU-baseline leg of ``bench.py``.  The product library never
 imports, links or runs anything in this directory.
 
 The binding only marshals numpy arrays into the C struct; every number is
-computed by the C code.
+computed by the C code, except one change of basis: for inversion-symmetric
+inputs (Sec. III.D) the Coulomb matrices arrive in the symmetrized MT basis
+and are taken back to the original one as v = S v' S^H with the matrix S of
+``ora_sym_matrix`` (a plain matrix product).
 """
 from __future__ import annotations
 
@@ -100,6 +103,10 @@ def lib():
             L.ora_lapw_trafo.argtypes = [ip, ip, vp, vp, vp, vp]
             L.ora_kp_term.restype = ip
             L.ora_kp_term.argtypes = [ip, ip, vp, vp, dp, dp, vp]
+            L.ora_inv_partner.restype = ip
+            L.ora_inv_partner.argtypes = [vp, vp]
+            L.ora_sym_matrix.restype = ip
+            L.ora_sym_matrix.argtypes = [vp, ip, vp]
             L.ora_num_threads.restype = ip
             L.ora_num_threads.argtypes = []
             _lib = L
@@ -162,6 +169,33 @@ class Oracle:
         self.s = s
         self._sp = ctypes.byref(s)
         assert nk == len(sysm.Gk)
+        if getattr(sysm, "inversion", False):
+            # v(q) is given over the symmetrized MT functions: v = S v' S^H
+            S = self.sym_matrix()
+            nmt = sysm.n_mt
+            full = []
+            for vq in sysm.v:
+                w = np.array(vq, dtype=np.complex128)
+                w[:nmt, :] = S @ w[:nmt, :]
+                w[:, :nmt] = w[:, :nmt] @ S.conj().T
+                full.append(w)
+            self.v = arr(np.concatenate([w.ravel() for w in full]), np.complex128)
+            s.v = _ptr(self.v)
+
+    def inv_partner(self) -> np.ndarray:
+        """Partner atom of every atom under r -> -r (-1 where none)."""
+        out = np.zeros(self.sys.n_atoms, np.int32)
+        self._L.ora_inv_partner(self._sp, _ptr(out))
+        return out
+
+    def sym_matrix(self, n_aux: int | None = None) -> np.ndarray:
+        """S with M'_J = sum_I S[I, J] M_I (Eqs. sym MT functions) over the
+        first n_aux functions of the MPB (default: the MT functions)."""
+        n = self.sys.n_mt if n_aux is None else int(n_aux)
+        S = np.zeros((n, n), np.complex128)
+        if self._L.ora_sym_matrix(self._sp, n, _ptr(S)) != 0:
+            raise ValueError("an atom has no inversion partner")
+        return S
 
     # -- thin wrappers ---------------------------------------------------
     def omega(self) -> float:

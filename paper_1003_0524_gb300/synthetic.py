@@ -28,6 +28,18 @@ Conventions (shared by every consumer):
 * v[q] shape (N_aux(q), N_aux(q)), Hermitian positive definite, in the
   original (untransformed) basis ordering above.
 
+Inversion-symmetric variants (``make_system(cfg, inversion=True)``, Sec. III.D):
+the atoms come in pairs a, a' with R_a' = -R_a up to a lattice vector T_a
+(an atom at an inversion centre is its own partner), partners share sphere
+radius, radial integrals and multipole moments, and the wave functions obey
+phi(-r) = phi(r)^*: real plane-wave coefficients and, with
+psi(R_a + T + x) = e^{ik.T} sum_lmp A^a_lmp u_lp(|x|) Y_lm(x) inside the spheres,
+A^{a'}_{l,-m,p} = (-1)^(l+m) e^{ik.T_a} conj(A^a_{lmp}).  v[q] is then given
+over the symmetrized MT functions of Eqs. (sym MT functions) (same labels,
+pairs ordered with the lower atom index first, M < 0 first on an atom at an
+inversion centre): a real symmetric positive-definite matrix with the block
+structure of Fig. 1, partner channels sharing their on-site blocks.
+
 Workload recipes follow the paper's systems in shape only (Sec. IV: cell sizes,
 2-10 atoms, Lmax = 4..5, band windows of tens to hundreds of bands, k meshes
 up to 6x6x6).  The paper's own crystals and FLEUR wave functions are not
@@ -85,11 +97,13 @@ CONFIGS = {
             rmt=[2.2], mesh=(2, 2, 2), nb=8, no=4, lmax=4, Lmax=4, P=2, gmax=3.0,
             aux=("cut", 2.5), sparse=False, a_scale=0.095, scale=19.7),
     1: dict(name="zincblende_2atom_k4x4x4_n40", lattice=_cubic(10.3),
-            pos=[[0.0, 0.0, 0.0], [0.25, 0.25, 0.25]], rmt=[2.2, 2.2], mesh=(4, 4, 4),
+            pos=[[0.0, 0.0, 0.0], [0.25, 0.25, 0.25]], pos_inv=[[0.125, 0.125, 0.125], [-0.125, -0.125, -0.125]],
+            rmt=[2.2, 2.2], mesh=(4, 4, 4),
             nb=40, no=8, lmax=4, Lmax=4, P=3, gmax=3.0, aux=("cut", 3.0), sparse=True,
             a_scale=0.065, scale=24.0),
     2: dict(name="zincblende_2atom_k4x4x4_uneven", lattice=_cubic(10.3),
-            pos=[[0.0, 0.0, 0.0], [0.25, 0.25, 0.25]], rmt=[2.2, 2.2], mesh=(4, 4, 4),
+            pos=[[0.0, 0.0, 0.0], [0.25, 0.25, 0.25]], pos_inv=[[0.125, 0.125, 0.125], [-0.125, -0.125, -0.125]],
+            rmt=[2.2, 2.2], mesh=(4, 4, 4),
             nb=("U", 32, 48), no=("U", 6, 10), lmax=4, Lmax=4, P=3, gmax=3.0,
             aux=("count", 520, 680), sparse=True, a_scale=0.065, scale=24.0),
     3: dict(name="perovskite_5atom_k6x6x6_n120", lattice=_cubic(7.4),
@@ -129,6 +143,7 @@ class System:
     sparse: bool
     scale: float
     seed: int
+    inversion: bool = False      # v over the symmetrized MT functions (Sec. III.D)
 
     @property
     def n_atoms(self) -> int:
@@ -209,6 +224,29 @@ def _haar_unitary(rng: np.random.Generator, n: int) -> np.ndarray:
     return q * (d / np.abs(d))[None, :]
 
 
+def _haar_orthogonal(rng: np.random.Generator, n: int) -> np.ndarray:
+    z = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r)
+    return q * np.sign(d)[None, :]
+
+
+def inversion_partners(pos_frac, rmt) -> np.ndarray:
+    """Partner of every atom under r -> -r (fractional positions summing to
+    integers, equal sphere radii); raises if an atom has none."""
+    pos = np.asarray(pos_frac, dtype=np.float64)
+    out = np.full(pos.shape[0], -1, dtype=np.int64)
+    for a in range(pos.shape[0]):
+        for b in range(pos.shape[0]):
+            d = pos[a] + pos[b]
+            if np.all(np.abs(d - np.round(d)) < 1e-8) and abs(rmt[a] - rmt[b]) < 1e-12:
+                out[a] = b
+                break
+        if out[a] < 0:
+            raise ValueError(f"atom {a} has no inversion partner")
+    return out
+
+
 def _frame_with_first_row(rng: np.random.Generator, mu: np.ndarray) -> np.ndarray:
     """A random real orthogonal P x P matrix whose first row is mu/|mu|.
 
@@ -266,11 +304,15 @@ def sphere_gap(lattice, pos_frac, rmt) -> float:
 
 
 def make_system(cfg: int | dict, *, seed: Optional[int] = None, mesh=None, nb=None,
-                no=None, aux=None, scale=None) -> System:
+                no=None, aux=None, scale=None, inversion: bool = False) -> System:
     """Build the seeded synthetic inputs of a workload.
 
     ``cfg`` is an index into CONFIGS or a dict with the same keys.  Keyword
-    overrides shrink a workload for tests (mesh, band counts, aux recipe)."""
+    overrides shrink a workload for tests (mesh, band counts, aux recipe).
+    ``inversion`` draws the inversion-symmetric variant (module docstring):
+    the positions of ``pos_inv`` where the workload gives one, its own seed."""
+    if inversion:
+        return _make_system_inv(cfg, seed=seed, mesh=mesh, nb=nb, no=no, aux=aux, scale=scale)
     if isinstance(cfg, int):
         index = cfg
         spec = dict(CONFIGS[cfg])
@@ -397,3 +439,174 @@ def make_system(cfg: int | dict, *, seed: Optional[int] = None, mesh=None, nb=No
                   Lmax=Lmax, P=P, mesh=mesh_t, gmax=float(spec["gmax"]), n_bands=n_bands,
                   n_occ=n_occ, Gk=Gk, c=c, A=A, R=R, mu=mu, Gaux=Gaux, v=v, sparse=sparse,
                   scale=s, seed=seed)
+
+
+def _make_system_inv(cfg, *, seed=None, mesh=None, nb=None, no=None, aux=None, scale=None) -> System:
+    """The inversion-symmetric variant of a workload (module docstring)."""
+    if isinstance(cfg, int):
+        index = cfg
+        spec = dict(CONFIGS[cfg])
+    else:
+        index = 99
+        spec = dict(cfg)
+    for key, val in (("mesh", mesh), ("nb", nb), ("no", no), ("aux", aux), ("scale", scale)):
+        if val is not None:
+            spec[key] = val
+    if seed is None:
+        seed = SEED_BASE + 100 + index
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    lattice = np.asarray(spec["lattice"], dtype=np.float64)
+    pos = np.asarray(spec.get("pos_inv", spec["pos"]), dtype=np.float64)
+    rmt = np.asarray(spec["rmt"], dtype=np.float64)
+    mesh_t = tuple(int(x) for x in spec["mesh"])
+    n_k = int(np.prod(mesh_t))
+    n_at = pos.shape[0]
+    lmax, Lmax, P = int(spec["lmax"]), int(spec["Lmax"]), int(spec["P"])
+    n_lmp = 2 * (lmax + 1) ** 2
+    n_lp = 2 * (lmax + 1)
+    nlm_aux = (Lmax + 1) ** 2
+    if sphere_gap(lattice, pos, rmt) <= 0.0:
+        raise ValueError("muffin-tin spheres overlap")
+    partner = inversion_partners(pos, rmt)
+
+    def draw(spec_val):
+        if isinstance(spec_val, tuple):
+            return rng.integers(spec_val[1], spec_val[2] + 1, size=n_k)
+        return np.full(n_k, int(spec_val))
+    n_bands = draw(spec["nb"]).astype(np.int32)
+    n_occ = np.minimum(draw(spec["no"]).astype(np.int32), n_bands)
+
+    a_scale = float(spec.get("a_scale", 1.0))
+    Gk, c, A = [], [], []
+    for ik in range(n_k):
+        kf = kpoint_frac(mesh_t, ik)
+        g, _ = _g_sphere(kf, lattice, float(spec["gmax"]))
+        Gk.append(g)
+        npw = g.shape[0]
+        nbk = int(n_bands[ik])
+        c.append(rng.standard_normal((nbk, npw)).astype(np.complex128) / math.sqrt(npw))
+        Ak = np.zeros((nbk, n_at, n_lmp), dtype=np.complex128)
+        for a in range(n_at):
+            b = int(partner[a])
+            if b < a:
+                continue
+            ph = np.exp(2j * math.pi * float(kf @ (pos[a] + pos[b])))   # e^{ik.T_a}
+            for l in range(lmax + 1):
+                for m in range(-l, l + 1):
+                    for p in range(2):
+                        i, j = 2 * (l * l + l + m) + p, 2 * (l * l + l - m) + p
+                        sg = 1.0 if (l + m) % 2 == 0 else -1.0
+                        if b != a:
+                            Ak[:, a, i] = _cn(rng, nbk) * a_scale
+                            Ak[:, b, j] = sg * ph * np.conj(Ak[:, a, i])
+                        elif m > 0:
+                            Ak[:, a, i] = _cn(rng, nbk) * a_scale
+                            Ak[:, a, j] = sg * ph * np.conj(Ak[:, a, i])
+                        elif m == 0:
+                            x = rng.standard_normal(nbk) * a_scale / math.sqrt(2.0)
+                            Ak[:, a, i] = np.exp(1j * math.pi * float(kf @ (pos[a] + pos[b]))) * (
+                                x if l % 2 == 0 else 1j * x)
+        A.append(Ak)
+
+    R = rng.standard_normal((n_at, (Lmax + 1) * P, n_lp, n_lp)) * 0.1
+    R = np.triu(R) + np.swapaxes(np.triu(R, 1), -1, -2)
+    mu = rng.standard_normal((n_at, (Lmax + 1) * P))
+    for a in range(n_at):
+        if partner[a] < a:
+            R[a] = R[partner[a]]
+            mu[a] = mu[partner[a]]
+
+    aux_spec = spec["aux"]
+    Gaux, gnorm = [], []
+    if aux_spec[0] == "count":
+        counts = rng.integers(aux_spec[1], aux_spec[2] + 1, size=n_k)
+    for iq in range(n_k):
+        qf = kpoint_frac(mesh_t, iq)
+        if aux_spec[0] == "cut":
+            g, nrm = _g_sphere(qf, lattice, float(aux_spec[1]))
+        else:
+            g, nrm = _g_count(qf, lattice, int(counts[iq]))
+        Gaux.append(g)
+        gnorm.append(nrm)
+    gp_max = max(float(x.max()) if x.size else 0.0 for x in gnorm)
+
+    s = float(spec["scale"])
+    sparse = bool(spec["sparse"])
+    n_mt = n_at * nlm_aux * P
+
+    def second(a, L, M):
+        """(a, L, M) is the second function of its pair: its channel copies the first's."""
+        b = int(partner[a])
+        return (b < a) or (b == a and M > 0)
+
+    frames = None
+    if sparse:
+        frames = [[_frame_with_first_row(rng, mu[a, L * P:(L + 1) * P]) for L in range(Lmax + 1)]
+                  for a in range(n_at)]
+        for a in range(n_at):
+            if partner[a] < a:
+                frames[a] = frames[partner[a]]
+    v = []
+    for iq in range(n_k):
+        n_ipw = Gaux[iq].shape[0]
+        if not sparse:
+            n = n_mt + n_ipw
+            kappa = rng.uniform(0.0, gp_max, size=n_mt)
+            g = np.concatenate([kappa, gnorm[iq]])
+            d = s * 4.0 * math.pi / (g * g + 0.05)
+            O = _haar_orthogonal(rng, n)
+            vq = (O * d[None, :]) @ O.T
+            v.append((0.5 * (vq + vq.T)).astype(np.complex128))
+            continue
+        D = n_at * nlm_aux + n_ipw
+        kappa = rng.uniform(0.0, gp_max, size=n_at * nlm_aux)
+        g = np.concatenate([kappa, gnorm[iq]])
+        d = s * 4.0 * math.pi / (g * g + 0.05)
+        O = _haar_orthogonal(rng, D)
+        vdd = (O * d[None, :]) @ O.T
+        vdd = 0.5 * (vdd + vdd.T)
+        lam_min = float(d.min())
+        n_aux = n_mt + n_ipw
+        vt = np.zeros((n_aux, n_aux), dtype=np.float64)
+        dense_idx = np.empty(D, dtype=np.int64)
+        for a in range(n_at):
+            for lm in range(nlm_aux):
+                dense_idx[a * nlm_aux + lm] = (a * nlm_aux + lm) * P
+        dense_idx[n_at * nlm_aux:] = n_mt + np.arange(n_ipw)
+        vt[np.ix_(dense_idx, dense_idx)] = vdd
+        if P > 1:
+            blocks = {}
+            for a in range(n_at):
+                for L in range(Lmax + 1):
+                    for M in range(-L, L + 1):
+                        if second(a, L, M):
+                            continue
+                        kap = rng.uniform(0.0, gp_max)
+                        w = rng.standard_normal((P - 1, P - 1))
+                        bc = s * 4.0 * math.pi / (kap * kap + 0.05) * 0.5 * (np.eye(P - 1) + w @ w.T / (P - 1))
+                        bc = 0.5 * (bc + bc.T)
+                        cc = rng.standard_normal(P - 1)
+                        q = float(cc @ np.linalg.solve(bc, cc))
+                        cc = cc * math.sqrt(0.25 * lam_min / q)
+                        blocks[(a, L, M)] = (bc, cc)
+            for a in range(n_at):
+                for L in range(Lmax + 1):
+                    for M in range(-L, L + 1):
+                        key = (int(partner[a]), L, -M) if second(a, L, M) else (a, L, M)
+                        bc, cc = blocks[key]
+                        base = (a * nlm_aux + L * L + L + M) * P
+                        vt[base + 1:base + P, base + 1:base + P] = bc
+                        vt[base + 1:base + P, base] = cc
+                        vt[base, base + 1:base + P] = cc
+        Fb = np.stack([frames[a][int(math.isqrt(lm))] for a in range(n_at) for lm in range(nlm_aux)])
+        nblk = Fb.shape[0]
+        vq = vt.copy()
+        vq[:n_mt] = np.einsum("bji,bjc->bic", Fb, vq[:n_mt].reshape(nblk, P, n_aux)).reshape(n_mt, n_aux)
+        vq[:, :n_mt] = np.einsum("rbj,bji->rbi", vq[:, :n_mt].reshape(n_aux, nblk, P), Fb).reshape(n_aux, n_mt)
+        v.append((0.5 * (vq + vq.T)).astype(np.complex128))
+
+    return System(name=str(spec["name"]) + "_inv", lattice=lattice, pos_frac=pos, rmt=rmt, lmax=lmax,
+                  Lmax=Lmax, P=P, mesh=mesh_t, gmax=float(spec["gmax"]), n_bands=n_bands,
+                  n_occ=n_occ, Gk=Gk, c=c, A=A, R=R, mu=mu, Gaux=Gaux, v=v, sparse=sparse,
+                  scale=s, seed=seed, inversion=True)
