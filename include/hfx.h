@@ -122,7 +122,34 @@ typedef struct {
                                  the kernel drains its copies and MMAs, frees its TMEM
                                  and returns, and the build returns HFX_ETIMEOUT.  The
                                  flag clears itself after that build. */
+    int inversion;            /* nonzero: the system has inversion symmetry and is given
+                                 in the real-valued form of Sec. III.D (see "Inversion
+                                 symmetry" below); V^x is real symmetric and the
+                                 contractions run on real operands */
 } hfx_options;
+
+/* Inversion symmetry (Sec. III.D), hfx_options.inversion != 0
+ * ------------------------------------------------------------
+ * Every atom a has a partner a' (possibly a itself) with R_a' = -R_a + T_a,
+ * T_a a lattice vector, the same sphere radius (checked at hfx_create:
+ * HFX_EINVAL), and the same radial integrals and multipole moments (checked at
+ * the build: HFX_EINVAL).  The wave functions obey phi(-r) = phi(r)^*, which
+ * with the conventions of hfx_set_kpoint reads
+ *     c_G(n,k) real,    A^{a'}_{l,-m,p}(n,k) = (-1)^(l+m) e^{i k.T_a} conj(A^a_{l,m,p}(n,k))
+ * (checked by hfx_set_kpoint within herm_tol: HFX_EINVAL).  The Coulomb matrix
+ * is given over the symmetrized MT functions of Eqs. (sym MT functions), which
+ * keep the labels (a, L, M, P) of the index convention above:
+ *     M'_(a,L,M,P)   = [M_(a,L,M,P) + s M_(a',L,-M,P)] / sqrt 2,     s = (-1)^(L+M)
+ *     M'_(a',L,-M,P) = i [M_(a,L,M,P) - s M_(a',L,-M,P)] / sqrt 2
+ * for every M when a < a', for M < 0 when a' = a, and M'_(a,L,0,P) = M or i M
+ * (L even or odd) when a' = a; the interstitial plane waves are unchanged.  In
+ * that basis v(q) is real symmetric (imaginary parts beyond herm_tol:
+ * HFX_EINVAL).  V^x is returned as before, with zero imaginary parts.  The
+ * library packs two occupied bands m, m+1 of k - q into one complex column
+ * (Z' real per band, so Z'_m + i Z'_{m+1} carries both and Re(Z^H v Z) sums
+ * their contributions), which halves the columns of every contraction; the
+ * Coulomb apply then runs on the real operand alone.  hfx_set_products and
+ * hfx_get_products are not available in this mode (HFX_EUNSUPPORTED). */
 
 /* Layout of the Coulomb matrix passed to hfx_set_coulomb. */
 enum {

@@ -34,10 +34,11 @@ NB_ZIPW = (8, 16, 24, 32, 40, 48, 56, 64)
 
 def size_class(sysm) -> dict:
     """What the tile choice depends on: band windows, occupied bands, aux and
-    plane-wave sizes, and the MT basis."""
+    plane-wave sizes, the MT basis, and the real (inversion-symmetric) path."""
     return {"nb": int(max(sysm.n_bands)), "no": int(max(sysm.n_occ)),
             "naux": int(max(sysm.n_aux(q) for q in range(sysm.n_k))),
-            "npw": int(max(g.shape[0] for g in sysm.Gk)), "n_mt": int(sysm.n_mt), "P": int(sysm.P)}
+            "npw": int(max(g.shape[0] for g in sysm.Gk)), "n_mt": int(sysm.n_mt), "P": int(sysm.P),
+            "inv": bool(getattr(sysm, "inversion", False))}
 
 
 def lookup(sysm, path: str = TUNING_FILE):
@@ -54,7 +55,7 @@ def lookup(sysm, path: str = TUNING_FILE):
     best, dist = None, None
     for e in data.get("entries", []):
         k = e.get("key", {})
-        if k.get("n_mt") != key["n_mt"] or k.get("P") != key["P"]:
+        if k.get("n_mt") != key["n_mt"] or k.get("P") != key["P"] or bool(k.get("inv", False)) != key["inv"]:
             continue
         db, da = abs(k["nb"] - key["nb"]), abs(k["naux"] - key["naux"]) / key["naux"]
         if db > 8 or da > 0.15:

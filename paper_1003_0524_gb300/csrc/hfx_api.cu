@@ -66,6 +66,47 @@ bool finite_all(const double *p, size_t n) {
     return true;
 }
 
+// Sec. III.D with the conventions of hfx_set_kpoint: phi(-r) = phi(r)^* holds
+// when the plane-wave coefficients are real and, for every atom a with partner
+// a' at -R_a + T_a, A^{a'}_{l,-m,p} = (-1)^(l+m) e^{i k.T_a} conj(A^a_{l,m,p}).
+int check_inversion_bands(hfx_ctx *ctx, int ik, int nb, int npw, const double *c, const double *A) {
+    const size_t nc = (size_t)nb * npw;
+    double cmax = 0.0, cim = 0.0;
+    for (size_t i = 0; i < nc; ++i) {
+        cmax = std::max(cmax, std::max(std::fabs(c[2 * i]), std::fabs(c[2 * i + 1])));
+        cim = std::max(cim, std::fabs(c[2 * i + 1]));
+    }
+    if (cim > ctx->opt.herm_tol * std::max(cmax, 1e-300))
+        return set_err(ctx, HFX_EINVAL, "set_kpoint: plane-wave coefficients are not real (inversion mode)");
+    const int *M = ctx->sys.mesh;
+    const double kf[3] = {(double)(ik / (M[1] * M[2])) / M[0], (double)((ik / M[2]) % M[1]) / M[1], (double)(ik % M[2]) / M[2]};
+    const int na = ctx->sys.n_atoms, nlmp = ctx->nlmp, lmax = ctx->sys.lmax;
+    double amax = 0.0, dev = 0.0;
+    for (size_t i = 0; i < (size_t)nb * na * nlmp * 2; ++i) amax = std::max(amax, std::fabs(A[i]));
+    for (int a = 0; a < na; ++a) {
+        const int b = ctx->partner[a];
+        double kt = 0.0;   // k . T_a with T_a = R_a + R_a' (an integer vector in fractional units)
+        for (int x = 0; x < 3; ++x) kt += kf[x] * std::floor(ctx->pos[3 * a + x] + ctx->pos[3 * b + x] + 0.5);
+        kt *= 2.0 * M_PI;
+        const double cr = std::cos(kt), ci = std::sin(kt);
+        for (int n = 0; n < nb; ++n)
+            for (int l = 0; l <= lmax; ++l)
+                for (int m = -l; m <= l; ++m) {
+                    const double sg = ((l + m) % 2 == 0) ? 1.0 : -1.0;
+                    for (int p = 0; p < 2; ++p) {
+                        const double *x = A + 2 * (((size_t)n * na + a) * nlmp + 2 * (l * l + l + m) + p);
+                        const double *y = A + 2 * (((size_t)n * na + b) * nlmp + 2 * (l * l + l - m) + p);
+                        // sg e^{i kt} conj(x)
+                        const double er = sg * (cr * x[0] + ci * x[1]), ei = sg * (ci * x[0] - cr * x[1]);
+                        dev = std::max(dev, std::fabs(y[0] - er) + std::fabs(y[1] - ei));
+                    }
+                }
+    }
+    if (dev > ctx->opt.herm_tol * std::max(amax, 1e-300))
+        return set_err(ctx, HFX_EINVAL, "set_kpoint: MT coefficients do not satisfy phi(-r) = phi(r)^* (inversion mode)");
+    return HFX_OK;
+}
+
 long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
 
 int sync(hfx_ctx *ctx) { return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronize"); }
@@ -92,6 +133,7 @@ void hfx_default_options(hfx_options *opt) {
     opt->tile_nb_zhy = 0;
     opt->tile_nb_zipw = 0;
     opt->test_fail_wait = 0;
+    opt->inversion = 0;
 }
 
 const char *hfx_strerror(int code) {
@@ -174,6 +216,22 @@ int hfx_create(const hfx_system *sys, const hfx_options *opt_in, hfx_ctx **out) 
                         }
                     }
     }
+    if (opt.inversion) {
+        // Sec. III.D: every atom needs a partner at -R_a (up to a lattice vector)
+        // with the same sphere radius
+        ctx->partner.assign(sys->n_atoms, -1);
+        for (int a = 0; a < sys->n_atoms; ++a) {
+            for (int b = 0; b < sys->n_atoms && ctx->partner[a] < 0; ++b) {
+                bool ok = std::fabs(sys->rmt[a] - sys->rmt[b]) < 1e-12;
+                for (int x = 0; x < 3 && ok; ++x) {
+                    const double d = sys->pos_frac[3 * a + x] + sys->pos_frac[3 * b + x];
+                    ok = std::fabs(d - std::floor(d + 0.5)) < 1e-8;
+                }
+                if (ok) ctx->partner[a] = b;
+            }
+            if (ctx->partner[a] < 0) { delete ctx; return HFX_EINVAL; }
+        }
+    }
     ctx->nk = sys->mesh[0] * sys->mesh[1] * sys->mesh[2];
     ctx->nlm = (sys->lmax + 1) * (sys->lmax + 1);
     ctx->nLM = (sys->Lmax + 1) * (sys->Lmax + 1);
@@ -185,6 +243,8 @@ int hfx_create(const hfx_system *sys, const hfx_options *opt_in, hfx_ctx **out) 
     ctx->kp.resize(ctx->nk);
     ctx->qp.resize(ctx->nk);
     ctx->rset.assign(sys->n_atoms, 0);
+    ctx->hR.assign((size_t)sys->n_atoms * (sys->Lmax + 1) * ctx->P * ctx->nlp * ctx->nlp, 0.0);
+    ctx->hmu.assign((size_t)sys->n_atoms * (sys->Lmax + 1) * ctx->P, 0.0);
     ctx->d_V.assign(ctx->nk, nullptr);
     ctx->device = opt.device;
     int rc = cuda_check(ctx, cudaSetDevice(opt.device), "cudaSetDevice");
@@ -239,6 +299,8 @@ int hfx_set_radial(hfx_ctx *ctx, int atom, const double *R, const double *mu) {
             for (int j = 0; j < i; ++j)
                 if (std::fabs(R[(size_t)t * nlp * nlp + i * nlp + j] - R[(size_t)t * nlp * nlp + j * nlp + i]) > 1e-12 * std::max(1.0, mx))
                     return set_err(ctx, HFX_EINVAL, "set_radial: R is not symmetric in (lp) <-> (l'p')");
+    std::memcpy(ctx->hR.data() + (size_t)atom * nR, R, sizeof(double) * nR);
+    std::memcpy(ctx->hmu.data() + (size_t)atom * nLP, mu, sizeof(double) * nLP);
     int rc = h2d(ctx, ctx->d_R + (size_t)atom * nR, R, nR);
     if (!rc) rc = h2d(ctx, ctx->d_mu + (size_t)atom * nLP, mu, nLP);
     if (!rc) rc = sync(ctx);
@@ -260,11 +322,41 @@ int hfx_set_kpoint(hfx_ctx *ctx, int ik, int n_bands, int n_occ, int npw, const 
         if (G[i] < -512 || G[i] > 512) return set_err(ctx, HFX_EINVAL, "set_kpoint: |G| component above 512");
     size_t nc = (size_t)n_bands * npw * 2, nA = (size_t)n_bands * ctx->sys.n_atoms * ctx->nlmp * 2;
     if (!finite_all(c, nc) || !finite_all(A, nA)) return set_err(ctx, HFX_ENONFINITE, "set_kpoint: non-finite coefficient");
+    // inversion symmetry (Sec. III.D): phi(-r) = phi(r)^*, and two occupied bands
+    // per complex column in the role m of k - q: X_j = X_{2j} - i X_{2j+1}
+    const int nom = ctx->opt.inversion ? (n_occ + 1) / 2 : n_occ;
+    const size_t nAb = (size_t)ctx->sys.n_atoms * ctx->nlmp;   // complex MT coefficients per band
+    std::vector<double2> cm, Am;
+    if (ctx->opt.inversion) {
+        int rc0 = check_inversion_bands(ctx, ik, n_bands, npw, c, A);
+        if (rc0) return rc0;
+        cm.assign((size_t)nom * npw, make_double2(0.0, 0.0));
+        Am.assign((size_t)nom * nAb, make_double2(0.0, 0.0));
+        const double2 *c2 = reinterpret_cast<const double2 *>(c), *A2 = reinterpret_cast<const double2 *>(A);
+        for (int j = 0; j < nom; ++j) {
+            const bool two = 2 * j + 1 < n_occ;
+            for (int g = 0; g < npw; ++g) {
+                const double2 x = c2[(size_t)(2 * j) * npw + g], y = two ? c2[(size_t)(2 * j + 1) * npw + g] : make_double2(0.0, 0.0);
+                cm[(size_t)j * npw + g] = make_double2(x.x + y.y, x.y - y.x);
+            }
+            for (size_t t = 0; t < nAb; ++t) {
+                const double2 x = A2[(size_t)(2 * j) * nAb + t], y = two ? A2[(size_t)(2 * j + 1) * nAb + t] : make_double2(0.0, 0.0);
+                Am[(size_t)j * nAb + t] = make_double2(x.x + y.y, x.y - y.x);
+            }
+        }
+    }
     KPoint &k = ctx->kp[ik];
+    auto drop_packed = [&]() {
+        if (k.d_cm != k.d_c) dfree(k.d_cm);
+        if (k.d_Am != k.d_A) dfree(k.d_Am);
+        k.d_cm = nullptr; k.d_Am = nullptr;
+    };
     if (k.set && (k.nb != n_bands || k.npw != npw)) {
+        drop_packed();
         dfree(k.d_G); dfree(k.d_c); dfree(k.d_A);
         k.d_G = nullptr; k.d_c = nullptr; k.d_A = nullptr;
     }
+    if (k.set && k.nom != nom) drop_packed();
     int rc = HFX_OK;
     if (!k.d_G && ((rc = dalloc(ctx, &k.d_G, (size_t)3 * npw)) || (rc = dalloc(ctx, &k.d_c, nc / 2)) ||
                    (rc = dalloc(ctx, &k.d_A, nA / 2))))
@@ -272,12 +364,25 @@ int hfx_set_kpoint(hfx_ctx *ctx, int ik, int n_bands, int n_occ, int npw, const 
     if ((rc = h2d(ctx, k.d_G, G, (size_t)3 * npw)) || (rc = h2d(ctx, k.d_c, reinterpret_cast<const double2 *>(c), nc / 2)) ||
         (rc = h2d(ctx, k.d_A, reinterpret_cast<const double2 *>(A), nA / 2)))
         return rc;
+    if (ctx->opt.inversion) {
+        if (!k.d_cm && ((rc = dalloc(ctx, &k.d_cm, std::max<size_t>(1, (size_t)nom * npw))) ||
+                        (rc = dalloc(ctx, &k.d_Am, std::max<size_t>(1, (size_t)nom * nAb)))))
+            return rc;
+        if ((rc = h2d(ctx, k.d_cm, cm.data(), cm.size())) || (rc = h2d(ctx, k.d_Am, Am.data(), Am.size())) ||
+            (rc = sync(ctx)))
+            return rc;
+    } else {
+        k.d_cm = k.d_c;
+        k.d_Am = k.d_A;
+    }
     bool gchanged = !k.set || k.G.size() != (size_t)3 * npw || std::memcmp(k.G.data(), G, sizeof(int) * 3 * npw) != 0;
     if (gchanged || k.nb != n_bands || k.no != n_occ || k.npw != npw) ++ctx->struct_epoch;
     if (gchanged) k.G.assign(G, G + 3 * npw);
     if (k.nb != n_bands) k.kp_set = false;   // the k.p inputs belong to the old band window
+    if (k.nom != nom) ++ctx->struct_epoch;
     k.nb = n_bands;
     k.no = n_occ;
+    k.nom = nom;
     k.npw = npw;
     k.set = true;
     ctx->built = false;
@@ -311,6 +416,17 @@ int hfx_set_coulomb(hfx_ctx *ctx, int iq, int n_ipw, const int *G_aux, const dou
             dev = std::max(dev, std::fabs(a[0] - b[0]) + std::fabs(a[1] + b[1]));
         }
     if (dev > ctx->opt.herm_tol * std::max(mx, 1e-300)) return set_err(ctx, HFX_ENOTHERM, "set_coulomb: v(q) is not Hermitian");
+    std::vector<double> vreal;
+    if (ctx->opt.inversion) {
+        // over the symmetrized MT functions of Sec. III.D, v(q) is real
+        double im = 0.0;
+        for (size_t i = 0; i < nv; ++i) im = std::max(im, std::fabs(vv[2 * i + 1]));
+        if (im > ctx->opt.herm_tol * std::max(mx, 1e-300))
+            return set_err(ctx, HFX_EINVAL, "set_coulomb: v(q) over the symmetrized basis is not real (inversion mode)");
+        vreal.assign(vv, vv + 2 * nv);
+        for (size_t i = 0; i < nv; ++i) vreal[2 * i + 1] = 0.0;
+        vv = vreal.data();
+    }
     QPoint &q = ctx->qp[iq];
     if (q.set && q.nipw != n_ipw) {
         dfree(q.d_G); dfree(q.d_v); dfree(q.d_VD); dfree(q.d_VB);
@@ -371,6 +487,7 @@ int hfx_set_momentum(hfx_ctx *ctx, int ik, const double *eps, const double *p) {
 
 int hfx_set_products(hfx_ctx *ctx, int ik, int iq, const double *Z) {
     if (!ctx) return HFX_EINVAL;
+    if (ctx->opt.inversion) return set_err(ctx, HFX_EUNSUPPORTED, "set_products: not available with inversion symmetry");
     if (ik < 0 || ik >= ctx->nk || iq < 0 || iq >= ctx->nk) return set_err(ctx, HFX_EINVAL, "set_products: index out of range");
     auto key = std::make_pair(ik, iq);
     auto it = ctx->zover.find(key);
@@ -403,7 +520,11 @@ void hfx_destroy(hfx_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     plan_release(ctx);
-    for (auto &k : ctx->kp) { dfree(k.d_G); dfree(k.d_c); dfree(k.d_A); dfree(k.d_eps); dfree(k.d_p); dfree(k.d_kp); }
+    for (auto &k : ctx->kp) {
+        if (k.d_cm != k.d_c) dfree(k.d_cm);
+        if (k.d_Am != k.d_A) dfree(k.d_Am);
+        dfree(k.d_G); dfree(k.d_c); dfree(k.d_A); dfree(k.d_eps); dfree(k.d_p); dfree(k.d_kp);
+    }
     for (auto &q : ctx->qp) { dfree(q.d_G); dfree(q.d_v); dfree(q.d_VD); dfree(q.d_VB); }
     for (auto &z : ctx->zover) dfree(z.second);
     for (auto &z : ctx->zkeep) dfree(z.second);
@@ -540,12 +661,33 @@ int check_ready(hfx_ctx *ctx) {
         if (!ctx->kp[i].set) return set_err(ctx, HFX_EMISSING, "set_kpoint missing for k " + std::to_string(i));
         if (!ctx->qp[i].set) return set_err(ctx, HFX_EMISSING, "set_coulomb missing for q " + std::to_string(i));
     }
+    if (ctx->opt.inversion) {
+        // partner atoms are the same species: equal radial integrals and multipoles
+        const size_t nR = ctx->hR.size() / ctx->sys.n_atoms, nmu = ctx->hmu.size() / ctx->sys.n_atoms;
+        for (int a = 0; a < ctx->sys.n_atoms; ++a) {
+            const int b = ctx->partner[a];
+            double mx = 0.0, dev = 0.0;
+            for (size_t i = 0; i < nR; ++i) {
+                mx = std::max(mx, std::fabs(ctx->hR[a * nR + i]));
+                dev = std::max(dev, std::fabs(ctx->hR[a * nR + i] - ctx->hR[b * nR + i]));
+            }
+            for (size_t i = 0; i < nmu; ++i) {
+                mx = std::max(mx, std::fabs(ctx->hmu[a * nmu + i]));
+                dev = std::max(dev, std::fabs(ctx->hmu[a * nmu + i] - ctx->hmu[b * nmu + i]));
+            }
+            if (dev > 1e-12 * std::max(mx, 1e-300))
+                return set_err(ctx, HFX_EINVAL, "inversion: atoms " + std::to_string(a) + " and " + std::to_string(b) +
+                                                    " differ in radial integrals or multipoles");
+        }
+    }
     return HFX_OK;
 }
 
 int build(hfx_ctx *ctx, const std::vector<int> &kset, int keep, hfx_stats *st) {
     int rc = check_ready(ctx);
     if (rc) return rc;
+    if (keep && ctx->opt.inversion)
+        return set_err(ctx, HFX_EUNSUPPORTED, "keep_products: not available with inversion symmetry");
     if ((rc = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice"))) return rc;
     if ((rc = prepare_coulomb(ctx)) || (rc = prepare_q0(ctx))) return rc;
     return build_run(ctx, kset, keep, st);
@@ -621,6 +763,7 @@ int hfx_get_transform(hfx_ctx *ctx, int atom, int L, double *T) {
 
 int hfx_get_products(hfx_ctx *ctx, int ik, int iq, double *Z) {
     if (!ctx) return HFX_EINVAL;
+    if (ctx->opt.inversion) return set_err(ctx, HFX_EUNSUPPORTED, "get_products: not available with inversion symmetry");
     if (ik < 0 || ik >= ctx->nk || iq < 0 || iq >= ctx->nk || !Z) return set_err(ctx, HFX_EINVAL, "get_products: bad index or pointer");
     auto it = ctx->zkeep.find(std::make_pair(ik, iq));
     if (it == ctx->zkeep.end()) return set_err(ctx, HFX_EMISSING, "get_products: build with keep_products first");

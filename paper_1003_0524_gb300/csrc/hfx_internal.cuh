@@ -79,6 +79,12 @@ struct KPoint {
     int *d_G = nullptr;          // [npw][3]
     double2 *d_c = nullptr;      // [nb][npw]
     double2 *d_A = nullptr;      // [nb][n_atoms][N_lmp]
+    // the occupied bands in their role m of k - q: d_c, d_A and no themselves,
+    // or with inversion symmetry (Sec. III.D) the packed pairs
+    // X_j = X_{2j} - i X_{2j+1} (own buffers), nom = ceil(no / 2)
+    double2 *d_cm = nullptr;     // [nom][npw]
+    double2 *d_Am = nullptr;     // [nom][n_atoms][N_lmp]
+    int nom = 0;
     std::vector<int> G;          // host copy (for boxes)
     // inputs of the k.p term at q = 0 (Appendix A) and its result
     double *d_eps = nullptr;     // [nb]
@@ -148,6 +154,8 @@ struct hfx_ctx {
     std::vector<hfx::KPoint> kp;
     std::vector<hfx::QPoint> qp;
     std::vector<char> rset;
+    std::vector<int> partner;    // inversion partner of every atom (inversion mode)
+    std::vector<double> hR, hmu; // host copies of the radial inputs (partner checks)
     double *d_R = nullptr;       // [n_atoms][(Lmax+1)P][nlp][nlp]
     double *d_mu = nullptr;      // [n_atoms][(Lmax+1)P]
     double *d_T = nullptr;       // [n_atoms][Lmax+1][P][P] multipole transforms
@@ -254,6 +262,12 @@ int launch_zipw(const PairDesc *d_pairs, const int *d_kpairs, int nk, int nb_max
 template <typename R>
 void launch_override(const double2 *d_user, const PairDesc &pr, int naux, const double *d_T, int n_atoms, int Lmax,
                      int P, int N0, int sparse, typename C2<R>::T *d_Z, long long RSc, int nmt, cudaStream_t st);
+// Sec. III.D: Z' = S^H Z on the MT rows of every column of a batch, with the
+// row operations of sym_row_ops (pairs of rows and lone rows).
+struct SymOp { int r1, r2, kind, pad; };   // kind 0: pair s = +1, 1: pair s = -1, 2: lone row times -i
+std::vector<SymOp> sym_row_ops(const hfx_ctx *ctx, int N0, int sparse);
+template <typename V>
+void launch_sym_rows(V *d_Z, long long RSc, long long ncols, const SymOp *d_ops, int nops, cudaStream_t st);
 template <typename R>
 void launch_unpermute(const typename C2<R>::T *d_Z, const PairDesc &pr, int naux, const double *d_T, int n_atoms,
                       int Lmax, int P, int N0, int sparse, long long RSc, int nmt, double2 *d_out, cudaStream_t st);
@@ -285,7 +299,9 @@ bool block_y_couples(int P, int N0);
 // GEMM1 tiles of one batch (host) and its launch: Y' = U Z for the dense-block
 // rows, U the upper triangle of v_t with half its diagonal (the slices of
 // launch_build_ap), K of every row tile from its first row on.
-int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, std::vector<unsigned char> &out);
+// real_v: v_t is real (inversion symmetry), so the real rows of Y' need only the
+// real half of K and the imaginary rows only the imaginary half.
+int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, bool real_v, std::vector<unsigned char> &out);
 int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *d_q,
                     const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc, long long NC, int N0,
                     int N0pad, int Dpad, int RS, const void *d_tiles, int ntiles);
@@ -364,7 +380,7 @@ int zmt_tc_run_batch(hfx_ctx *ctx, const ZmtPlan &zs, const ZmtBatch &zb, const 
 // ------------------------------------------------------------ kernels (finish, k_finish.cu)
 void launch_reduce_pairs(const PairDesc *d_pairs, const int *d_kstart, const int *d_klist_pairs, int nk_in_batch,
                          const int *d_klist, const double *d_praw, const long long *d_praw_off, int NB, int raw_format,
-                         double2 *const *d_vacc, const int *d_nb_k, int nb_max, cudaStream_t st);
+                         int real_part, double2 *const *d_vacc, const int *d_nb_k, int nb_max, cudaStream_t st);
 // V = -(1/N_k) Vacc - q->0 term (+ the k.p term d_kp[k] if d_kp is non-null), and E_x.
 void launch_finish(double2 *const *d_vacc, double2 *const *d_V, const int *d_nb_k, const int *d_no_k, int nk,
                    int nb_max, double inv_nk, double q0b, int q0_on, double2 *const *d_kp, double *d_Ex,

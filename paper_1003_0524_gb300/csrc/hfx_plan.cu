@@ -132,6 +132,9 @@ struct BuildPlan {
     int NB = 8;
     size_t o_A = 0, o_c = 0, o_G = 0, o_Ga = 0, o_npw = 0, o_nb = 0, o_no = 0, o_B = 0, o_T = 0, o_vacc = 0, o_V = 0;
     bool kp = false;                  // the k.p term at q = 0 is added
+    bool inv = false;                 // inversion symmetry: packed real bands (Sec. III.D)
+    size_t o_sym = 0;                 // row operations Z' = S^H Z
+    int nsym = 0;
     size_t o_eps = 0, o_p = 0, o_kp = 0;
     size_t vtot = 0;
     TpPlan tp;
@@ -198,7 +201,8 @@ uint64_t plan_signature(hfx_ctx *ctx, const std::vector<int> &kset) {
     for (auto &q : ctx->qp) { h.val(q.d_G); h.val(q.d_VD); h.val(q.d_VB); h.val(q.nipw); }
     h.val(ctx->d_T); h.val(ctx->d_R); h.val(ctx->d_gaunt); h.val(ctx->d_posf); h.val(ctx->d_err); h.val(ctx->d_Ex);
     h.val(ctx->s_ap.p); h.val(ctx->s_aexp.p);
-    h.val(ctx->opt.kp_term); h.val(ctx->opt.kp_deg_tol);
+    h.val(ctx->opt.kp_term); h.val(ctx->opt.kp_deg_tol); h.val(ctx->opt.inversion);
+    for (auto &k : ctx->kp) { h.val(k.d_cm); h.val(k.d_Am); h.val(k.nom); }
     for (auto &k : ctx->kp) { h.val(k.d_eps); h.val(k.d_p); h.val(k.d_kp); }
     for (auto &z : ctx->zover) { h.val(z.first); h.val(z.second); }
     return h.h;
@@ -222,9 +226,10 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
     for (auto &q : ctx->qp) { naux_max = std::max(naux_max, nmt + q.nipw); pl.maxD = std::max(pl.maxD, nmt + q.nipw - N0); }
     for (auto &k : ctx->kp) {
         pl.nb_max = std::max(pl.nb_max, k.nb);
-        pl.no_max = std::max(pl.no_max, k.no);
+        pl.no_max = std::max(pl.no_max, k.nom);   // occupied columns per k' (packed pairs with inversion)
         pl.npw_max = std::max(pl.npw_max, k.npw);
     }
+    pl.inv = ctx->opt.inversion != 0;
     pl.RSc = naux_max;
     pl.N0pad = (int)rup(N0, 64);
     pl.Dpad = (int)rup(pl.maxD, 128);
@@ -235,8 +240,12 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
     pl.NB = gemm2_check_nb(ctx->opt.tile_nb_zhy) ? ctx->opt.tile_nb_zhy : pick_nb_zhy(pl.nb_max);
     const int NB = pl.NB;
 
-    std::vector<int> hnpw(nk), hnb(nk), hno(nk);
-    for (int i = 0; i < nk; ++i) { hnpw[i] = ctx->kp[i].npw; hnb[i] = ctx->kp[i].nb; hno[i] = ctx->kp[i].no; }
+    // hno: occupied bands (the q->0 and k.p terms); hnom: occupied columns of k' in
+    // the projections (with inversion symmetry two real bands share a column)
+    std::vector<int> hnpw(nk), hnb(nk), hno(nk), hnom(nk);
+    for (int i = 0; i < nk; ++i) {
+        hnpw[i] = ctx->kp[i].npw; hnb[i] = ctx->kp[i].nb; hno[i] = ctx->kp[i].no; hnom[i] = ctx->kp[i].nom;
+    }
     pl.geo = boxes(ctx);
     pl.tbox = (long long)pl.geo.tdim[0] * pl.geo.tdim[1] * pl.geo.tdim[2];
     pl.dbox = (long long)pl.geo.ddim[0] * pl.geo.ddim[1] * pl.geo.ddim[2];
@@ -272,7 +281,7 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
     std::vector<V *> hB(nk), hT(nk);
     std::vector<double2 *> hvacc(nk), hV(nk);
     for (int i = 0; i < nk; ++i) {
-        hA[i] = ctx->kp[i].d_A; hc[i] = ctx->kp[i].d_c; hG[i] = ctx->kp[i].d_G; hGa[i] = ctx->qp[i].d_G;
+        hA[i] = ctx->kp[i].d_Am; hc[i] = ctx->kp[i].d_cm; hG[i] = ctx->kp[i].d_G; hGa[i] = ctx->qp[i].d_G;
         hB[i] = at<V>(ctx->s_B.p, boff[i] * sizeof(V));
         hT[i] = at<V>(ctx->s_thpsi.p, toff[i] * sizeof(V));
         hvacc[i] = at<double2>(ctx->s_vacc.p, voff[i] * sizeof(double2));
@@ -295,6 +304,11 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
         pl.kp = true;
         pl.o_eps = tab.put(he); pl.o_p = tab.put(hp); pl.o_kp = tab.put(hk);
     }
+    if (pl.inv) {
+        std::vector<SymOp> ops = sym_row_ops(ctx, N0, sparse);
+        pl.nsym = (int)ops.size();
+        pl.o_sym = tab.put(ops);
+    }
 
     // ---- per-build products on the tensor cores (plans; their scratch is reserved below)
     if (tc) {
@@ -316,7 +330,7 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
         budget = fr > reserve ? (size_t)(0.93 * (double)(fr - reserve)) : 0;
     }
     auto pair_bytes = [&](int ik, int ikp) {
-        const long long nc = (long long)hno[ikp] * hnb[ik];
+        const long long nc = (long long)hnom[ikp] * hnb[ik];
         size_t praw = tc ? (size_t)((hnb[ik] + NB - 1) / NB) * ((hnb[ik] + NB - 1) / NB) * (2 * NB) * (2 * NB) * sizeof(double)
                          : (size_t)hnb[ik] * hnb[ik] * sizeof(double2);
         size_t b = (size_t)nc * RSc * sizeof(V) + praw + (size_t)nc * RSc * sizeof(double2);
@@ -387,21 +401,26 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
             pr.iq = iq;
             fold_kq(ctx, ik, iq, &pr.ikp, pr.g0);
             pr.nb = hnb[ik];
-            pr.no = hno[pr.ikp];
+            pr.no = hnom[pr.ikp];
             pr.col0 = col;
             pr.qslot = (int)bt.qs.size() - 1;
             pr.pad = 0;
             bt.pairs.push_back(pr);
             col += (long long)pr.no * pr.nb;
-            // useful flops of the method (sparse form of Fig. 1 where used)
-            const double m = pr.no, n = pr.nb;
+            // useful flops of the method (sparse form of Fig. 1 where used): 8 per
+            // complex multiply-add, or 2 per real one over the m = n_occ(k') real
+            // bands with inversion symmetry (Sec. III.D)
+            const double m = pl.inv ? hno[pr.ikp] : pr.no, n = pr.nb, f = pl.inv ? 2.0 : 8.0;
             const double nnz = sparse ? (double)qd.D * qd.D + (double)nch * (P * P - 1) : (double)qd.naux * qd.naux;
-            pl.flops += 8.0 * m * n * (nnz + (double)qd.naux * n) + 8.0 * m * n * ctx->nlmp * nmt +
-                        8.0 * m * n * qd.nipw * hnpw[pr.ikp];
-            pl.fl_apply += 8.0 * m * n * (double)qd.D * qd.D;
-            pl.fl_apply_exec += tc ? 8.0 * m * n * 0.5 * (double)qd.D * (qd.D + 1) : 8.0 * m * n * (double)qd.D * qd.D;
-            pl.fl_zhy += 8.0 * m * n * (double)qd.naux * n;
-            pl.fl_zipw += 8.0 * m * n * (double)qd.nipw * hnpw[pr.ikp];
+            pl.flops += f * m * n * (nnz + (double)qd.naux * n) + f * m * n * ctx->nlmp * nmt +
+                        f * m * n * qd.nipw * hnpw[pr.ikp];
+            pl.fl_apply += f * m * n * (double)qd.D * qd.D;
+            // as executed: the upper triangle (sliced path), over the packed columns
+            // (two real parts of Y' per column with a real v_t)
+            const double mc = pr.no, fe = pl.inv ? 4.0 : 8.0;
+            pl.fl_apply_exec += tc ? fe * mc * n * 0.5 * (double)qd.D * (qd.D + 1) : 8.0 * mc * n * (double)qd.D * qd.D;
+            pl.fl_zhy += f * m * n * (double)qd.naux * n;
+            pl.fl_zipw += f * m * n * (double)qd.nipw * hnpw[pr.ikp];
         }
         if (!bt.qd.empty()) {
             QDesc &qp = bt.qd.back();
@@ -493,7 +512,7 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
         if (tc) {
             if ((rc = zmt_tc_plan_batch(ctx, pl.zmt, bt.pairs, RSc, tab, bt.zmt))) return rc;
             std::vector<unsigned char> t1, t2;
-            bt.n_g1t = gemm1_tiles(bt.qd.data(), nq, pl.N0pad, t1);
+            bt.n_g1t = gemm1_tiles(bt.qd.data(), nq, pl.N0pad, pl.inv, t1);
             bt.n_g2t = gemm2_tiles(bt.pairs.data(), npairs, NB, t2);
             bt.o_g1t = tab.put(t1);
             bt.o_g2t = tab.put(t2);
@@ -644,6 +663,10 @@ int plan_run(hfx_ctx *ctx, BuildPlan &pl, int keep, int fail_wait) {
             rec(ctx, bt.ev[3]);
             ++nl;
         }
+        if (pl.inv) {   // Z' = S^H Z on the MT rows (Sec. III.D)
+            launch_sym_rows<V>(Zc, RSc, bt.ncols, reinterpret_cast<const SymOp *>(tab + pl.o_sym), pl.nsym, ctx->stream);
+            ++nl;
+        }
         rec(ctx, bt.ev[4]);
         for (auto &ov : bt.overrides) {
             const PairDesc &pr = bt.pairs[ov.first];
@@ -712,7 +735,8 @@ int plan_run(hfx_ctx *ctx, BuildPlan &pl, int keep, int fail_wait) {
         launch_reduce_pairs(d_pairs, reinterpret_cast<const int *>(tab + bt.o_kstart),
                             reinterpret_cast<const int *>(tab + bt.o_klp), bt.nklist,
                             reinterpret_cast<const int *>(tab + bt.o_klist), praw, d_praw_off, pl.NB, tc ? 1 : 0,
-                            reinterpret_cast<double2 *const *>(tab + pl.o_vacc), reinterpret_cast<const int *>(tab + pl.o_nb),
+                            pl.inv ? 1 : 0, reinterpret_cast<double2 *const *>(tab + pl.o_vacc),
+                            reinterpret_cast<const int *>(tab + pl.o_nb),
                             pl.nb_max, ctx->stream);
         ++nl;
         if ((rc = cuda_check(ctx, cudaGetLastError(), "q reduction"))) return rc;

@@ -573,7 +573,7 @@ int zmt_tc_plan(hfx_ctx *ctx, const std::vector<int> &kset, const std::vector<do
     zs.kbase.assign(nk, 0);
     for (int kp = 0; kp < nk; ++kp) {
         zs.kbase[kp] = (int)pk.size();
-        for (int m = 0; m < ctx->kp[kp].no; ++m) { pk.push_back(kp); pm.push_back(m); }
+        for (int m = 0; m < ctx->kp[kp].nom; ++m) { pk.push_back(kp); pm.push_back(m); }
     }
     zs.npairs_a = (int)pk.size();
     if (zs.npairs_a == 0) return HFX_OK;
@@ -590,7 +590,7 @@ int zmt_tc_plan(hfx_ctx *ctx, const std::vector<int> &kset, const std::vector<do
     for (size_t b = 0; b < blk_k.size(); ++b) zs.blocks.push_back({blk_k[b], blk_a[b]});
     std::vector<const double2 *> hA(nk), hBc(nk);
     std::vector<int> hnb(nk);
-    for (int k = 0; k < nk; ++k) { hA[k] = ctx->kp[k].d_A; hBc[k] = hB[k]; hnb[k] = ctx->kp[k].nb; }
+    for (int k = 0; k < nk; ++k) { hA[k] = ctx->kp[k].d_Am; hBc[k] = hB[k]; hnb[k] = ctx->kp[k].nb; }
     zs.o_ro = tab.put(rowoff);
     zs.o_pk = tab.put(pkey);
     zs.o_bk = tab.put(blk_k);

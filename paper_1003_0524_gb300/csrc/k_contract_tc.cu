@@ -237,7 +237,11 @@ __global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *c
 // stage, three stages; the four class accumulators fill TMEM (single buffer:
 // the MMA warp waits for the epilogue to read a K group before the next).
 // Each CTA loads the A and B tiles of its own output tile.
-struct G1Tile { int qslot, mrow, ncol0, klen, iq, kbeg; };   // K of each half: [kbeg, kbeg + klen); iq: the q of A
+// K of each half: [kbeg, kbeg + klen); iq: the q of A.  half < 0: both K halves
+// (complex v_t, rows [0, D) real and [D, 2D) imaginary parts of Y');
+// half = 0 / 1 (real v_t): rows [0, D) of A' (U itself) against the real or
+// imaginary half of the Z columns, giving the real or imaginary part of Y'.
+struct G1Tile { int qslot, mrow, ncol0, klen, iq, kbeg, half; };
 
 struct G1Params {
     const G1Tile *tiles;
@@ -306,16 +310,18 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
                 if (t + (int)gridDim.x < p.ntiles) nx = p.tiles[t + gridDim.x];
                 const int qi = tl.iq;
                 int nk = tl.klen / G1_KC;
+                const int nchunk = tl.half < 0 ? 2 * nk : nk;
                 bool stop = false;
-                for (int kc = 0; kc < 2 * nk; ++kc) {
+                for (int kc = 0; kc < nchunk; ++kc) {
                     if (!mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma)) { stop = true; break; }
-                    int x = tl.kbeg + ((kc < nk) ? kc * G1_KC : p.HS + (kc - nk) * G1_KC);
+                    int xa = tl.kbeg + ((kc < nk) ? kc * G1_KC : p.HS + (kc - nk) * G1_KC), xb = xa;
+                    if (tl.half >= 0) { xa = tl.kbeg + kc * G1_KC; xb = xa + tl.half * p.HS; }
                     unsigned char *st = stages + (size_t)s * G1_STAGE;
                     mbar_expect_tx(&full_bar[s], G1_STAGE);
 #pragma unroll
                     for (int pl = 0; pl < NPL; ++pl) {
-                        tma_load_2d(saddr(st + pl * G1_A_PLANE), &tmA, &full_bar[s], x, (qi * NPL + pl) * p.MP + tl.mrow);
-                        tma_load_2d(saddr(st + NPL * G1_A_PLANE + pl * G1_B_PLANE), &tmB, &full_bar[s], x,
+                        tma_load_2d(saddr(st + pl * G1_A_PLANE), &tmA, &full_bar[s], xa, (qi * NPL + pl) * p.MP + tl.mrow);
+                        tma_load_2d(saddr(st + NPL * G1_A_PLANE + pl * G1_B_PLANE), &tmB, &full_bar[s], xb,
                                     (int)(pl * p.NC + tl.ncol0));
                     }
                     ++issued;
@@ -335,10 +341,14 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
             constexpr uint32_t id1 = idesc_bf16(G1_BM, G1_BN), id2 = idesc_bf16(G1_BM, 2 * G1_BN);
             bool ok = true;
             int nklen = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x].klen : 0;
+            int nhalf = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x].half : -1;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-                const int klen = nklen;
-                if (t + (int)gridDim.x < p.ntiles) nklen = p.tiles[t + gridDim.x].klen;   // prefetch
-                int nchunk = 2 * (klen / G1_KC);
+                const int klen = nklen, half = nhalf;
+                if (t + (int)gridDim.x < p.ntiles) {   // prefetch
+                    nklen = p.tiles[t + gridDim.x].klen;
+                    nhalf = p.tiles[t + gridDim.x].half;
+                }
+                int nchunk = (half < 0 ? 2 : 1) * (klen / G1_KC);
                 for (int g0 = 0; g0 < nchunk && ok; g0 += G1_GROUP) {
                     if (!mbar_wait(&tempty_bar, eph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
                     tc_fence_after();
@@ -380,15 +390,15 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             G1Tile tl = p.tiles[t];
             const QDesc q = p.qd[tl.qslot];
-            int nchunk = 2 * (tl.klen / G1_KC);
+            int nchunk = (tl.half < 0 ? 2 : 1) * (tl.klen / G1_KC);
             int ngroups = (nchunk + G1_GROUP - 1) / G1_GROUP;
             // output scales: the row exponent, and the exponents of the 64 columns of
             // this half (lane l holds columns l and 32 + l; the store loop shuffles
             // them), fetched at tile start so that their latency overlaps the first
             // K group instead of following the last one
             const int r = tl.mrow + quarter * 32 + lane;     // row of A' in this q: [0, D) real, [D, 2D) imaginary
-            const bool im = r >= q.D;
-            const int rr = im ? r - q.D : r;
+            const bool im = tl.half < 0 ? r >= q.D : tl.half == 1;
+            const int rr = (tl.half < 0 && im) ? r - q.D : r;
             const bool live = rr < q.D;
             const long long c0 = tl.ncol0 + half * 64, cend = q.colbase + q.ncols;
             const int ea = live ? p.aexp[(size_t)q.iq * p.MP + r] - 16 : 0;
@@ -800,24 +810,29 @@ template void launch_block_y<double2>(const QDesc *, int, const double2 *const *
 // are up to ~140 MB on the largest workloads, more than L2), and the Re and Im
 // rows of one Y column meet in L2.
 constexpr int G1_COLGROUP = 8;
-int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, std::vector<unsigned char> &out) {
+int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, bool real_v, std::vector<unsigned char> &out) {
     std::vector<G1Tile> tiles;
     for (int s = 0; s < nq; ++s) {
         const QDesc &q = h_q[s];
-        int mt = (2 * q.D + G1_BM - 1) / G1_BM;   // row tiles over the D real and D imaginary rows
+        // row tiles over the D real and D imaginary rows; with a real v_t over
+        // the D rows of U, each taken once per half of the Z columns
+        const int rows = real_v ? q.D : 2 * q.D;
+        const int mt = (rows + G1_BM - 1) / G1_BM;
         std::vector<int> kbeg(mt), klen(mt);
         for (int i = 0; i < mt; ++i) {
-            const int r0 = i * G1_BM, r1 = std::min(2 * q.D, r0 + G1_BM);   // rows [r0, r1)
-            const int rmin = (r0 < q.D && r1 > q.D) ? 0 : (r0 < q.D ? r0 : r0 - q.D);
+            const int r0 = i * G1_BM, r1 = std::min(rows, r0 + G1_BM);   // rows [r0, r1)
+            const int rmin = real_v ? r0 : ((r0 < q.D && r1 > q.D) ? 0 : (r0 < q.D ? r0 : r0 - q.D));
             kbeg[i] = N0pad + rmin / G1_KC * G1_KC;
             klen[i] = (N0pad + q.D - kbeg[i] + G1_KC - 1) / G1_KC * G1_KC;
         }
         for (long long g0 = 0; g0 < q.ncols; g0 += (long long)G1_BN * G1_COLGROUP)
             for (int i = 0; i < mt; ++i)
-                for (int j = 0; j < G1_COLGROUP; ++j) {
-                    const long long n0 = g0 + (long long)j * G1_BN;
-                    if (n0 < q.ncols) tiles.push_back(G1Tile{s, i * G1_BM, (int)(q.colbase + n0), klen[i], q.iq, kbeg[i]});
-                }
+                for (int h = real_v ? 0 : -1; h < (real_v ? 2 : 0); ++h)
+                    for (int j = 0; j < G1_COLGROUP; ++j) {
+                        const long long n0 = g0 + (long long)j * G1_BN;
+                        if (n0 < q.ncols)
+                            tiles.push_back(G1Tile{s, i * G1_BM, (int)(q.colbase + n0), klen[i], q.iq, kbeg[i], h});
+                    }
     }
     out.assign(reinterpret_cast<const unsigned char *>(tiles.data()),
                reinterpret_cast<const unsigned char *>(tiles.data()) + tiles.size() * sizeof(G1Tile));

@@ -8,10 +8,14 @@ namespace {
 
 // Vacc[k] += sum_{pairs of k in this batch, ascending q} P_pair, where the
 // tensor-core tiles (raw_format 1) hold P' = Z^H U Z and P_pair = P' + P'^H.
+// With real_part (inversion symmetry, two real bands packed per column, Sec.
+// III.D) only the real part is the pair's term; the imaginary part holds the
+// cross products of the two bands and is dropped.
 __global__ void reduce_pairs_kernel(const PairDesc *__restrict__ pairs, const int *__restrict__ kstart,
                                     const int *__restrict__ klist_pairs, const int *__restrict__ klist,
                                     const double *__restrict__ praw, const long long *__restrict__ praw_off, int NB,
-                                    int raw_format, double2 *const *__restrict__ vacc, const int *__restrict__ nb_k) {
+                                    int raw_format, int real_part, double2 *const *__restrict__ vacc,
+                                    const int *__restrict__ nb_k) {
     int slot = blockIdx.y;
     int ik = klist[slot];
     int nb = nb_k[ik];
@@ -27,7 +31,7 @@ __global__ void reduce_pairs_kernel(const PairDesc *__restrict__ pairs, const in
                 const double2 *Pc = reinterpret_cast<const double2 *>(P);
                 double2 v = Pc[(size_t)n * nb + n2];
                 acc.x += v.x;
-                acc.y += v.y;
+                if (!real_part) acc.y += v.y;
             } else {
                 // real-embedded tiles of P' = Z^H U Z; the pair's term is P' + P'^H
                 int nblk = (nb + NB - 1) / NB;
@@ -40,7 +44,7 @@ __global__ void reduce_pairs_kernel(const PairDesc *__restrict__ pairs, const in
                 double qr = t1[(size_t)b * W + a] + t1[(size_t)(NB + b) * W + NB + a];
                 double qim = t1[(size_t)b * W + NB + a] - t1[(size_t)(NB + b) * W + a];
                 acc.x += pr + qr;
-                acc.y += pim - qim;
+                if (!real_part) acc.y += pim - qim;
             }
         }
         V[e] = acc;
@@ -126,13 +130,13 @@ __global__ void energy_kernel(double2 *const *__restrict__ Vout, const int *__re
 
 void launch_reduce_pairs(const PairDesc *d_pairs, const int *d_kstart, const int *d_klist_pairs, int nk_in_batch,
                          const int *d_klist, const double *d_praw, const long long *d_praw_off, int NB, int raw_format,
-                         double2 *const *d_vacc, const int *d_nb_k, int nb_max, cudaStream_t st) {
+                         int real_part, double2 *const *d_vacc, const int *d_nb_k, int nb_max, cudaStream_t st) {
     if (nk_in_batch == 0) return;
     int nx = (nb_max * nb_max + 255) / 256;
     if (nx > 64) nx = 64;
     dim3 grid((unsigned)nx, (unsigned)nk_in_batch);
     reduce_pairs_kernel<<<grid, 256, 0, st>>>(d_pairs, d_kstart, d_klist_pairs, d_klist, d_praw, d_praw_off, NB,
-                                              raw_format, d_vacc, d_nb_k);
+                                              raw_format, real_part, d_vacc, d_nb_k);
 }
 
 void launch_finish(double2 *const *d_vacc, double2 *const *d_V, const int *d_nb_k, const int *d_no_k, int nk,

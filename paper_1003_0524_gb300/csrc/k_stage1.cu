@@ -11,6 +11,8 @@
 //
 // Output Zc[col][row]: column col = pair col0 + m*nb + n, row in the permuted
 // MPB order [mu=0 | mu!=0 | IPW] (sparse) or the original order (dense).
+#include <algorithm>
+
 #include "hfx_internal.cuh"
 
 namespace hfx {
@@ -330,6 +332,34 @@ __global__ void unpermute_kernel(const typename C2<R>::T *__restrict__ Z, PairDe
     }
 }
 
+// Sec. III.D, Eqs. (sym MT functions): Z' = S^H Z, Z'_I = sum_J conj(S_JI) Z_J.
+// For a pair of rows (the first and second function of one symmetrized pair,
+// s = (-1)^(L+M)):  first' = (z1 + s z2)/sqrt2,  second' = -i (z1 - s z2)/sqrt2;
+// a lone row (M = 0, odd L, atom at an inversion centre) becomes -i z.
+template <typename V>
+__global__ void sym_rows_kernel(V *__restrict__ Z, long long RSc, long long ncols, const SymOp *__restrict__ ops,
+                                int nops) {
+    const double h = 0.70710678118654752440;
+    const long long total = ncols * nops;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long col = e / nops;
+        const SymOp op = ops[e % nops];
+        V *z = Z + col * RSc;
+        const V a = z[op.r1];
+        if (op.kind == 2) {
+            z[op.r1] = ld_c<decltype(a.x)>(make_double2((double)a.y, -(double)a.x));
+            continue;
+        }
+        const V b = z[op.r2];
+        const double sg = op.kind == 0 ? 1.0 : -1.0;
+        const double fx = ((double)a.x + sg * b.x) * h, fy = ((double)a.y + sg * b.y) * h;
+        const double dx = ((double)a.x - sg * b.x) * h, dy = ((double)a.y - sg * b.y) * h;
+        z[op.r1] = ld_c<decltype(a.x)>(make_double2(fx, fy));
+        z[op.r2] = ld_c<decltype(a.x)>(make_double2(dy, -dx));
+    }
+}
+
 int grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     if (g > 152LL * 32) g = 152LL * 32;
@@ -338,6 +368,45 @@ int grid_for(long long n, int block) {
 }
 
 }  // namespace
+
+// The row operations of Z' = S^H Z in the batch row layout: MT function
+// (a, L, M, i) of the transformed (sparse) or original (dense) order sits in row
+// N0 + ch (sparse, i = 0), ch (P - 1) + i - 1 (sparse, i >= 1) or ch P + i
+// (dense), ch = a (Lmax+1)^2 + L^2 + L + M.  Partner channels share their
+// multipole transform (equal multipoles), so the pairing acts index by index.
+std::vector<SymOp> sym_row_ops(const hfx_ctx *ctx, int N0, int sparse) {
+    std::vector<SymOp> ops;
+    const int P = ctx->P, Lmax = ctx->sys.Lmax, nLM = ctx->nLM;
+    auto row = [&](int a, int L, int M, int i) {
+        const int ch = a * nLM + L * L + L + M;
+        if (!sparse) return ch * P + i;
+        return i == 0 ? N0 + ch : ch * (P - 1) + i - 1;
+    };
+    for (int a = 0; a < ctx->sys.n_atoms; ++a) {
+        const int b = ctx->partner[a];
+        for (int L = 0; L <= Lmax; ++L)
+            for (int M = -L; M <= L; ++M) {
+                const int kind = ((L + M) % 2 == 0) ? 0 : 1;
+                for (int i = 0; i < P; ++i) {
+                    if (a == b && M == 0) {
+                        if (L % 2) ops.push_back(SymOp{row(a, L, 0, i), -1, 2, 0});
+                    } else if (a < b || (a == b && M < 0)) {
+                        ops.push_back(SymOp{row(a, L, M, i), row(b, L, -M, i), kind, 0});
+                    }
+                }
+            }
+    }
+    std::sort(ops.begin(), ops.end(), [](const SymOp &x, const SymOp &y) { return x.r1 < y.r1; });
+    return ops;
+}
+
+template <typename V>
+void launch_sym_rows(V *d_Z, long long RSc, long long ncols, const SymOp *d_ops, int nops, cudaStream_t st) {
+    if (nops == 0 || ncols == 0) return;
+    sym_rows_kernel<V><<<grid_for(ncols * nops, 256), 256, 0, st>>>(d_Z, RSc, ncols, d_ops, nops);
+}
+template void launch_sym_rows<float2>(float2 *, long long, long long, const SymOp *, int, cudaStream_t);
+template void launch_sym_rows<double2>(double2 *, long long, long long, const SymOp *, int, cudaStream_t);
 
 template <typename R>
 void launch_thetapsi(const double2 *d_theta, const int dlo[3], const int ddim[3], const int tlo[3], const int tdim[3],

@@ -518,7 +518,7 @@ int zipw_tc_plan_build(hfx_ctx *ctx, const std::vector<int> &kset, int nb_max, c
     zb.rowbase.assign(nk, -1);
     for (int kp : korder) {
         zb.rowbase[kp] = (int)rowk.size();
-        for (int m = 0; m < ctx->kp[kp].no; ++m) { rowk.push_back(kp); rowm.push_back(m); }
+        for (int m = 0; m < ctx->kp[kp].nom; ++m) { rowk.push_back(kp); rowm.push_back(m); }
     }
     const int R = (int)rowk.size();
     if (R == 0) return HFX_OK;

@@ -75,6 +75,7 @@ class hfx_options(ctypes.Structure):
         ("kp_term", ctypes.c_int),
         ("kp_deg_tol", ctypes.c_double),
         ("test_fail_wait", ctypes.c_int),
+        ("inversion", ctypes.c_int),
     ]
 
 
@@ -346,9 +347,11 @@ class Context:
     def __init__(self, sysm, precision: str = "sliced", sparse: str = "auto", q0_term: bool = True,
                  beta: float = 0.005, stream: Optional[int] = None, device: int = 0, work_bytes: int = 0,
                  use_graph: bool = True, tile_nb_zhy: int = 0, tile_nb_zipw: int = 0, test_fail_wait: bool = False,
-                 tuning: bool = False, kp_term: bool = False):
+                 tuning: bool = False, kp_term: bool = False, inversion: Optional[bool] = None):
         """tuning: take the tile shapes of this size class from the autotuner's
-        file (paper_1003_0524_gb300/tuning.json) when it has them."""
+        file (paper_1003_0524_gb300/tuning.json) when it has them.
+        inversion: the real-valued path of an inversion-symmetric system
+        (default: what the system says, ``sysm.inversion``)."""
         self.tuned = None
         if tuning and not tile_nb_zhy and not tile_nb_zipw:
             from .autotune import lookup
@@ -369,6 +372,7 @@ class Context:
         opt.tile_nb_zipw = int(tile_nb_zipw)
         opt.test_fail_wait = int(bool(test_fail_wait))
         opt.kp_term = int(bool(kp_term))
+        opt.inversion = int(bool(getattr(sysm, "inversion", False) if inversion is None else inversion))
         self.sys = sysm
         self.ctx = hfx_create(sysm.lattice, sysm.pos_frac, sysm.rmt, sysm.lmax, sysm.Lmax, sysm.P, sysm.mesh, opt)
 
