@@ -391,6 +391,8 @@ def run_ours(args):
         extra["lapw_transform"] = lapw
     if args.extra_config2 and args.config != 2 and not args.mesh:
         extra["config2"] = measure_config2(args, stream, local)
+    if args.extra_inversion and args.precision == "sliced" and not args.mesh:
+        extra["inversion"] = measure_inversion(args, stream, local, ms)
 
     line = None
     if rank == 0:
@@ -514,6 +516,62 @@ def measure_config2(args, stream, local):
             "max_abs_dV_vs_oracle_k5": float(np.abs(V5 - ref).max())}
 
 
+def measure_inversion(args, stream, local, ms_complex):
+    """The inversion-symmetric variant of the workload (same cell sizes, band
+    windows and aux sizes; five atom pairs on config 4) on the real path of
+    Sec. III.D: a few graph-replayed steps, the dominant kernel's fraction of the
+    tensor peak, and V^x(k = 0) against the plain FP64 GPU build of that k."""
+    import numpy as np
+    import torch
+
+    from paper_1003_0524_gb300 import hfx
+    from paper_1003_0524_gb300 import synthetic as S
+    t0 = time.perf_counter()
+    s = S.make_system(args.config, inversion=True)
+    t_gen = time.perf_counter() - t0
+    with hfx.Context(s, precision="sliced", stream=stream, device=local, tuning=True) as c:
+        tuned = c.tuned
+        c.load_system()
+        for _ in range(3):
+            c.build_all()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 3
+        e0.record()
+        sts = [c.build_all() for _ in range(n)]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        V0 = c.exchange(0)
+        imag_max = max(float(np.abs(c.exchange(ik).imag).max()) for ik in range(s.n_k))
+    st = sts[0]
+    peaks, peak_kind = _peaks()
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    ms_apply = statistics.mean(x["ms_apply"] for x in sts)
+    with hfx.Context(s, precision="fp64", stream=stream, device=local) as c64:
+        c64.load_system()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        V64 = c64.build_exchange(0)
+        f1.record()
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) * s.n_k
+    return {"workload": WORKLOADS[args.config] + ", inversion-symmetric variant (real path, Sec. III.D)",
+            "ms_per_step": ms, "steps": n, "speedup_over_complex_path": ms_complex / ms,
+            "useful_tflops_real_count": st["useful_flops"] / (ms * 1e-3) / 1e12,
+            "stage_ms": {k: statistics.mean(x[k] for x in sts) for k in ("ms_zipw", "ms_apply", "ms_zhy")},
+            "gemm1_frac": 10.0 * st["flops_apply_exec"] / (ms_apply * 1e-3) / 1e12 / peak,
+            "gemm1_frac_peak_source": f"bf16_tflops_sustained ({peak_kind})",
+            "batches": st["n_batches"], "graph_replayed": all(x["graph_replayed"] for x in sts),
+            "tiles": {"nb_zhy": st["tile_nb_zhy"], "nb_zipw": st["tile_nb_zipw"],
+                      "source": "autotuner" if tuned else "library formula"},
+            "fp64_gpu_ms_per_step": ms64, "fp64_sample": f"V^x(k=0) (its {s.n_k} pairs), time x{s.n_k}",
+            "speedup_over_fp64_gpu": ms64 / ms,
+            "max_abs_dV_vs_fp64_gpu_k0": float(np.abs(V0 - V64).max()), "max_abs_imag_V": imag_max,
+            "input_generation_s": t_gen}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -526,6 +584,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-config2", dest="extra_config2", action="store_false")
+    ap.add_argument("--no-extra-inversion", dest="extra_inversion", action="store_false")
     ap.add_argument("--mesh", type=int, default=0, help="override the k mesh (N x N x N); profiling of small cases only")
     args = ap.parse_args()
     if args.impl == "reference":

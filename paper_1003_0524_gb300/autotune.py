@@ -14,7 +14,7 @@ build.  (A reduced k mesh does not do: with a few pairs the kernels run a
 fraction of a wave, and small band blocks win there that lose at full size.)
 It stores the fastest per size class in a JSON file beside this module:
 
-    python -m paper_1003_0524_gb300.autotune 1 2 3 4      # configs to tune
+    python -m paper_1003_0524_gb300.autotune 1 2 3 4 4inv  # configs to tune
 
 Context(..., tuning=True) looks up the nearest stored size class there; a
 missing class leaves the library's formula in charge.
@@ -55,12 +55,14 @@ def lookup(sysm, path: str = TUNING_FILE):
     best, dist = None, None
     for e in data.get("entries", []):
         k = e.get("key", {})
-        if k.get("n_mt") != key["n_mt"] or k.get("P") != key["P"] or bool(k.get("inv", False)) != key["inv"]:
+        if k.get("n_mt") != key["n_mt"] or k.get("P") != key["P"]:
             continue
         db, da = abs(k["nb"] - key["nb"]), abs(k["naux"] - key["naux"]) / key["naux"]
         if db > 8 or da > 0.15:
             continue
-        d = db + 50.0 * da + abs(k["no"] - key["no"])
+        # the real path (inversion symmetry) prefers its own entry, else takes
+        # the complex one of the same band windows and aux size
+        d = db + 50.0 * da + abs(k["no"] - key["no"]) + (100.0 if bool(k.get("inv", False)) != key["inv"] else 0.0)
         if dist is None or d < dist:
             best, dist = e, d
     return best
@@ -77,11 +79,14 @@ def _time(sysm, reps: int, one_k: bool, **tiles) -> dict:
     return {k: min(st[k] for st in sts) for k in ("ms_zhy", "ms_zipw", "ms_total")}
 
 
-def tune(cfg: int, reps: int = 3) -> dict:
-    """Time every candidate of both tile parameters on config cfg; return the
-    entry (not yet stored)."""
+def tune(cfg, reps: int = 3) -> dict:
+    """Time every candidate of both tile parameters on config cfg (an index, or
+    "<index>inv" for its inversion-symmetric variant); return the entry (not yet
+    stored)."""
     from . import synthetic as S
-    s = S.make_system(cfg)
+    inv = str(cfg).endswith("inv")
+    cfg = int(str(cfg)[:-3]) if inv else int(cfg)
+    s = S.make_system(cfg, inversion=inv)
     one_k = cfg >= 3
     res_zhy = {nb: _time(s, reps, one_k, tile_nb_zhy=nb)["ms_zhy"] for nb in NB_ZHY}
     best_zhy = min(res_zhy, key=res_zhy.get)
@@ -110,7 +115,8 @@ def store(entries, path: str = TUNING_FILE) -> None:
 def main(argv) -> None:
     import argparse
     ap = argparse.ArgumentParser(description="time the tile candidates and store the fastest per size class")
-    ap.add_argument("configs", nargs="*", type=int, default=[1, 2, 3, 4])
+    ap.add_argument("configs", nargs="*", default=["1", "2", "3", "4"],
+                    help="config indices, or <index>inv for the inversion-symmetric variant")
     ap.add_argument("--out", default=TUNING_FILE, help="JSON file to update (default: beside this module)")
     args = ap.parse_args(argv)
     from . import build as B

@@ -305,12 +305,15 @@ int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, bool real_v, std::vector<un
 int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_rows, const int *d_aexp, const QDesc *d_q,
                     const __nv_bfloat16 *d_ZS, const int *d_zexp, double2 *d_Y, long long RSc, long long NC, int N0,
                     int N0pad, int Dpad, int RS, const void *d_tiles, int ntiles);
-int gemm2_tiles(const PairDesc *h_pairs, int npairs, int NB, std::vector<unsigned char> &out);
+// real_form: the Z^H Y tiles of the inversion-symmetric path (only Re P', two
+// row blocks per tile; band blocks of 16, 32, 48 or 64, see gemm2_real_form)
+int gemm2_tiles(const PairDesc *h_pairs, int npairs, int NB, bool real_form, std::vector<unsigned char> &out);
 int gemm2_check_nb(int NB);
+bool gemm2_real_form(int NB);
 int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16 *d_YS, const int *d_zexp,
                     const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *d_pairs, const QDesc *d_q,
                     int NB, const long long *d_praw_off, double *d_praw, const void *d_tiles, int ntiles,
-                    int fail_wait);
+                    int fail_wait, bool real_form);
 
 // ------------------------------------------------------------ interstitial projections on the tensor cores (k_zipw_tc.cu)
 struct ZipwBuild {                          // per build: rows (k', m), segment grid, C slices

@@ -513,7 +513,7 @@ int plan_build(hfx_ctx *ctx, const std::vector<int> &kset, BuildPlan &pl) {
             if ((rc = zmt_tc_plan_batch(ctx, pl.zmt, bt.pairs, RSc, tab, bt.zmt))) return rc;
             std::vector<unsigned char> t1, t2;
             bt.n_g1t = gemm1_tiles(bt.qd.data(), nq, pl.N0pad, pl.inv, t1);
-            bt.n_g2t = gemm2_tiles(bt.pairs.data(), npairs, NB, t2);
+            bt.n_g2t = gemm2_tiles(bt.pairs.data(), npairs, NB, pl.inv && gemm2_real_form(NB), t2);
             bt.o_g1t = tab.put(t1);
             bt.o_g2t = tab.put(t2);
         } else {
@@ -714,7 +714,8 @@ int plan_run(hfx_ctx *ctx, BuildPlan &pl, int keep, int fail_wait) {
                                        ctx->stream);
             rec(ctx, bt.ev[8]);
             if ((rc = launch_gemm2_tc(ctx, ZS, YS, zexp, yexp, bt.ncols, pl.RS, pl.HS, pl.N0pad, d_pairs, d_qd, pl.NB,
-                                      d_praw_off, praw, tab + bt.o_g2t, bt.n_g2t, fail_wait)))
+                                      d_praw_off, praw, tab + bt.o_g2t, bt.n_g2t, fail_wait,
+                                      pl.inv && gemm2_real_form(pl.NB))))
                 return rc;
             fail_wait = 0;   // one kernel waits in vain
             rec(ctx, bt.ev[9]);
@@ -734,7 +735,8 @@ int plan_run(hfx_ctx *ctx, BuildPlan &pl, int keep, int fail_wait) {
         }
         launch_reduce_pairs(d_pairs, reinterpret_cast<const int *>(tab + bt.o_kstart),
                             reinterpret_cast<const int *>(tab + bt.o_klp), bt.nklist,
-                            reinterpret_cast<const int *>(tab + bt.o_klist), praw, d_praw_off, pl.NB, tc ? 1 : 0,
+                            reinterpret_cast<const int *>(tab + bt.o_klist), praw, d_praw_off, pl.NB,
+                            tc ? ((pl.inv && gemm2_real_form(pl.NB)) ? 2 : 1) : 0,
                             pl.inv ? 1 : 0, reinterpret_cast<double2 *const *>(tab + pl.o_vacc),
                             reinterpret_cast<const int *>(tab + pl.o_nb),
                             pl.nb_max, ctx->stream);

@@ -453,7 +453,8 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
 }
 
 // ------------------------------------------------------------- GEMM2
-struct G2Tile { int pair, bi, bj, pad; };
+// bi2: the real form's second row block (-1: none); the complex form leaves it 0
+struct G2Tile { int pair, bi, bj, bi2; };
 
 struct G2Params {
     const G2Tile *tiles;
@@ -480,17 +481,28 @@ __host__ __device__ constexpr int g2_kc(int NB) { return NB >= 48 ? 32 : 64; }
 template <int KC> __device__ __forceinline__ int g2_chunks(const QDesc &q, int N0pad) { return (N0pad + q.D + KC - 1) / KC; }
 
 // warp 0: TMA; warp 1: MMA; warps 2..9: epilogue (lane quarter = w%4,
-// column half = (w-2)/4 of the 2NB accumulator columns).  Four class
-// accumulators of 2NB columns each, single-buffered.
-template <int NB>
+// column half = (w-2)/4 of the W accumulator columns).  Four class
+// accumulators of W columns each, single-buffered.
+//
+// Complex form (RE = false): A rows [0,NB) Re Z, [NB,2NB) Im Z of band block
+// bi, B rows the same of Y block bj, K over each half: the W x W real
+// embedding of P' (W = 2 NB).
+// Real form (RE = true, inversion symmetry: two real bands per column, only
+// Re P' = Zr^T Yr + Zi^T Yi is wanted): K runs over both halves of a column
+// (2 x the chunks), A rows [0,NB) are Z block bi and [NB,2NB) block bi2, B rows
+// Y block bj only (W = NB): half the MMA work.  Re P'[bi][bj] goes to the
+// real-real quadrant of the complex tile layout.
+template <int NB, bool RE>
 __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const __grid_constant__ CUtensorMap tmZ,
                                                                           const __grid_constant__ CUtensorMap tmY,
                                                                           G2Params p) {
     constexpr int KC = g2_kc(NB);                  // K values per chunk
-    constexpr int G2_A_PLANE = 128 * KC * 2;       // rows [0,NB) Re, [NB,2NB) Im, rest zero
+    constexpr int G2_A_PLANE = 128 * KC * 2;       // rows [0, 2NB) loaded, rest zero
     constexpr int G2_GROUP = 256 / KC;             // chunks per exact K group (256)
-    constexpr int W = 2 * NB, CW = W / 2;   // accumulator columns; per thread
+    constexpr int W = RE ? NB : 2 * NB, CW = W / 2;   // accumulator columns; per thread
+    constexpr int WT = 2 * NB;                     // output tile width of the complex layout
     constexpr int B_PLANE = W * KC * 2;
+    static_assert(!RE || NB % 16 == 0, "the real form needs N = NB to be a multiple of 16");
     extern __shared__ __align__(1024) unsigned char g2_smem[];
     uintptr_t base = (reinterpret_cast<uintptr_t>(g2_smem) + 1023) & ~(uintptr_t)1023;
     unsigned char *stages = reinterpret_cast<unsigned char *>(base);
@@ -534,22 +546,32 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                 const PairDesc pr = p.pairs[tl.pair];
                 const QDesc q = p.qd[pr.qslot];
                 int nc = g2_chunks<KC>(q, p.N0pad);
+                const int nct = RE ? 2 * nc : nc;
                 bool stop = false;
                 for (int m = 0; m < pr.no && !stop; ++m) {
                     long long ya = pr.col0 + (long long)m * pr.nb + tl.bi * NB;
                     long long yb = pr.col0 + (long long)m * pr.nb + tl.bj * NB;
-                    for (int c = 0; c < nc; ++c) {
+                    long long ya2 = pr.col0 + (long long)m * pr.nb + (tl.bi2 >= 0 ? tl.bi2 : tl.bi) * NB;
+                    for (int c = 0; c < nct; ++c) {
                         if (!mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma)) { stop = true; break; }
                         unsigned char *st = stages + (size_t)s * SB;
-                        mbar_expect_tx(&full_bar[s], 4u * NPL * box_bytes);
+                        mbar_expect_tx(&full_bar[s], (RE ? 3u : 4u) * NPL * box_bytes);
                         for (int pl = 0; pl < NPL; ++pl) {
                             unsigned char *a = st + pl * G2_A_PLANE;
                             unsigned char *b = st + NPL * G2_A_PLANE + pl * B_PLANE;
                             int ra = (int)(pl * p.NC + ya), rb = (int)(pl * p.NC + yb);
-                            tma_load_2d(saddr(a), &tmZ, &full_bar[s], c * KC, ra);
-                            tma_load_2d(saddr(a + NB * KC * 2), &tmZ, &full_bar[s], p.HS + c * KC, ra);
-                            tma_load_2d(saddr(b), &tmY, &full_bar[s], c * KC, rb);
-                            tma_load_2d(saddr(b + NB * KC * 2), &tmY, &full_bar[s], p.HS + c * KC, rb);
+                            if constexpr (RE) {
+                                // K over [Re half | Im half] of every column
+                                const int x = c < nc ? c * KC : p.HS + (c - nc) * KC;
+                                tma_load_2d(saddr(a), &tmZ, &full_bar[s], x, ra);
+                                tma_load_2d(saddr(a + NB * KC * 2), &tmZ, &full_bar[s], x, (int)(pl * p.NC + ya2));
+                                tma_load_2d(saddr(b), &tmY, &full_bar[s], x, rb);
+                            } else {
+                                tma_load_2d(saddr(a), &tmZ, &full_bar[s], c * KC, ra);
+                                tma_load_2d(saddr(a + NB * KC * 2), &tmZ, &full_bar[s], p.HS + c * KC, ra);
+                                tma_load_2d(saddr(b), &tmY, &full_bar[s], c * KC, rb);
+                                tma_load_2d(saddr(b + NB * KC * 2), &tmY, &full_bar[s], p.HS + c * KC, rb);
+                            }
                         }
                         ++issued;
                         if (++s == NS) { s = 0; ph ^= 1; }
@@ -577,7 +599,7 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                 G2Tile tl = p.tiles[t];
                 const PairDesc pr = p.pairs[tl.pair];
                 const QDesc q = p.qd[pr.qslot];
-                int nc = g2_chunks<KC>(q, p.N0pad);
+                int nc = (RE ? 2 : 1) * g2_chunks<KC>(q, p.N0pad);
                 for (int m = 0; m < pr.no && ok; ++m) {
                     for (int g0 = 0; g0 < nc && ok; g0 += G2_GROUP) {
                         if (!mbar_wait(&tempty_bar, tph ^ 1, &abort_flag, p.err, kDevTimeoutMma)) { ok = false; break; }
@@ -623,19 +645,22 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
         int quarter = warp % 4, cg = e / 4;
         uint32_t tph = 0;
         bool ok = true;
-        int row = quarter * 32 + lane;            // accumulator row: Re (< NB) or Im part of band bi*NB + row % NB
+        // accumulator row: complex form Re (< NB) or Im part of band bi*NB + row % NB;
+        // real form band bi*NB + row (< NB) or bi2*NB + row - NB
+        int row = quarter * 32 + lane;
         // fault-injection hook: a bounded wait of about 1 ms that nothing completes
         if (p.fail_wait && !mbar_wait_ns(&never_bar, 0, &abort_flag, p.err, kDevTimeoutEpi, 1000000ULL)) ok = false;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             G2Tile tl = p.tiles[t];
             const PairDesc pr = p.pairs[tl.pair];
             const QDesc q = p.qd[pr.qslot];
-            int nc = g2_chunks<KC>(q, p.N0pad);
+            int nc = (RE ? 2 : 1) * g2_chunks<KC>(q, p.N0pad);
+            const int brow = (RE && row >= NB) ? (tl.bi2 >= 0 ? tl.bi2 : tl.bi) : tl.bi;
             uint64_t hi[CW / 2], lo[CW / 2];   // packed pairs of columns
 #pragma unroll
             for (int j = 0; j < CW / 2; ++j) { hi[j] = 0; lo[j] = 0; }
             for (int m = 0; m < pr.no && ok; ++m) {
-                long long cola = pr.col0 + (long long)m * pr.nb + tl.bi * NB + (row % NB);
+                long long cola = pr.col0 + (long long)m * pr.nb + brow * NB + (row % NB);
                 long long colb0 = pr.col0 + (long long)m * pr.nb + tl.bj * NB;
                 int ea = p.zexp[min(cola, p.NC - 1)] - 16;
                 // exponents of the NB columns of Y, fetched once per m: lane l holds
@@ -672,10 +697,11 @@ __global__ void __launch_bounds__(64 + 32 * G2_EPI_WARPS, 1) gemm2_kernel(const 
                 }
             }
             if (!ok) break;
-            if (row < W) {
+            const bool store = RE ? (row < NB || (row < 2 * NB && tl.bi2 >= 0)) : row < W;
+            if (store) {
                 int nblk = (pr.nb + NB - 1) / NB;
-                double *out = p.praw + p.praw_off[tl.pair] + ((size_t)tl.bi * nblk + tl.bj) * W * W + (size_t)row * W +
-                              cg * CW;
+                double *out = p.praw + p.praw_off[tl.pair] + ((size_t)brow * nblk + tl.bj) * WT * WT +
+                              (size_t)(RE ? row % NB : row) * WT + cg * CW;
 #pragma unroll
                 for (int j = 0; j < CW; j += 2) {
                     const float2 h = f2_unpack(hi[j / 2]), l = f2_unpack(lo[j / 2]);
@@ -882,13 +908,18 @@ int launch_gemm1_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_Ap_all, long long ap_ro
 
 // Tiles of GEMM2: every (band block i, band block j) of every pair with
 // occupied bands at k - q.
-int gemm2_tiles(const PairDesc *h_pairs, int npairs, int NB, std::vector<unsigned char> &out) {
+int gemm2_tiles(const PairDesc *h_pairs, int npairs, int NB, bool real_form, std::vector<unsigned char> &out) {
     std::vector<G2Tile> tiles;
     for (int i = 0; i < npairs; ++i) {
         int nblk = (h_pairs[i].nb + NB - 1) / NB;
         if (h_pairs[i].no == 0) continue;
-        for (int bi = 0; bi < nblk; ++bi)
-            for (int bj = 0; bj < nblk; ++bj) tiles.push_back(G2Tile{i, bi, bj, 0});
+        if (real_form) {   // two row blocks per tile
+            for (int bi = 0; bi < nblk; bi += 2)
+                for (int bj = 0; bj < nblk; ++bj) tiles.push_back(G2Tile{i, bi, bj, bi + 1 < nblk ? bi + 1 : -1});
+        } else {
+            for (int bi = 0; bi < nblk; ++bi)
+                for (int bj = 0; bj < nblk; ++bj) tiles.push_back(G2Tile{i, bi, bj, 0});
+        }
     }
     out.assign(reinterpret_cast<const unsigned char *>(tiles.data()),
                reinterpret_cast<const unsigned char *>(tiles.data()) + tiles.size() * sizeof(G2Tile));
@@ -896,10 +927,13 @@ int gemm2_tiles(const PairDesc *h_pairs, int npairs, int NB, std::vector<unsigne
 }
 
 int gemm2_check_nb(int NB) { return NB % 8 == 0 && NB >= 8 && NB <= 64; }
+bool gemm2_real_form(int NB) { return NB % 16 == 0; }
 
 int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16 *d_YS, const int *d_zexp,
                     const int *d_yexp, long long NC, int RS, int HS, int N0pad, const PairDesc *d_pairs, const QDesc *d_q,
-                    int NB, const long long *d_praw_off, double *d_praw, const void *d_tiles, int ntiles, int fail_wait) {
+                    int NB, const long long *d_praw_off, double *d_praw, const void *d_tiles, int ntiles, int fail_wait,
+                    bool real_form) {
+    if (real_form && !gemm2_real_form(NB)) return set_err(ctx, HFX_EINVAL, "gemm2: the real form needs a band tile of 16, 32, 48 or 64");
     if (!gemm2_check_nb(NB)) return set_err(ctx, HFX_EINVAL, "gemm2: band tile must be a multiple of 8 up to 64");
     if (ntiles == 0) return HFX_OK;
     if (NC > 0x7fffffffLL / 4) return set_err(ctx, HFX_EUNSUPPORTED, "batch has too many columns for 32-bit TMA coordinates");
@@ -922,7 +956,7 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
     p.N0pad = N0pad;
     p.fail_wait = fail_wait;
     p.err = ctx->d_err;
-    p.stage_bytes = NPL * (128 * KC * 2 + 2 * NB * KC * 2);
+    p.stage_bytes = NPL * (128 * KC * 2 + (real_form ? 1 : 2) * NB * KC * 2);
     p.nstages = std::min(G2_MAX_STAGES, (int)((226 * 1024) / p.stage_bytes));
     if (p.nstages < 1) return set_err(ctx, HFX_EUNSUPPORTED, "gemm2 stage does not fit in shared memory");
     size_t smem = (size_t)p.nstages * p.stage_bytes + 1024;
@@ -931,15 +965,24 @@ int launch_gemm2_tc(hfx_ctx *ctx, const __nv_bfloat16 *d_ZS, const __nv_bfloat16
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<grid, 64 + 32 * G2_EPI_WARPS, smem, ctx->stream>>>(mZ, mY, p);
     };
-    switch (NB) {
-    case 8: go(gemm2_kernel<8>); break;
-    case 16: go(gemm2_kernel<16>); break;
-    case 24: go(gemm2_kernel<24>); break;
-    case 32: go(gemm2_kernel<32>); break;
-    case 40: go(gemm2_kernel<40>); break;
-    case 48: go(gemm2_kernel<48>); break;
-    case 56: go(gemm2_kernel<56>); break;
-    default: go(gemm2_kernel<64>); break;
+    if (real_form) {
+        switch (NB) {
+        case 16: go(gemm2_kernel<16, true>); break;
+        case 32: go(gemm2_kernel<32, true>); break;
+        case 48: go(gemm2_kernel<48, true>); break;
+        default: go(gemm2_kernel<64, true>); break;
+        }
+    } else {
+        switch (NB) {
+        case 8: go(gemm2_kernel<8, false>); break;
+        case 16: go(gemm2_kernel<16, false>); break;
+        case 24: go(gemm2_kernel<24, false>); break;
+        case 32: go(gemm2_kernel<32, false>); break;
+        case 40: go(gemm2_kernel<40, false>); break;
+        case 48: go(gemm2_kernel<48, false>); break;
+        case 56: go(gemm2_kernel<56, false>); break;
+        default: go(gemm2_kernel<64, false>); break;
+        }
     }
     return cuda_check(ctx, cudaGetLastError(), "gemm2 launch");
 }

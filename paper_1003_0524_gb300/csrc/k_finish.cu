@@ -7,7 +7,8 @@ namespace hfx {
 namespace {
 
 // Vacc[k] += sum_{pairs of k in this batch, ascending q} P_pair, where the
-// tensor-core tiles (raw_format 1) hold P' = Z^H U Z and P_pair = P' + P'^H.
+// tensor-core tiles (raw_format 1) hold P' = Z^H U Z and P_pair = P' + P'^H
+// (raw_format 2: the real tiles of the inversion-symmetric path, Re P' only).
 // With real_part (inversion symmetry, two real bands packed per column, Sec.
 // III.D) only the real part is the pair's term; the imaginary part holds the
 // cross products of the two bands and is dropped.
@@ -32,6 +33,13 @@ __global__ void reduce_pairs_kernel(const PairDesc *__restrict__ pairs, const in
                 double2 v = Pc[(size_t)n * nb + n2];
                 acc.x += v.x;
                 if (!real_part) acc.y += v.y;
+            } else if (raw_format == 2) {
+                // real tiles: Re P' in the real-real quadrant of each block
+                int nblk = (nb + NB - 1) / NB;
+                int bi = n / NB, a = n % NB, bj = n2 / NB, b = n2 % NB;
+                int W = 2 * NB;
+                acc.x += P[((size_t)bi * nblk + bj) * W * W + (size_t)a * W + b] +
+                         P[((size_t)bj * nblk + bi) * W * W + (size_t)b * W + a];
             } else {
                 // real-embedded tiles of P' = Z^H U Z; the pair's term is P' + P'^H
                 int nblk = (nb + NB - 1) / NB;

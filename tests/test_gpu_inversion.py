@@ -175,3 +175,20 @@ def test_inversion_input_checks():
         assert e.value.code == hfx.HFX_EUNSUPPORTED
         st = c.build_all()
         assert st["n_pairs"] == s.n_k * s.n_k
+
+
+@pytest.mark.parametrize("nb_zhy", [16, 32, 48, 64, 40])
+def test_inversion_zhy_tile_shapes(nb_zhy):
+    """The real form of the Z^H Y tiles (two row blocks per tile, band blocks of
+    16, 32, 48 or 64; 72 bands give 5, 3, 2 and 2 blocks, so an odd count leaves
+    a tile with one row block) and the complex form it falls back to (40)."""
+    name = "inv_cfg1_nb72"
+    s = CASES[name]()
+    ref = oracle_v(name, s)
+    V, ex, st = gpu_v(s, "sliced", tile_nb_zhy=nb_zhy)
+    assert st["tile_nb_zhy"] == nb_zhy
+    err = _err(V, ref)
+    print(f"{name} NB {nb_zhy}: max|dV| = {err:.3e}")
+    assert err <= TOL_SPLIT_ABS
+    for k in V:
+        assert np.abs(V[k].imag).max() == 0.0
