@@ -773,6 +773,183 @@ int ora_kp_term(int nb, int nocc, const double *eps, const double *pd, double nk
     return 0;
 }
 
+/* ------------------------------------------------- MT product basis */
+
+/* Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix a (row-major,
+ * destroyed): eigenvalues in ev, eigenvectors in the columns of V. */
+static void jacobi_eig(int n, double *a, double *ev, double *V) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                tot += a[i * n + j] * a[i * n + j];
+                if (i != j) off += a[i * n + j] * a[i * n + j];
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = a[p * n + q];
+                if (apq == 0.0) continue;
+                double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {          /* rows p, q of a: a <- J^T a */
+                    double akp = a[k * n + p], akq = a[k * n + q];
+                    a[k * n + p] = c * akp - sn * akq;
+                    a[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = a[p * n + k], aqk = a[q * n + k];
+                    a[p * n + k] = c * apk - sn * aqk;
+                    a[q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - sn * vkq;
+                    V[k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i) ev[i] = a[i * n + i];
+}
+
+/* The on-site Coulomb integral of two radial functions of one angular channel
+ * L (Laplace expansion of 1/|r - r'| and orthonormal Y_LM):
+ *   4 pi/(2L+1) int int f(r) g(r') r<^L / r>^(L+1) r^2 r'^2 dr dr',
+ * as the tensor product of the grid's quadrature (the kernel's kink on r = r'
+ * limits the order; the pins bound the error on fine grids). */
+double ora_radial_coulomb(int n_r, const double *r, const double *w, int L, const double *f, const double *g) {
+    double acc = 0.0;
+    for (int i = 0; i < n_r; ++i)
+        for (int j = 0; j < n_r; ++j) {
+            double rl = r[i] < r[j] ? r[i] : r[j], rg = r[i] < r[j] ? r[j] : r[i];
+            acc += w[i] * w[j] * r[i] * r[i] * r[j] * r[j] * f[i] * g[j] * pow(rl, L) / pow(rg, L + 1);
+        }
+    return 4.0 * M_PI / (2 * L + 1) * acc;
+}
+
+/* Sec. III.B: the MT functions of the mixed product basis of one atom, from
+ * its LAPW radial functions u_lp (Eq. FLAPW-basis) on a radial grid r_i with
+ * quadrature weights w_i for int_0^S g(r) dr.  For every L:
+ *   - the products u_lp u_l'p' with lp <= l'p' and |l - l'| <= L <= l + l',
+ *     each normalised (int f^2 r^2 dr = 1);
+ *   - for L = 0 the spherically symmetric constant function is added first and
+ *     projected out of the products;
+ *   - the overlap matrix of the products is diagonalised and the eigenfunctions
+ *     with eigenvalue above thr are the candidates (linear-dependence removal);
+ *   - the library has a fixed count P per (a, L): the P (L = 0: P - 1 after the
+ *     constant) of largest eigenvalue are kept, each normalised, the sign fixed
+ *     so that its largest eigenvector component is positive (a reading).
+ * Outputs: M [(Lmax+1) P][n_r] on the grid, mu [(Lmax+1) P] the multipole
+ * moments int M r^(L+2) dr (Sec. III.C), R [(Lmax+1) P][n_lp][n_lp] the radial
+ * integrals int M u_lp u_l'p' r^2 dr, and C [(Lmax+1)][P][P] the on-site
+ * Coulomb integrals 4 pi/(2L+1) int int M_P(r) M_P'(r') r<^L / r>^(L+1) r^2 r'^2
+ * dr dr' (Laplace expansion of 1/|r - r'|; tensor-product quadrature).
+ * Returns 0, or -(L+1) if fewer than P functions survive for that L. */
+int ora_mpb_radial(int n_r, const double *r, const double *w, const double *u, int lmax, int Lmax, int P, double thr,
+                   double *Mout, double *mu, double *R, double *C) {
+    const int nlp = 2 * (lmax + 1);
+    int maxc = nlp * (nlp + 1) / 2 + 1;
+    double *f = (double *)malloc(sizeof(double) * (size_t)maxc * n_r);
+    double *O = (double *)malloc(sizeof(double) * maxc * maxc);
+    double *V = (double *)malloc(sizeof(double) * maxc * maxc);
+    double *ev = (double *)malloc(sizeof(double) * maxc);
+    int rc = 0;
+    for (int L = 0; L <= Lmax && !rc; ++L) {
+        /* candidate products */
+        int nc = 0;
+        for (int a = 0; a < nlp; ++a)
+            for (int b = a; b < nlp; ++b) {
+                int la = a / 2, lb = b / 2;
+                if (abs(la - lb) > L || L > la + lb) continue;
+                double nrm = 0.0;
+                for (int i = 0; i < n_r; ++i) {
+                    double v = u[(size_t)a * n_r + i] * u[(size_t)b * n_r + i];
+                    f[(size_t)nc * n_r + i] = v;
+                    nrm += w[i] * r[i] * r[i] * v * v;
+                }
+                if (nrm <= 0.0) continue;
+                for (int i = 0; i < n_r; ++i) f[(size_t)nc * n_r + i] /= sqrt(nrm);
+                ++nc;
+            }
+        /* L = 0: the constant function, normalised, projected out of the products */
+        double *cst = NULL;
+        if (L == 0) {
+            cst = (double *)malloc(sizeof(double) * n_r);
+            double nrm = 0.0;
+            for (int i = 0; i < n_r; ++i) nrm += w[i] * r[i] * r[i];
+            for (int i = 0; i < n_r; ++i) cst[i] = 1.0 / sqrt(nrm);
+            for (int c = 0; c < nc; ++c) {
+                double d = 0.0;
+                for (int i = 0; i < n_r; ++i) d += w[i] * r[i] * r[i] * cst[i] * f[(size_t)c * n_r + i];
+                for (int i = 0; i < n_r; ++i) f[(size_t)c * n_r + i] -= d * cst[i];
+            }
+        }
+        /* overlap matrix and its eigenpairs */
+        for (int a = 0; a < nc; ++a)
+            for (int b = 0; b < nc; ++b) {
+                double o = 0.0;
+                for (int i = 0; i < n_r; ++i) o += w[i] * r[i] * r[i] * f[(size_t)a * n_r + i] * f[(size_t)b * n_r + i];
+                O[a * nc + b] = o;
+            }
+        jacobi_eig(nc, O, ev, V);
+        const int want = (L == 0) ? P - 1 : P;
+        /* the want largest eigenvalues above the threshold, descending */
+        int *pick = (int *)malloc(sizeof(int) * (want > 0 ? want : 1));
+        char *used = (char *)calloc(nc > 0 ? nc : 1, 1);
+        int got = 0;
+        for (int k = 0; k < want; ++k) {
+            int best = -1;
+            for (int c = 0; c < nc; ++c)
+                if (!used[c] && ev[c] > thr && (best < 0 || ev[c] > ev[best])) best = c;
+            if (best < 0) break;
+            used[best] = 1;
+            pick[got++] = best;
+        }
+        if (got < want) rc = -(L + 1);
+        for (int P_ = 0; P_ < P && !rc; ++P_) {
+            double *M = Mout + ((size_t)L * P + P_) * n_r;
+            if (L == 0 && P_ == 0) {
+                memcpy(M, cst, sizeof(double) * n_r);
+            } else {
+                int e = pick[L == 0 ? P_ - 1 : P_];
+                int big = 0;
+                for (int c = 1; c < nc; ++c)
+                    if (fabs(V[c * nc + e]) > fabs(V[big * nc + e])) big = c;
+                double sg = V[big * nc + e] >= 0 ? 1.0 : -1.0, sc = sg / sqrt(ev[e]);
+                for (int i = 0; i < n_r; ++i) {
+                    double acc = 0.0;
+                    for (int c = 0; c < nc; ++c) acc += V[c * nc + e] * f[(size_t)c * n_r + i];
+                    M[i] = sc * acc;
+                }
+            }
+        }
+        free(pick);
+        free(used);
+        free(cst);
+        if (rc) break;
+        /* multipole moments, radial integrals, on-site Coulomb */
+        for (int P_ = 0; P_ < P; ++P_) {
+            const double *M = Mout + ((size_t)L * P + P_) * n_r;
+            double m = 0.0;
+            for (int i = 0; i < n_r; ++i) m += w[i] * M[i] * pow(r[i], L + 2);
+            mu[L * P + P_] = m;
+            for (int a = 0; a < nlp; ++a)
+                for (int b = 0; b < nlp; ++b) {
+                    double acc = 0.0;
+                    for (int i = 0; i < n_r; ++i) acc += w[i] * r[i] * r[i] * M[i] * u[(size_t)a * n_r + i] * u[(size_t)b * n_r + i];
+                    R[(((size_t)L * P + P_) * nlp + a) * nlp + b] = acc;
+                }
+            for (int Q = 0; Q < P; ++Q)
+                C[((size_t)L * P + P_) * P + Q] = ora_radial_coulomb(n_r, r, w, L, M, Mout + ((size_t)L * P + Q) * n_r);
+        }
+    }
+    free(f); free(O); free(V); free(ev);
+    return rc;
+}
+
 /* ------------------------------------------------- inversion symmetry */
 
 /* Sec. III.D: the partner of every atom under r -> -r, i.e. the atom a' whose

@@ -107,6 +107,10 @@ def lib():
             L.ora_inv_partner.argtypes = [vp, vp]
             L.ora_sym_matrix.restype = ip
             L.ora_sym_matrix.argtypes = [vp, ip, vp]
+            L.ora_radial_coulomb.restype = dp
+            L.ora_radial_coulomb.argtypes = [ip, vp, vp, ip, vp, vp]
+            L.ora_mpb_radial.restype = ip
+            L.ora_mpb_radial.argtypes = [ip, vp, vp, vp, ip, ip, ip, dp, vp, vp, vp, vp]
             L.ora_num_threads.restype = ip
             L.ora_num_threads.argtypes = []
             _lib = L
@@ -303,6 +307,37 @@ def kp_term(eps, p, nocc: int, nk_omega: float, deg_tol: float = 1e-6) -> np.nda
     out = np.zeros((nb, nb), np.complex128)
     lib().ora_kp_term(nb, int(nocc), _ptr(eps), _ptr(p), float(nk_omega), float(deg_tol), _ptr(out))
     return out
+
+
+def radial_coulomb(r, w, L: int, f, g) -> float:
+    """4 pi/(2L+1) int int f(r) g(r') r<^L/r>^(L+1) r^2 r'^2 dr dr' on the grid."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    return lib().ora_radial_coulomb(r.size, _ptr(r), _ptr(w), int(L), _ptr(f), _ptr(g))
+
+
+def mpb_radial(r, w, u, lmax: int, Lmax: int, P: int, thr: float = 1e-4) -> dict:
+    """Sec. III.B: the MT product basis of one atom from its radial functions
+    u [2(lmax+1)][n_r] on the grid r with weights w: M [(Lmax+1) P][n_r], the
+    multipole moments mu, the radial integrals R and the on-site Coulomb blocks
+    C [(Lmax+1)][P][P].  Raises if fewer than P functions survive for some L."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    n = r.size
+    nlp = 2 * (lmax + 1)
+    assert u.shape == (nlp, n)
+    M = np.zeros(((Lmax + 1) * P, n))
+    mu = np.zeros((Lmax + 1) * P)
+    R = np.zeros(((Lmax + 1) * P, nlp, nlp))
+    C = np.zeros((Lmax + 1, P, P))
+    rc = lib().ora_mpb_radial(n, _ptr(r), _ptr(w), _ptr(u), lmax, Lmax, P, float(thr), _ptr(M), _ptr(mu), _ptr(R),
+                              _ptr(C))
+    if rc != 0:
+        raise ValueError(f"fewer than P product functions above the threshold for L = {-rc - 1}")
+    return {"M": M, "mu": mu, "R": R, "C": C}
 
 
 def num_threads() -> int:

@@ -610,3 +610,25 @@ def _make_system_inv(cfg, *, seed=None, mesh=None, nb=None, no=None, aux=None, s
                   Lmax=Lmax, P=P, mesh=mesh_t, gmax=float(spec["gmax"]), n_bands=n_bands,
                   n_occ=n_occ, Gk=Gk, c=c, A=A, R=R, mu=mu, Gaux=Gaux, v=v, sparse=sparse,
                   scale=s, seed=seed, inversion=True)
+
+
+def radial_grid(rmt: float, n_r: int):
+    """Gauss-Legendre nodes and weights on (0, rmt] for int_0^rmt g(r) dr."""
+    x, w = np.polynomial.legendre.leggauss(int(n_r))
+    return 0.5 * rmt * (x + 1.0), 0.5 * rmt * w
+
+
+def radial_functions(lmax: int, rmt: float, n_r: int, seed: int):
+    """Seeded stand-ins for the LAPW radial functions u_lp(r) of one atom
+    (p = 0: the solution, p = 1: its energy derivative, Eq. FLAPW-basis): smooth
+    functions r^l (a_0 + a_1 r + ... + a_4 r^4) with random coefficients on the
+    Gauss-Legendre grid of radial_grid.  Returns (r, w, u[2(lmax+1)][n_r])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r, w = radial_grid(rmt, n_r)
+    u = np.zeros((2 * (lmax + 1), r.size))
+    for l in range(lmax + 1):
+        for p in range(2):
+            a = rng.standard_normal(5) / (1.0 + np.arange(5)) ** 2
+            x = r / rmt
+            u[2 * l + p] = x ** l * (a[0] + a[1] * x + a[2] * x ** 2 + a[3] * x ** 3 + a[4] * x ** 4)
+    return r, w, u
