@@ -154,10 +154,17 @@ typedef struct {
 /* Layout of the Coulomb matrix passed to hfx_set_coulomb. */
 enum {
     HFX_LAYOUT_DENSE = 0,       /* v(q) in the MPB order above (Eq. coulomb matrix) */
-    HFX_LAYOUT_TRANSFORMED = 1  /* v_t = T v T^T in the same index positions, T the
+    HFX_LAYOUT_TRANSFORMED = 1, /* v_t = T v T^T in the same index positions, T the
                                    multipole transform of hfx_get_transform (Sec. III.C):
                                    MT function P' = 0 of every (a, L, M) is the one with
                                    a multipole, P' >= 1 are multipole-free */
+    HFX_LAYOUT_TRANSFORMED_ONSITE = 2 /* as TRANSFORMED, but the rows and columns of the
+                                   multipole-free functions (P' >= 1) are ignored: the
+                                   library fills them at the build with the on-site
+                                   blocks T C T^T of hfx_set_radial_functions (every
+                                   atom needs it) and zero elsewhere, which is exact:
+                                   a multipole-free function makes no potential outside
+                                   its sphere (Sec. III.C, Fig. 1) */
 };
 
 /* Per-build statistics (filled if the pointer is non-NULL). */
@@ -206,6 +213,32 @@ HFX_API int hfx_create(const hfx_system *sys, const hfx_options *opt, hfx_ctx **
  *   mu [(Lmax+1)*P] real: multipole moments mu_{aLP} = int_0^S M_{aLP} r^{L+2} dr,
  *      which define the unitary transform of Sec. III.C. */
 HFX_API int hfx_set_radial(hfx_ctx *ctx, int atom, const double *R, const double *mu);
+
+/* The MT product functions of one atom built from its LAPW radial functions
+ * (Sec. III.B), on the GPU in FP64, replacing the inputs of hfx_set_radial:
+ *   n_r, r, w  radial grid: r [n_r] increasing in (0, R_MT], w [n_r] quadrature
+ *              weights of int_0^R_MT g(r) dr (2 <= n_r <= 8192)
+ *   u          [2(lmax+1)][n_r] u_lp(r) on the grid, lp = 2l + p (Eq. FLAPW-basis)
+ *   threshold  eigenvalue threshold of the linear-dependence removal (the paper
+ *              uses 1e-4), > 0
+ * For every L the products u_lp u_l'p' (lp <= l'p', |l - l'| <= L <= l + l') are
+ * normalised, for L = 0 the constant function is added and projected out of them,
+ * the overlap matrix of the products is diagonalised, and the P eigenfunctions of
+ * largest eigenvalue above the threshold (P - 1 for L = 0) become M_aLP,
+ * normalised, each with its largest eigenvector component positive.  From them
+ * the library computes the multipole moments mu_aLP = int M r^(L+2) dr
+ * (Sec. III.C), the radial integrals R = int M u_lp u_l'p' r^2 dr, and the on-site
+ * Coulomb blocks C_aL[P][P'] = 4 pi/(2L+1) int int M_P M_P' r<^L/r>^(L+1) r^2 r'^2
+ * (Eq. coulomb matrix restricted to one sphere; used by
+ * HFX_LAYOUT_TRANSFORMED_ONSITE).  Errors: HFX_EINVAL (grid, pointer, or fewer
+ * than P functions above the threshold for some L), HFX_ENONFINITE. */
+HFX_API int hfx_set_radial_functions(hfx_ctx *ctx, int atom, int n_r, const double *r, const double *w,
+                                     const double *u, double threshold);
+
+/* The basis built by hfx_set_radial_functions for one atom; any pointer may be NULL:
+ *   M [(Lmax+1) P][n_r], mu [(Lmax+1) P], R [(Lmax+1) P][2(lmax+1)][2(lmax+1)],
+ *   C [Lmax+1][P][P].  HFX_EMISSING if the atom has none. */
+HFX_API int hfx_get_radial_basis(hfx_ctx *ctx, int atom, double *M, double *mu, double *R, double *C);
 
 /* Wave functions of one k point (Eq. FLAPW-basis), uploaded to the device.
  *   n_bands   band window n_max of Sec. III (V^x is n_bands x n_bands), >= 1

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhfx.so")
 SOURCES = ["hfx_api.cu", "hfx_plan.cu", "hfx_lapw.cu", "k_setup.cu", "k_stage1.cu", "k_contract64.cu", "k_contract_tc.cu", "k_zipw_tc.cu",
-           "k_cgemm_tc.cu", "k_finish.cu"]
+           "k_cgemm_tc.cu", "k_finish.cu", "k_radial.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -393,7 +393,8 @@ int hfx_set_coulomb(hfx_ctx *ctx, int iq, int n_ipw, const int *G_aux, const dou
     if (!ctx) return HFX_EINVAL;
     if (iq < 0 || iq >= ctx->nk) return set_err(ctx, HFX_EINVAL, "set_coulomb: q index out of range");
     if (n_ipw < 0 || n_ipw > (1 << 16) || (n_ipw > 0 && !G_aux) || !v) return set_err(ctx, HFX_EINVAL, "set_coulomb: bad size or pointer");
-    if (layout != HFX_LAYOUT_DENSE && layout != HFX_LAYOUT_TRANSFORMED) return set_err(ctx, HFX_EINVAL, "set_coulomb: unknown layout");
+    if (layout != HFX_LAYOUT_DENSE && layout != HFX_LAYOUT_TRANSFORMED && layout != HFX_LAYOUT_TRANSFORMED_ONSITE)
+        return set_err(ctx, HFX_EINVAL, "set_coulomb: unknown layout");
     for (int i = 0; i < 3 * n_ipw; ++i)
         if (G_aux[i] < -512 || G_aux[i] > 512) return set_err(ctx, HFX_EINVAL, "set_coulomb: |G| component above 512");
     const int naux = ctx->nmt + n_ipw;
@@ -533,7 +534,7 @@ void hfx_destroy(hfx_ctx *ctx) {
     dfree(ctx->s_lapw.p);
     dfree(ctx->s_lapw_tab.p);
     dfree(ctx->d_R); dfree(ctx->d_mu); dfree(ctx->d_T); dfree(ctx->d_Tid); dfree(ctx->d_gaunt); dfree(ctx->d_posf);
-    dfree(ctx->d_err); dfree(ctx->d_Ex);
+    dfree(ctx->d_err); dfree(ctx->d_Ex); dfree(ctx->d_radC);
     Scratch *all[] = {&ctx->s_theta, &ctx->s_thpsi, &ctx->s_B,    &ctx->s_zc,   &ctx->s_zs,   &ctx->s_ys,
                       &ctx->s_y64,   &ctx->s_praw,  &ctx->s_vacc, &ctx->s_pairs, &ctx->s_qd,  &ctx->s_misc,
                       &ctx->s_ap,    &ctx->s_aexp,  &ctx->s_xexp, &ctx->s_zipw, &ctx->s_cgT, &ctx->s_cgZ};
@@ -565,6 +566,16 @@ int prepare_coulomb(hfx_ctx *ctx) {
     const hfx_system &s = ctx->sys;
     int P = ctx->P, rc;
     if ((rc = prepare_T(ctx))) return rc;
+    bool onsite = false;
+    for (auto &q : ctx->qp) onsite |= q.layout == HFX_LAYOUT_TRANSFORMED_ONSITE;
+    if (onsite) {
+        for (int a = 0; a < s.n_atoms; ++a)
+            if (ctx->rad_set.size() != (size_t)s.n_atoms || !ctx->rad_set[a])
+                return set_err(ctx, HFX_EMISSING, "TRANSFORMED_ONSITE: set_radial_functions missing for atom " + std::to_string(a));
+        if (!ctx->d_radC && (rc = dalloc(ctx, &ctx->d_radC, ctx->rad_C.size()))) return rc;
+        if ((rc = h2d(ctx, ctx->d_radC, ctx->rad_C.data(), ctx->rad_C.size()))) return rc;
+        ctx->rad_C_dirty = false;
+    }
     bool want_sparse = ctx->opt.sparse != HFX_SPARSE_OFF && P > 1;
     unsigned long long *d_mx = nullptr;
     if ((rc = dalloc(ctx, &d_mx, 2 * (size_t)ctx->nk))) return rc;
@@ -591,8 +602,11 @@ int prepare_coulomb(hfx_ctx *ctx) {
                 q.vb_cap = nvb;
             }
             cudaMemsetAsync(q.d_VB, 0, sizeof(double2) * nvb, ctx->stream);
+            // the multipole-free rows and columns from the on-site blocks of the radial basis
+            if (q.layout == HFX_LAYOUT_TRANSFORMED_ONSITE && pass == 0)
+                launch_onsite_fill(q.d_v, naux, ctx->d_radC, ctx->d_T, s.n_atoms, s.Lmax, P, ctx->stream);
             // a v(q) given already transformed is only permuted (identity blocks)
-            const double *T = q.layout == HFX_LAYOUT_TRANSFORMED ? ctx->d_Tid : ctx->d_T;
+            const double *T = q.layout != HFX_LAYOUT_DENSE ? ctx->d_Tid : ctx->d_T;
             launch_transform_v(q.d_v, q.d_VD, q.d_VB, T, s.n_atoms, s.Lmax, P, q.nipw, sparse ? 1 : 0, d_mx + 2 * iq,
                                d_mx + 2 * iq + 1, ctx->stream);
         }

@@ -156,6 +156,13 @@ struct hfx_ctx {
     std::vector<char> rset;
     std::vector<int> partner;    // inversion partner of every atom (inversion mode)
     std::vector<double> hR, hmu; // host copies of the radial inputs (partner checks)
+    // the MT product basis built from radial functions (hfx_set_radial_functions)
+    std::vector<std::vector<double>> rad_M;   // per atom [(Lmax+1) P][n_r]
+    std::vector<int> rad_nr;
+    std::vector<double> rad_C;                // [n_atoms][Lmax+1][P][P] on-site Coulomb blocks
+    std::vector<char> rad_set;
+    bool rad_C_dirty = false;
+    double *d_radC = nullptr;                 // device copy of rad_C
     double *d_R = nullptr;       // [n_atoms][(Lmax+1)P][nlp][nlp]
     double *d_mu = nullptr;      // [n_atoms][(Lmax+1)P]
     double *d_T = nullptr;       // [n_atoms][Lmax+1][P][P] multipole transforms
@@ -262,6 +269,10 @@ int launch_zipw(const PairDesc *d_pairs, const int *d_kpairs, int nk, int nb_max
 template <typename R>
 void launch_override(const double2 *d_user, const PairDesc &pr, int naux, const double *d_T, int n_atoms, int Lmax,
                      int P, int N0, int sparse, typename C2<R>::T *d_Z, long long RSc, int nmt, cudaStream_t st);
+// Sec. III.C: the mu = 0 rows and columns of v_t (transformed index positions)
+// from the on-site Coulomb blocks C [n_atoms][Lmax+1][P][P] of the radial basis.
+void launch_onsite_fill(double2 *d_v, int naux, const double *d_C, const double *d_T, int n_atoms, int Lmax, int P,
+                        cudaStream_t st);
 // Sec. III.D: Z' = S^H Z on the MT rows of every column of a batch, with the
 // row operations of sym_row_ops (pairs of rows and lone rows).
 struct SymOp { int r1, r2, kind, pad; };   // kind 0: pair s = +1, 1: pair s = -1, 2: lone row times -i

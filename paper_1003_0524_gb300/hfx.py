@@ -28,7 +28,7 @@ HFX_EUNSUPPORTED = -9
 HFX_PREC_FP64 = 0
 HFX_PREC_SLICED = 1
 HFX_SPARSE_AUTO, HFX_SPARSE_ON, HFX_SPARSE_OFF = 0, 1, 2
-HFX_LAYOUT_DENSE, HFX_LAYOUT_TRANSFORMED = 0, 1
+HFX_LAYOUT_DENSE, HFX_LAYOUT_TRANSFORMED, HFX_LAYOUT_TRANSFORMED_ONSITE = 0, 1, 2
 
 EXPORTS = (
     "hfx_default_options", "hfx_create", "hfx_set_radial", "hfx_set_kpoint", "hfx_set_coulomb",
@@ -36,6 +36,7 @@ EXPORTS = (
     "hfx_exchange_device_ptr", "hfx_get_energy", "hfx_get_q0_bracket", "hfx_destroy", "hfx_strerror",
     "hfx_last_error", "hfx_version", "hfx_q0_bracket_noalloc", "hfx_get_transform",
     "hfx_set_overlap", "hfx_lapw_transform_all", "hfx_get_lapw_exchange", "hfx_set_momentum",
+    "hfx_set_radial_functions", "hfx_get_radial_basis",
 )
 
 
@@ -168,6 +169,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.hfx_last_error.argtypes = [vp]
     L.hfx_version.restype = ctypes.c_char_p
     L.hfx_version.argtypes = []
+    L.hfx_set_radial_functions.restype = ip
+    L.hfx_set_radial_functions.argtypes = [vp, ip, ip, vp, vp, vp, dp]
+    L.hfx_get_radial_basis.restype = ip
+    L.hfx_get_radial_basis.argtypes = [vp, ip, vp, vp, vp, vp]
     L.hfx_q0_bracket_noalloc.restype = ip
     L.hfx_q0_bracket_noalloc.argtypes = [vp, vp, dp, vp, vp]
     _lib = L
@@ -217,6 +222,26 @@ def hfx_set_radial(ctx, atom: int, R, mu):
     R = _c(R, np.float64)
     mu = _c(mu, np.float64)
     _check(ctx, load().hfx_set_radial(ctx, int(atom), R.ctypes.data, mu.ctypes.data))
+
+
+def hfx_set_radial_functions(ctx, atom: int, r, w, u, threshold: float = 1e-4):
+    """u: (2(lmax+1), n_r) radial functions on the grid r with weights w."""
+    r = _c(r, np.float64)
+    w = _c(w, np.float64)
+    u = _c(u, np.float64)
+    _check(ctx, load().hfx_set_radial_functions(ctx, int(atom), int(r.size), r.ctypes.data, w.ctypes.data,
+                                                u.ctypes.data, float(threshold)))
+
+
+def hfx_get_radial_basis(ctx, atom: int, n_r: int, lmax: int, Lmax: int, P: int) -> dict:
+    nlp = 2 * (lmax + 1)
+    M = np.zeros(((Lmax + 1) * P, n_r))
+    mu = np.zeros((Lmax + 1) * P)
+    R = np.zeros(((Lmax + 1) * P, nlp, nlp))
+    C = np.zeros((Lmax + 1, P, P))
+    _check(ctx, load().hfx_get_radial_basis(ctx, int(atom), M.ctypes.data, mu.ctypes.data, R.ctypes.data,
+                                            C.ctypes.data))
+    return {"M": M, "mu": mu, "R": R, "C": C}
 
 
 def hfx_set_kpoint(ctx, ik: int, n_bands: int, n_occ: int, G, c, A):

@@ -632,3 +632,22 @@ def radial_functions(lmax: int, rmt: float, n_r: int, seed: int):
             x = r / rmt
             u[2 * l + p] = x ** l * (a[0] + a[1] * x + a[2] * x ** 2 + a[3] * x ** 3 + a[4] * x ** 4)
     return r, w, u
+
+
+def coulomb_dense_block(sysm, iq: int, seed: Optional[int] = None) -> np.ndarray:
+    """A seeded Hermitian positive-definite stand-in for the dense block of the
+    transformed Coulomb matrix of Fig. 1 (the functions with a multipole, one per
+    (a, L, M) in the MT order, then the interstitial plane waves of q):
+    U diag(s 4 pi / (g^2 + 0.05)) U^H with g = |q + G| for the plane waves and
+    U(0, max|q+G|) for the MT functions, U Haar-unitary."""
+    rng = np.random.Generator(np.random.PCG64((sysm.seed if seed is None else seed) * 1000 + 900 + iq))
+    B = reciprocal(sysm.lattice)
+    qf = kpoint_frac(sysm.mesh, iq)
+    gn = np.linalg.norm((qf[None, :] + sysm.Gaux[iq]) @ B, axis=1)
+    nch = sysm.n_atoms * (sysm.Lmax + 1) ** 2
+    kappa = rng.uniform(0.0, float(gn.max()) if gn.size else 1.0, size=nch)
+    g = np.concatenate([kappa, gn])
+    d = sysm.scale * 4.0 * math.pi / (g * g + 0.05)
+    U = _haar_unitary(rng, g.size)
+    v = (U * d[None, :]) @ U.conj().T
+    return 0.5 * (v + v.conj().T)
