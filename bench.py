@@ -214,7 +214,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_1003_0524_gb300 import synthetic as S
-    s = S.make_system(args.config)
+    s = S.make_system(args.config, inversion=args.inversion)
     smp = reference_sample(args.config, s)
     full = oracle_step_flops(s)
     for _ in range(args.warmup):
@@ -238,8 +238,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _workload(args):
+    w = WORKLOADS[args.config]
+    return w + ", inversion-symmetric variant (real path, Sec. III.D)" if getattr(args, "inversion", False) else w
+
+
 def _config(args, ws):
-    return {"workload": WORKLOADS[args.config], "config_index": args.config, "precision": args.precision,
+    return {"workload": _workload(args), "config_index": args.config, "precision": args.precision,
+            "inversion": bool(getattr(args, "inversion", False)),
             "l2": "inputs larger than L2 (per-step working set of tens to hundreds of GB)",
             "parallelism": "replicas" if ws > 1 else "1 GPU"}
 
@@ -266,7 +272,7 @@ def run_ours(args):
     B.build()
     hfx.load()
     t_gen = time.perf_counter()
-    s = S.make_system(args.config, **({"mesh": (args.mesh,) * 3} if args.mesh else {}))
+    s = S.make_system(args.config, inversion=args.inversion, **({"mesh": (args.mesh,) * 3} if args.mesh else {}))
     t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.current_stream().cuda_stream
     ctx = hfx.Context(s, precision=args.precision, stream=stream, device=local, tuning=True)
@@ -308,6 +314,8 @@ def run_ours(args):
     # pair count m n per (k, q), for the FFT term of the algorithmic count
     mn = sum(int(s.n_occ[_fold(s, ik, iq)]) * int(s.n_bands[ik]) for ik in range(s.n_k) for iq in range(s.n_k))
     fl_fft = fft_flops(mn, FFT_N.get(args.config, 24))
+    if args.inversion:
+        fl_fft *= 0.5   # real products: real-to-complex transforms, half the work
     useful_8d = st["useful_flops"] - st["flops_zipw"] + fl_fft
     V_ours = {ik: ctx.exchange(ik) for ik in range(s.n_k)}
     ex_ours = ctx.energy()
@@ -391,7 +399,7 @@ def run_ours(args):
         extra["lapw_transform"] = lapw
     if args.extra_config2 and args.config != 2 and not args.mesh:
         extra["config2"] = measure_config2(args, stream, local)
-    if args.extra_inversion and args.precision == "sliced" and not args.mesh:
+    if args.extra_inversion and args.precision == "sliced" and not args.mesh and not args.inversion:
         extra["inversion"] = measure_inversion(args, stream, local, ms)
 
     line = None
@@ -405,9 +413,10 @@ def run_ours(args):
         }
         dom = max(kernels, key=lambda k: kernels[k][0])
         names = {"apply": "gemm1_kernel", "zhy": "gemm2_kernel", "zipw": "zipw_tc_kernel"}
-        files = {"apply": ("k_contract_tc.cu", f"gemm1_kernel_config{args.config}.md"),
-                 "zhy": ("k_contract_tc.cu", f"gemm2_kernel_config{args.config}.md"),
-                 "zipw": ("k_zipw_tc.cu", f"zipw_tc_kernel_config{args.config}.md")}
+        sfx = f"config{args.config}" + ("_inversion" if args.inversion else "")
+        files = {"apply": ("k_contract_tc.cu", f"gemm1_kernel_{sfx}.md"),
+                 "zhy": ("k_contract_tc.cu", f"gemm2_kernel_{sfx}.md"),
+                 "zipw": ("k_zipw_tc.cu", f"zipw_tc_kernel_{sfx}.md")}
         nlaunch_dom = st["n_batches"]
         if args.precision == "sliced":
             peak = peaks.get("bf16_tflops_sustained", 1700.0)
@@ -585,6 +594,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-config2", dest="extra_config2", action="store_false")
     ap.add_argument("--no-extra-inversion", dest="extra_inversion", action="store_false")
+    ap.add_argument("--inversion", action="store_true",
+                    help="time the inversion-symmetric variant of the workload (real path) as the main line")
     ap.add_argument("--mesh", type=int, default=0, help="override the k mesh (N x N x N); profiling of small cases only")
     args = ap.parse_args()
     if args.impl == "reference":

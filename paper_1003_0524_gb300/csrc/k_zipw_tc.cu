@@ -252,8 +252,12 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
         uint32_t ph = 0;
         int issued = 0;
         const char *tq = reinterpret_cast<const char *>(p.Tq);
+        // the tables of the next chunk (and the next tile's descriptor) are loaded
+        // one step ahead, so that their latency overlaps the wait for a free stage
+        ZTile tl_next = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x] : ZTile{};
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
-            const ZTile tl = p.tiles[t];
+            const ZTile tl = tl_next;
+            if (t + (int)gridDim.x < p.ntiles) tl_next = p.tiles[t + gridDim.x];
             const int4 W = p.wxyz[tl.w];
             const int gt = tl.mrow / ZT_BM, nch = p.nchunk[gt];
             const int slot = p.kslot[tl.k];
@@ -265,8 +269,15 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             const int bxy = (W.x - p.tlo0) * p.td1 + (W.y - p.tlo1);
             const int bz = W.z - p.tlo2;
             bool stop = false;
+            int ri_next = nch > 0 ? runs[0] : 0;
+            int2 sg_next = (nch > 0 && lane < KSEG) ? so[lane] : make_int2(0, 0);
             for (int c = 0; c < nch; ++c) {
-                const int ri = runs[c], live = ri >> 8, starts = ri & 0xff;
+                const int ri = ri_next, live = ri >> 8, starts = ri & 0xff;
+                const int2 sg = sg_next;
+                if (c + 1 < nch) {
+                    ri_next = runs[c + 1];
+                    if (lane < KSEG) sg_next = so[(c + 1) * KSEG + lane];
+                }
                 int ok = 1;
                 if (lane == 0) {
                     ok = mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kDevTimeoutTma) ? 1 : 0;
@@ -280,7 +291,6 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                 if (lane < live && ((starts >> lane) & 1)) {
                     const int rest = starts >> (lane + 1);
                     const int len = rest ? __ffs(rest) : live - lane;   // segments up to the next run
-                    const int2 sg = so[c * KSEG + lane];
                     const int Zs = bz + sg.y;
                     const int cp = Zs & (ZT_NCOPY - 1);
                     const long long cell =
