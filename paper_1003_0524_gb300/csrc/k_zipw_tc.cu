@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
     __shared__ uint64_t full_bar[ZT_STAGES], empty_bar[ZT_STAGES], tfull_bar, tempty_bar, mma_done;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
+    __shared__ int s_eT[ZT_EPI][32];      // per epilogue warp: the band exponents of its bands
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     // B segments of every stage start as zeros: padding segments are never loaded
     for (int s = 0; s < ZT_STAGES; ++s) {
@@ -378,10 +379,16 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             // everything the output of this row needs, fetched now so that the
             // dependent loads overlap the first K group instead of following it:
             // the output row g, the first column and the live bands, the scales
-            int g = -1, nlive = 0;
+            int g = -1, nlive = 0, ea = 0;
             long long col = 0;
-            int ex[NH];
             {
+                // the band exponents of this warp's bands (the same for every row of
+                // the tile: one k) go to shared memory, one per lane; the row's own
+                // exponent stays in a register
+                const int n0 = tl.nblk * NB + cs * NH;
+                __syncwarp();
+                s_eT[e][lane] = (lane < NH && n0 + lane < p.nbmax) ? p.eT[(size_t)tl.k * p.nbmax + n0 + lane] : 0;
+                __syncwarp();
                 const int r = tl.mrow + quarter * 32 + lane;
                 if (r < p.R) {
                     const int kp = p.rowk[r], m = p.rowm[r];
@@ -391,13 +398,9 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                         const int Gx = W.x + pi.g0x - p.ax0, Gy = W.y + pi.g0y - p.ay0, Gz = W.z + pi.g0z - p.az0;
                         if (Gx >= 0 && Gx < p.ad0 && Gy >= 0 && Gy < p.ad1 && Gz >= 0 && Gz < p.ad2)
                             g = p.gtab[(((size_t)pr.qslot * p.ad0 + Gx) * p.ad1 + Gy) * p.ad2 + Gz];
-                        const int n0 = tl.nblk * NB + cs * NH;
                         nlive = min(NH, pr.nb - n0);
                         col = pr.col0 + (long long)m * pr.nb + n0;
-                        const int ea = p.aexp[r] - 16;
-                        const int *eTk = p.eT + (size_t)tl.k * p.nbmax;
-#pragma unroll
-                        for (int jj = 0; jj < NH; ++jj) ex[jj] = jj < nlive ? ea + eTk[n0 + jj] : 0;
+                        ea = p.aexp[r] - 16;
                     }
                 }
             }
@@ -447,8 +450,9 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
                         // Omega^{-1/2} is in the C slices; the conversion runs on the integer
                         // units (measured faster here than the one-FP64-add form)
                         double2 v;
-                        v.x = f32pair_to_f64_int(odd ? h1.y : h1.x, odd ? l1.y : l1.x, ex[jj]);
-                        v.y = f32pair_to_f64_int(odd ? h2.y : h2.x, odd ? l2.y : l2.x, ex[jj]);
+                        const int ex = ea + s_eT[e][jj];
+                        v.x = f32pair_to_f64_int(odd ? h1.y : h1.x, odd ? l1.y : l1.x, ex);
+                        v.y = f32pair_to_f64_int(odd ? h2.y : h2.x, odd ? l2.y : l2.x, ex);
                         __stcs(out + jj * p.RSc, v);   // streaming: keep the operands in L2
                     }
                 }
