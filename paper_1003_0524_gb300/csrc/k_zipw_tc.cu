@@ -38,6 +38,13 @@ constexpr int ZT_BM = 128;
 __host__ __device__ constexpr int zt_kseg(int NB) { return NB > 40 ? 4 : 8; }
 __host__ __device__ constexpr int zt_stages(int KSEG) { return KSEG == 8 ? 2 : 3; }
 constexpr int ZT_EPI = 8;
+constexpr int ZT_THREADS = 128 + 32 * ZT_EPI;   // warpgroup 0: producer, MMA (2 idle); 1, 2: epilogue
+// register split (setmaxnreg) for the band blocks whose epilogue needs more than
+// the 168 registers a thread gets at launch: the control warpgroup gives its
+// registers to the two epilogue warpgroups (4*32*64 + 8*32*216 <= 12*32*168)
+__host__ __device__ constexpr bool zt_split(int NB) { return NB >= 56; }
+constexpr int ZT_REG_LAUNCH = 168, ZT_REG_CTRL = 64, ZT_REG_EPI = 216;
+static_assert(4 * ZT_REG_CTRL + 8 * ZT_REG_EPI <= 12 * ZT_REG_LAUNCH, "register split exceeds the launch allocation");
 constexpr int ZT_SEGZ = 4;                 // z values per segment (8 K values: real and imaginary parts)
 constexpr int ZT_NCOPY = ZT_SEGZ;          // z-shifted copies of the sliced T box
 
@@ -199,9 +206,9 @@ struct ZParams {
     int *err;
 };
 
-// warp 0: TMA; warp 1: MMA; warps 2..9: epilogue (lane quarter, real/imaginary output)
+// warp 0: TMA; warp 1: MMA; warps 4..11: epilogue (lane quarter, real/imaginary output)
 template <int NB>
-__global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(ZT_THREADS, 1) zipw_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                       ZParams p) {
     constexpr int N = 2 * NB;                            // real and imaginary output columns
     constexpr int KSEG = zt_kseg(NB);                    // segments per K chunk
@@ -243,6 +250,8 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
     tc_fence_after();
     uint32_t tmem = tmem_slot;
 
+    if (warp < 4) {
+    if constexpr (zt_split(NB)) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(ZT_REG_CTRL));
     if (warp == 0) {
         // producer warp: lane 0 waits for the stage and arms its barrier, then
         // lanes 0..3 load the four A planes and the lanes of the segments that
@@ -364,11 +373,13 @@ __global__ void __launch_bounds__(64 + 32 * ZT_EPI, 1) zipw_tc_kernel(const __gr
             }
             umma_drain(&mma_done);
         }
+    }
     } else {
+        if constexpr (zt_split(NB)) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(ZT_REG_EPI));
         // epilogue warp (quarter, cs): TMEM lanes of its quarter, bands
         // [cs NB/2, (cs + 1) NB/2) of the block, real and imaginary columns of each
         constexpr int NH = NB / 2;                     // a multiple of 4
-        const int e = warp - 2;
+        const int e = warp - 4;
         const int quarter = warp % 4, cs = e / 4;
         uint32_t eph = 0;
         bool ok = true;
@@ -801,14 +812,20 @@ int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, co
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int rc_launch = HFX_OK;
     auto go = [&](auto kern, int nb) {
         cudaFuncAttributes fa;
         cudaFuncGetAttributes(&fa, kern);
+        if (zt_split(nb) && fa.numRegs < ZT_REG_LAUNCH) {
+            // the register split assumes this launch allocation
+            rc_launch = set_err(ctx, HFX_EUNSUPPORTED, "zipw kernel compiled with fewer registers than its warpgroup split needs");
+            return;
+        }
         const size_t stage = (size_t)NPL * 128 * KC * 2 + (size_t)KSEG * NPL * 2 * nb * 16;
         size_t smem = std::max<size_t>((size_t)zt_stages(KSEG) * stage + 1024, (size_t)smem_max - fa.sharedSizeBytes);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ev0) record_event(ev0, st);
-        kern<<<grid, 64 + 32 * ZT_EPI, smem, st>>>(mA, p);
+        kern<<<grid, ZT_THREADS, smem, st>>>(mA, p);
         if (ev1) record_event(ev1, st);
     };
     switch (zb.NBt) {
@@ -821,6 +838,7 @@ int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, co
     case 56: go(zipw_tc_kernel<56>, 56); break;
     default: go(zipw_tc_kernel<64>, 64); break;
     }
+    if (rc_launch) return rc_launch;
     if (nlaunch) *nlaunch += 2;
     return cuda_check(ctx, cudaGetLastError(), "zipw tensor-core kernel");
 }
