@@ -78,3 +78,50 @@ def test_generator_is_deterministic_and_hermitian():
     for v in a.v:
         assert np.abs(v - v.conj().T).max() < 1e-14 * np.abs(v).max()
         assert np.linalg.eigvalsh(v).min() > 0
+
+
+def test_inversion_needs_partner_atoms(libpath):
+    """hfx_create with inversion = 1 checks, before touching the device, that
+    every atom has a partner at -R_a (same sphere radius): the zincblende pair
+    of config 1 has none (HFX_EINVAL); the centred pair of its inversion
+    variant passes the check and then needs the device."""
+    plain = S.make_system(1, mesh=(1, 1, 2), nb=3, no=2)
+    opt = hfx.hfx_default_options()
+    opt.inversion = 1
+    with pytest.raises(hfx.HfxError) as e:
+        hfx.hfx_create(plain.lattice, plain.pos_frac, plain.rmt, plain.lmax, plain.Lmax, plain.P, plain.mesh, opt)
+    assert e.value.code == hfx.HFX_EINVAL
+    # unequal radii of the partners
+    inv = S.make_system(1, mesh=(1, 1, 2), nb=3, no=2, inversion=True)
+    with pytest.raises(hfx.HfxError) as e:
+        hfx.hfx_create(inv.lattice, inv.pos_frac, np.array([2.2, 2.1]), inv.lmax, inv.Lmax, inv.P, inv.mesh, opt)
+    assert e.value.code == hfx.HFX_EINVAL
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return
+    except ImportError:
+        pass
+    with pytest.raises(hfx.HfxError) as e:
+        hfx.hfx_create(inv.lattice, inv.pos_frac, inv.rmt, inv.lmax, inv.Lmax, inv.P, inv.mesh, opt)
+    assert e.value.code in (hfx.HFX_EDEVICE, hfx.HFX_EUNSUPPORTED)
+
+
+def test_inversion_generator_obeys_its_stated_relations():
+    """The generator's inversion variant, checked against the relation the
+    library enforces (real c; A of the partner from A of the atom)."""
+    s = S.make_system(4, mesh=(1, 2, 2), nb=4, no=2, aux=("count", 50, 50), inversion=True)
+    p = S.inversion_partners(s.pos_frac, s.rmt)
+    for ik in range(s.n_k):
+        assert not np.any(s.c[ik].imag)
+        kf = s.kpoint_frac(ik)
+        for a in range(s.n_atoms):
+            b = int(p[a])
+            ph = np.exp(2j * np.pi * kf @ np.round(s.pos_frac[a] + s.pos_frac[b]))
+            for l in range(s.lmax + 1):
+                for m in range(-l, l + 1):
+                    for q in range(2):
+                        x = s.A[ik][:, a, 2 * (l * l + l + m) + q]
+                        y = s.A[ik][:, b, 2 * (l * l + l - m) + q]
+                        assert np.abs(y - (-1) ** (l + m) * ph * np.conj(x)).max() < 1e-14
+    assert np.array_equal(s.R[0], s.R[p[0]]) and np.array_equal(s.mu[0], s.mu[p[0]])
