@@ -352,9 +352,12 @@ int zipw_tc_plan_batch(hfx_ctx *ctx, const ZipwBuild &zb, const std::vector<int>
                        HostArena &tab, ZipwBatch &bt);
 int zipw_tc_run_build(hfx_ctx *ctx, const ZipwBuild &zb, const char *dtab, char *dscr, const double2 *const *d_ck,
                       const int *const *d_Gk, const int *d_npw, const double2 *const *d_Tk, const int *d_nb);
+// The interstitial rows come out G-major into d_ZI [g][NCi] (the kernel's
+// stores then fill whole sectors) and are transposed into d_Z after the kernel.
 int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, const char *dtab, const char *dscr,
                       __nv_bfloat16 *dTq, const PairDesc *d_pairs, const double2 *const *d_Tk, const int *d_nb,
-                      double2 *d_Z, long long RSc, cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch);
+                      double2 *d_Z, long long RSc, double2 *d_ZI, long long NCi, const QDesc *d_qd, int nq,
+                      long long maxcols, int max_nipw, cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch);
 
 // ------------------------------------------------------------ stage-1 products on the tensor cores (k_cgemm_tc.cu)
 struct TpPlan {                             // T_n(K) of every k of the build (Sec. III.B)

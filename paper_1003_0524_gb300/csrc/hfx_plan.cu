@@ -645,10 +645,15 @@ int plan_run(hfx_ctx *ctx, BuildPlan &pl, int keep, int fail_wait) {
         }
         rec(ctx, bt.ev[1]);
         if (tc && sizeof(R) == 8) {
+            // the G-major output plane of the interstitial kernel lives in the Y buffer,
+            // which is free until the Coulomb apply
+            int max_nipw = 0;
+            for (auto &q : bt.qd) max_nipw = std::max(max_nipw, q.nipw);
             if ((rc = zipw_tc_run_batch(ctx, pl.zipw, bt.zipw, tab, reinterpret_cast<char *>(ctx->s_zipw.p),
                                         at<__nv_bfloat16>(ctx->s_zipw.p, pl.zipw_tq_off), d_pairs,
                                         reinterpret_cast<const double2 *const *>(tab + pl.o_T),
                                         reinterpret_cast<const int *>(tab + pl.o_nb), reinterpret_cast<double2 *>(Zc), RSc,
+                                        reinterpret_cast<double2 *>(ctx->s_y64.p), bt.ncols, d_qd, nq, bt.maxcols, max_nipw,
                                         bt.ev[2], bt.ev[3], &nl)))
                 return rc;
         } else {

@@ -199,8 +199,8 @@ struct ZParams {
     const int *runs;              // [row tile][chunk] bit j: segment j of the chunk starts a bulk copy; bits 8..: live segments
     const __nv_bfloat16 *Tq;      // sliced T blocks (t_slices_kernel layout)
     int td0, td1, nzb, nblk, nslot;
-    double2 *Z;
-    long long RSc;
+    double2 *ZI;                  // output plane ZI[g][col] (rows g of the interstitial part, G-major)
+    long long NCi;                // row stride of ZI: the columns of the batch
     int nmt, nk, R, Rpad, nbmax, tlo0, tlo1, tlo2;
     double rs;                    // Omega^{-1/2}
     int *err;
@@ -451,7 +451,9 @@ __global__ void __launch_bounds__(ZT_THREADS, 1) zipw_tc_kernel(const __grid_con
             }
             if (!ok) break;
             if (g >= 0) {
-                double2 *out = p.Z + col * p.RSc + p.nmt + g;
+                // G-major: this row's bands are consecutive columns of row g, so the
+                // thread's stores fill whole sectors (the transpose into Z follows)
+                double2 *out = p.ZI + (size_t)g * p.NCi + col;
 #pragma unroll
                 for (int jj = 0; jj < NH; ++jj) {
                     if (jj < nlive) {
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(ZT_THREADS, 1) zipw_tc_kernel(const __grid_con
                         const int ex = ea + s_eT[e][jj];
                         v.x = f32pair_to_f64_int(odd ? h1.y : h1.x, odd ? l1.y : l1.x, ex);
                         v.y = f32pair_to_f64_int(odd ? h2.y : h2.x, odd ? l2.y : l2.x, ex);
-                        __stcs(out + jj * p.RSc, v);   // streaming: keep the operands in L2
+                        __stcs(out + jj, v);   // streaming: keep the operands in L2
                     }
                 }
             }
@@ -475,6 +477,33 @@ __global__ void __launch_bounds__(ZT_THREADS, 1) zipw_tc_kernel(const __grid_con
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
+    }
+}
+
+// Z[col][nmt + g] = ZI[g][col] for the interstitial rows g < nipw(q) of every
+// column of every q of the batch: 32 x 32 tiles through shared memory, reads
+// along the columns of ZI and writes along the rows of Z, both coalesced.
+__global__ void __launch_bounds__(256) ipw_transpose_kernel(const double2 *__restrict__ ZI, long long NCi,
+                                                            double2 *__restrict__ Z, long long RSc, int nmt,
+                                                            const QDesc *__restrict__ qd) {
+    __shared__ double2 tile[32][33];
+    const QDesc q = qd[blockIdx.z];
+    const long long c0 = (long long)blockIdx.x * 32;
+    const int g0 = blockIdx.y * 32;
+    if (c0 >= q.ncols || g0 >= q.nipw) return;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int g = g0 + ty + 8 * i;
+        const long long c = c0 + tx;
+        if (g < q.nipw && c < q.ncols) tile[ty + 8 * i][tx] = ZI[(size_t)g * NCi + q.colbase + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long c = c0 + ty + 8 * i;
+        const int g = g0 + tx;
+        if (g < q.nipw && c < q.ncols) Z[(size_t)(q.colbase + c) * RSc + nmt + g] = tile[tx][ty + 8 * i];
     }
 }
 
@@ -757,7 +786,8 @@ int zipw_tc_valid_nb(int nb) { return nb >= 8 && nb <= 64 && nb % 8 == 0; }
 // Per batch: T slices of the batch's k and the GEMM.
 int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, const char *dtab, const char *dscr,
                       __nv_bfloat16 *dTq, const PairDesc *d_pairs, const double2 *const *d_Tk, const int *d_nb,
-                      double2 *d_Z, long long RSc, cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch) {
+                      double2 *d_Z, long long RSc, double2 *d_ZI, long long NCi, const QDesc *d_qd, int nq,
+                      long long maxcols, int max_nipw, cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch) {
     if (!zb.ok || !bt.ok) return HFX_OK;
     cudaStream_t st = ctx->stream;
     int rc;
@@ -796,8 +826,8 @@ int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, co
     p.nzb = zb.nzb;
     p.nblk = zb.nblk;
     p.nslot = bt.nslot;
-    p.Z = d_Z;
-    p.RSc = RSc;
+    p.ZI = d_ZI;
+    p.NCi = NCi;
     p.nmt = ctx->nmt;
     p.nk = ctx->nk;
     p.R = zb.R;
@@ -839,8 +869,13 @@ int zipw_tc_run_batch(hfx_ctx *ctx, const ZipwBuild &zb, const ZipwBatch &bt, co
     default: go(zipw_tc_kernel<64>, 64); break;
     }
     if (rc_launch) return rc_launch;
-    if (nlaunch) *nlaunch += 2;
-    return cuda_check(ctx, cudaGetLastError(), "zipw tensor-core kernel");
+    if ((rc = cuda_check(ctx, cudaGetLastError(), "zipw tensor-core kernel"))) return rc;
+    if (nq > 0 && maxcols > 0 && max_nipw > 0) {
+        const dim3 tg((unsigned)((maxcols + 31) / 32), (unsigned)((max_nipw + 31) / 32), (unsigned)nq);
+        ipw_transpose_kernel<<<tg, 256, 0, st>>>(d_ZI, NCi, d_Z, RSc, ctx->nmt, d_qd);
+    }
+    if (nlaunch) *nlaunch += 3;
+    return cuda_check(ctx, cudaGetLastError(), "interstitial transpose");
 }
 
 }  // namespace hfx
