@@ -643,8 +643,10 @@ int prepare_coulomb(hfx_ctx *ctx) {
         for (int iq = 0; iq < ctx->nk; ++iq) {
             QPoint &q = ctx->qp[iq];
             int naux = ctx->nmt + q.nipw;
+            // the complex path interleaves the real and imaginary rows of U; the real
+            // path (inversion symmetry) keeps them in two blocks
             launch_build_ap(q.d_VD, ap + per * iq, aexp + (size_t)MP * iq, naux - ctx->N0, naux, ctx->N0, N0pad, Dpad, RS,
-                            ctx->stream);
+                            ctx->opt.inversion ? 0 : 1, ctx->stream);
         }
         if ((rc = cuda_check(ctx, cudaGetLastError(), "slice embedding")) || (rc = sync(ctx))) return rc;
     }

@@ -239,9 +239,10 @@ void launch_transform_v(const double2 *d_v, double2 *d_VD, double2 *d_VB, const 
                         unsigned long long *d_absmax, cudaStream_t st);
 // Fixed-point slices (four BF16 planes, per-row exponents) of the real
 // embedding [[Ur,-Ui],[Ui,Ur]] of U, the dense-block rows of the upper triangle
-// of v_t with half its diagonal.
+// of v_t with half its diagonal; interleave: the real and imaginary rows of each
+// row of U adjacent (complex path), else in two blocks (real path).
 void launch_build_ap(const double2 *d_VD, __nv_bfloat16 *d_Ap, int *d_aexp, int D, int naux, int N0, int N0pad,
-                     int Dpad, int RS, cudaStream_t st);
+                     int Dpad, int RS, int interleave, cudaStream_t st);
 // q->0 bracket of Eq. (div final) into *d_out (FP64); d_partial holds
 // q0_partial_count() doubles.
 void launch_q0_bracket_impl(double *d_out, double *d_partial, const int mesh[3], const double *B, double omega,

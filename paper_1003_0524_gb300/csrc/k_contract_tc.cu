@@ -238,7 +238,8 @@ __global__ void block_y_df_kernel(const QDesc *__restrict__ qd, const double2 *c
 // the MMA warp waits for the epilogue to read a K group before the next).
 // Each CTA loads the A and B tiles of its own output tile.
 // K of each half: [kbeg, kbeg + klen); iq: the q of A.  half < 0: both K halves
-// (complex v_t, rows [0, D) real and [D, 2D) imaginary parts of Y');
+// (complex v_t; row 2r of A' gives the real, 2r + 1 the imaginary part of row r
+// of Y', so a warp's stores into one column of Y' are contiguous);
 // half = 0 / 1 (real v_t): rows [0, D) of A' (U itself) against the real or
 // imaginary half of the Z columns, giving the real or imaginary part of Y'.
 struct G1Tile { int qslot, mrow, ncol0, klen, iq, kbeg, half; };
@@ -396,9 +397,9 @@ __global__ void __launch_bounds__(G1_THREADS, 1) gemm1_kernel(const __grid_const
             // this half (lane l holds columns l and 32 + l; the store loop shuffles
             // them), fetched at tile start so that their latency overlaps the first
             // K group instead of following the last one
-            const int r = tl.mrow + quarter * 32 + lane;     // row of A' in this q: [0, D) real, [D, 2D) imaginary
-            const bool im = tl.half < 0 ? r >= q.D : tl.half == 1;
-            const int rr = (tl.half < 0 && im) ? r - q.D : r;
+            const int r = tl.mrow + quarter * 32 + lane;     // row of A' in this q
+            const bool im = tl.half < 0 ? (r & 1) : tl.half == 1;
+            const int rr = tl.half < 0 ? (r >> 1) : r;
             const bool live = rr < q.D;
             const long long c0 = tl.ncol0 + half * 64, cend = q.colbase + q.ncols;
             const int ea = live ? p.aexp[(size_t)q.iq * p.MP + r] - 16 : 0;
@@ -840,14 +841,14 @@ int gemm1_tiles(const QDesc *h_q, int nq, int N0pad, bool real_v, std::vector<un
     std::vector<G1Tile> tiles;
     for (int s = 0; s < nq; ++s) {
         const QDesc &q = h_q[s];
-        // row tiles over the D real and D imaginary rows; with a real v_t over
-        // the D rows of U, each taken once per half of the Z columns
+        // row tiles over the 2 D interleaved real and imaginary rows; with a real
+        // v_t over the D rows of U, each taken once per half of the Z columns
         const int rows = real_v ? q.D : 2 * q.D;
         const int mt = (rows + G1_BM - 1) / G1_BM;
         std::vector<int> kbeg(mt), klen(mt);
         for (int i = 0; i < mt; ++i) {
-            const int r0 = i * G1_BM, r1 = std::min(rows, r0 + G1_BM);   // rows [r0, r1)
-            const int rmin = real_v ? r0 : ((r0 < q.D && r1 > q.D) ? 0 : (r0 < q.D ? r0 : r0 - q.D));
+            const int r0 = i * G1_BM;   // rows [r0, r0 + 128) of A': rows r0 / 2 .. of U when interleaved
+            const int rmin = real_v ? r0 : r0 / 2;
             kbeg[i] = N0pad + rmin / G1_KC * G1_KC;
             klen[i] = (N0pad + q.D - kbeg[i] + G1_KC - 1) / G1_KC * G1_KC;
         }

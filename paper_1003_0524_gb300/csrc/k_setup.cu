@@ -270,9 +270,11 @@ __global__ void transform_v_kernel(const double2 *v, double2 *VD, double2 *VB, c
 // Dpad)] (zero in the padding).  In the order [mu=0 | dense], the mu = 0
 // columns of the dense-block rows lie below the diagonal and are zero in U.
 __device__ __forceinline__ double ap_elem(const double2 *VD, int r, int c, int D, int naux, int N0, int N0pad,
-                                         int Dpad) {
+                                         int Dpad, int interleave) {
     int HS = N0pad + Dpad;
-    int rim = r >= D, rr = rim ? r - D : r;   // real rows [0, D), imaginary rows [D, 2D)
+    // interleaved: row 2r real, 2r + 1 imaginary part of row r; else real rows
+    // [0, D), imaginary rows [D, 2D)
+    int rim = interleave ? (r & 1) : (r >= D), rr = interleave ? (r >> 1) : (rim ? r - D : r);
     int cim = c >= HS, u = cim ? c - HS : c;
     if (rr >= D || u < N0pad) return 0.0;
     const int d = u - N0pad;                  // dense column index
@@ -285,17 +287,19 @@ __device__ __forceinline__ double ap_elem(const double2 *VD, int r, int c, int D
     return val.x;
 }
 
-// Fixed-point slices of A' (one block per row; rows [0, D) real, [D, 2D)
-// imaginary, the rest of the 2 Dpad rows zero): exponent e_r with
+// Fixed-point slices of A' (one block per row; rows 2r and 2r + 1 the real and
+// imaginary parts of row r, or with a real v_t rows [0, D) real and [D, 2D)
+// imaginary; the rest of the 2 Dpad rows zero): exponent e_r with
 // max_c |A'_rc| < 2^e_r, then the four slices of tc_ptx.cuh per element, stored
 // as BF16 planes [4][2 Dpad][RS] (the slice format of k_contract_tc.cu).
 __global__ void build_ap_kernel(const double2 *VD, __nv_bfloat16 *Ap, int *aexp, int D, int naux, int N0, int N0pad,
-                                int Dpad, int RS) {
+                                int Dpad, int RS, int interleave) {
     int r = blockIdx.x;
     long long plane = 2LL * Dpad * RS;
     __shared__ unsigned long long red[256];
     unsigned long long mx = 0;
-    for (int c = threadIdx.x; c < RS; c += blockDim.x) mx = max(mx, tc::abs_bits(ap_elem(VD, r, c, D, naux, N0, N0pad, Dpad)));
+    for (int c = threadIdx.x; c < RS; c += blockDim.x)
+        mx = max(mx, tc::abs_bits(ap_elem(VD, r, c, D, naux, N0, N0pad, Dpad, interleave)));
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
@@ -306,7 +310,7 @@ __global__ void build_ap_kernel(const double2 *VD, __nv_bfloat16 *Ap, int *aexp,
     if (threadIdx.x == 0) aexp[r] = e;
     for (int c = threadIdx.x; c < RS; c += blockDim.x) {
         __nv_bfloat16 sl[tc::NPL];
-        tc::slice4(ap_elem(VD, r, c, D, naux, N0, N0pad, Dpad), e, sl);
+        tc::slice4(ap_elem(VD, r, c, D, naux, N0, N0pad, Dpad, interleave), e, sl);
         for (int i = 0; i < tc::NPL; ++i) Ap[i * plane + (long long)r * RS + c] = sl[i];
     }
 }
@@ -395,8 +399,8 @@ void launch_transform_v(const double2 *d_v, double2 *d_VD, double2 *d_VB, const 
 }
 
 void launch_build_ap(const double2 *d_VD, __nv_bfloat16 *d_Ap, int *d_aexp, int D, int naux, int N0, int N0pad,
-                     int Dpad, int RS, cudaStream_t st) {
-    build_ap_kernel<<<2 * Dpad, 256, 0, st>>>(d_VD, d_Ap, d_aexp, D, naux, N0, N0pad, Dpad, RS);
+                     int Dpad, int RS, int interleave, cudaStream_t st) {
+    build_ap_kernel<<<2 * Dpad, 256, 0, st>>>(d_VD, d_Ap, d_aexp, D, naux, N0, N0pad, Dpad, RS, interleave);
 }
 
 // q->0 bracket with box bounds from the lattice (|n_i| <= q0 |a_i| / 2pi + 2).
