@@ -78,3 +78,17 @@ def test_linear_dependence_removal_keeps_the_rank():
     assert np.sqrt(np.sum(w * r * r * res ** 2)) < 1e-8 * np.sqrt(np.sum(w * r * r * x ** 2))
     with pytest.raises(ValueError):
         O.mpb_radial(r, w, u, lmax, 0, 8, thr=1e-10)
+
+
+def test_product_basis_at_the_papers_lmax():
+    """lmax = 8 (the paper's setting for its crystals): 171 candidate products per
+    L; the kept functions stay orthonormal and their Coulomb blocks positive
+    definite."""
+    Sr, lmax, Lmax, P = 2.1, 8, 4, 4
+    r, w, u = S.radial_functions(lmax, Sr, 300, seed=11)
+    b = O.mpb_radial(r, w, u, lmax, Lmax, P)
+    for L in range(Lmax + 1):
+        M = b["M"][L * P:(L + 1) * P]
+        G = (M * (w * r * r)) @ M.T
+        assert np.abs(G - np.eye(P)).max() < 1e-10
+        assert np.linalg.eigvalsh(b["C"][L]).min() > 0.0
